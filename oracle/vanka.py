@@ -1,0 +1,66 @@
+"""Additive Vanka relaxation (Sec. 3.3.1).
+
+One sweep on level l is x <- x + omega * M^-1 (b - K x) with
+
+    M^-1 = sum_i V_i^T W_i (V_i K V_i^T)^-1 V_i          (Eq. vanka)
+
+V_i injects the DoFs of patch i, W_i is the partition of unity whose entries
+are 1 / (number of patches holding the DoF).  Each patch system
+K_i = V_i K V_i^T is formed densely and solved by LU with partial pivoting
+(LAPACK gesv) - deliberately not the block factorisation of Eqs.
+vanka_fact1/2 that the CUDA path uses.
+"""
+import numpy as np
+
+
+def patch_lists(patches):
+    ptr, dof = patches.ptr, patches.dof
+    return [dof[ptr[i]:ptr[i + 1]] for i in range(ptr.size - 1)]
+
+
+def partition_of_unity(patches, n):
+    """Diagonal of W: 1 / number of patches holding each DoF (0 if none)."""
+    cnt = np.bincount(patches.dof, minlength=n).astype(np.float64)
+    w = np.zeros(n)
+    w[cnt > 0] = 1.0 / cnt[cnt > 0]
+    return w
+
+
+class VankaLevel:
+    """Dense patch matrices K_i = V_i K V_i^T of one level, grouped by size
+    so that numpy can solve each group in one call (the solves are
+    independent, so grouping changes no result)."""
+
+    def __init__(self, K, patches):
+        K = K.tocsr()
+        self.n = K.shape[0]
+        self.W = partition_of_unity(patches, self.n)
+        lists = patch_lists(patches)
+        sizes = np.array([len(p) for p in lists])
+        self.groups = []
+        for m in np.unique(sizes):
+            ids = np.nonzero(sizes == m)[0]
+            idx = np.stack([lists[i] for i in ids]).astype(np.int64)  # g x m
+            mats = np.stack([K[ix][:, ix].toarray() for ix in idx])   # g x m x m
+            self.groups.append((ids, idx, mats))
+        self.npatch = len(lists)
+
+    def apply(self, r):
+        """Return M^-1 r = sum_i V_i^T W_i K_i^-1 V_i r, summing each DoF's
+        contributions in ascending patch order."""
+        ixs = [None] * self.npatch
+        ys = [None] * self.npatch
+        for ids, idx, mats in self.groups:
+            y = np.linalg.solve(mats, r[idx][:, :, None])[:, :, 0]
+            for k, i in enumerate(ids):
+                ixs[i] = idx[k]
+                ys[i] = y[k]
+        acc = np.zeros(self.n)
+        if self.npatch:
+            # np.add.at accumulates sequentially, i.e. in ascending patch order
+            np.add.at(acc, np.concatenate(ixs), np.concatenate(ys))
+        return self.W * acc
+
+    def sweep(self, K, x, b, omega):
+        """One stationary damped sweep x <- x + omega M^-1 (b - K x)."""
+        return x + omega * self.apply(b - K @ x)

@@ -1,0 +1,31 @@
+"""The synthetic workloads and their solver parameters.
+
+Each entry names the problem (mesh, element pair, boundary conditions,
+right-hand side, seeds) and the solver parameters of the defect-correction
+cycle.  Parameter sources: eta from the optimal-damping table for Taylor-Hood
+(Sec. 4.1: DC-all Vanka, 2D structured 0.75, 3D 1.00) and the
+(omega_0, eta_p) table for Scott-Vogelius (Sec. 4.2); the stationary Vanka
+damping omega for Taylor-Hood from the brute-force search of Sec. 4
+(run by the oracle's search tool on the 16^2 and 64^2 lid/manufactured
+problems: 0.70 and 0.55; the larger problem's value is kept).
+"""
+from . import mesh as M, stokes
+
+# cycle parameters ------------------------------------------------------------
+TH2D_VANKA = dict(schedule=0, nu1=1, nu2=1, eta_u=0.75, eta_p=0.75, omega=0.55)
+TH3D_VANKA = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=1.0, omega=0.55)
+SV2D_VANKA = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=2.68, omega0=0.78, omega=0.55)
+SV2D_VANKA_DLSC = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=2.96, omega0=0.87, omega=1.0)
+
+FGMRES = dict(rtol=1e-8, restart=30, maxit=600)
+
+
+def c1():
+    """2D Taylor-Hood 16x16, lid-driven cavity, f = 0, nu = 1."""
+    return stokes.build_th(M.unit_square(16), nu=1.0, bc="lid", rhs="zero", name="C1 TH2D 16^2 lid")
+
+
+def c2(n=256):
+    """2D Taylor-Hood 256x256, manufactured smooth solution, ~6 levels."""
+    return stokes.build_th(M.unit_square(n), nu=1.0, bc="noslip", rhs="manufactured",
+                           max_levels=6, name=f"C2 TH2D {n}^2 manufactured")

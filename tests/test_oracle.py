@@ -1,0 +1,199 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by linear
+algebra: the partition of unity of Eq. vanka, the block factorisation of
+Eqs. vanka_fact1/2 against dense LU on every patch, a single all-covering
+patch against a direct solve, the two-level form of Eq. TG-operator-full as
+a dense operator product, the Chebyshev closed form, FGMRES special cases,
+and convergence of the stationary DC iteration."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import cycle, direct, krylov, vanka
+from problems import configs, mesh as M, stokes
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return configs.c1()
+
+
+def test_partition_of_unity(c1):
+    for l, pa in enumerate(c1.patches):
+        n = c1.K[l].shape[0]
+        W = vanka.partition_of_unity(pa, n)
+        s = np.zeros(n)
+        for ix in vanka.patch_lists(pa):
+            s[ix] += 1.0
+        covered = s > 0
+        assert np.allclose((W * s)[covered], 1.0, atol=1e-15)
+        # every non-Dirichlet DoF of the assembled levels lies in some patch
+        if l <= 1:
+            assert np.array_equal(covered, ~c1.dirichlet)
+
+
+def _block_solve(Kp, m_u, m_p, rhs):
+    """x = [I U^; 0 I][A^-1 0; B^ S^-1] b with U = A^-1 B^T, S = -B A^-1 B^T,
+    B^ = -S^-1 B A^-1, U^ = -U (Eqs. vanka_fact1/2)."""
+    A = Kp[:m_u, :m_u]
+    B = Kp[m_u:, :m_u]
+    Ainv = np.linalg.inv(A)
+    U = Ainv @ B.T
+    S = -B @ U
+    Sinv = np.linalg.inv(S)
+    Bh = -Sinv @ B @ Ainv
+    Uh = -U
+    y_u = Ainv @ rhs[:m_u]
+    y_p = Bh @ rhs[:m_u] + Sinv @ rhs[m_u:]
+    return np.concatenate([y_u + Uh @ y_p, y_p])
+
+
+def test_block_factorisation_equals_dense_lu(c1):
+    rng = np.random.default_rng(0)
+    worst = 0.0
+    for l, pa in enumerate(c1.patches):
+        K = c1.K[l].tocsr()
+        for i, ix in enumerate(vanka.patch_lists(pa)):
+            Kp = K[ix][:, ix].toarray()
+            m_p = int(pa.npres[i])
+            m_u = ix.size - m_p
+            rhs = rng.standard_normal(ix.size)
+            x_lu = np.linalg.solve(Kp, rhs)
+            x_bf = _block_solve(Kp, m_u, m_p, rhs)
+            worst = max(worst, np.linalg.norm(x_bf - x_lu) / np.linalg.norm(x_lu))
+            # the velocity block is block diagonal by component (vector Laplacian)
+            m = pa.nvel[i, 0]
+            assert np.abs(Kp[:m, m:2 * m]).max() == 0.0
+    assert worst < 1e-12
+
+
+def test_single_patch_is_a_direct_solve(c1):
+    """One patch holding every free DoF except one pressure DoF (which fixes
+    the pressure constant): Vanka with W = 1 is an exact solve."""
+    K = c1.K[0].tocsr()
+    n = K.shape[0]
+    off = c1.field_off[0]
+    free = np.nonzero(~c1.dirichlet)[0]
+    free = free[free != off[2]]
+    nv = np.sum(free < off[1])
+    pa = stokes.Patches(np.array([0, free.size]), free.astype(np.int32),
+                        np.array([[nv, nv]], dtype=np.int32), np.array([off[3] - off[2] - 1], dtype=np.int32))
+    vl = vanka.VankaLevel(K, pa)
+    rng = np.random.default_rng(1)
+    xs = rng.standard_normal(n)
+    xs[c1.dirichlet] = 0.0
+    r = K @ xs
+    z = vl.apply(r)
+    ref = xs.copy()
+    ref[off[2]:] -= xs[off[2]]
+    ref[c1.dirichlet] = 0.0
+    assert np.linalg.norm(z - ref) < 1e-10 * np.linalg.norm(ref)
+
+
+def _dense_vanka(K, pa):
+    n = K.shape[0]
+    Kd = K.toarray()
+    W = vanka.partition_of_unity(pa, n)
+    Minv = np.zeros((n, n))
+    for ix in vanka.patch_lists(pa):
+        Minv[np.ix_(ix, ix)] += np.linalg.inv(Kd[np.ix_(ix, ix)])
+    return W[:, None] * Minv
+
+
+def test_two_level_cycle_is_eq_tg_operator_full():
+    """With K1 as the coarsest level (gamma = infinity), one DC application
+    has error propagation
+    G = (I - w M0^-1 K0)(I - P0 K1^-1 eta R0 K0)(I - w M0^-1 K0)."""
+    pr = stokes.build_th(M.unit_square(6), bc="lid", max_levels=2)
+    assert pr.nlevels == 2
+    par = cycle.Params(eta_u=0.8, eta_p=0.6, omega=[0.55])
+    o = cycle.Oracle(pr, par)
+    K0 = pr.K[0].toarray()
+    K1 = pr.K[1].toarray()
+    n = K0.shape[0]
+    Minv = _dense_vanka(pr.K[0], pr.patches[0])
+    S = np.eye(n) - 0.55 * Minv @ K0
+    nvec = pr.coarse_null
+    Bd = np.block([[K1, nvec[:, None]], [nvec[None, :], np.zeros((1, 1))]])
+    K1inv = np.linalg.inv(Bd)[:n, :n]
+    off = pr.field_off[0]
+    eta = np.diag(np.concatenate([np.full(off[2], 0.8), np.full(off[3] - off[2], 0.6)]))
+    P0 = pr.P[0].toarray()
+    G = S @ (np.eye(n) - P0 @ K1inv @ eta @ P0.T @ K0) @ S
+    rng = np.random.default_rng(2)
+    e = rng.standard_normal(n)
+    e[pr.dirichlet] = 0.0
+    z = o.apply(K0 @ e)
+    free = ~pr.dirichlet
+    lhs = (e - z)[free]
+    rhs = (G @ e)[free]
+    assert np.linalg.norm(lhs - rhs) < 1e-11 * np.linalg.norm(e)
+
+
+def test_dropping_eta_is_detected():
+    """A planted mistake (eta ignored) breaks the two-level identity above."""
+    pr = stokes.build_th(M.unit_square(4), bc="lid", max_levels=2)
+    par = cycle.Params(eta_u=0.8, eta_p=0.6, omega=[0.55])
+    good = cycle.Oracle(pr, par)
+    bad = cycle.Oracle(pr, par)
+    bad.eta = np.ones_like(bad.eta)
+    r = np.random.default_rng(3).standard_normal(pr.K[0].shape[0])
+    assert np.linalg.norm(good.apply(r) - bad.apply(r)) > 1e-3 * np.linalg.norm(good.apply(r))
+
+
+def test_chebyshev_jacobi_closed_form():
+    """On an eigenvector of D^-1 M with eigenvalue mu in [a, b] the error of
+    the degree-k semi-iteration is T_k((b+a-2mu)/(b-a)) / T_k((b+a)/(b-a))."""
+    n = 50
+    M_ = sp.diags([-0.5, 2.0, -0.5], [-1, 0, 1], shape=(n, n)).tocsr()  # D^-1 M = I - T/4
+    a, b = 0.5, 1.5
+    for j in (1, 7, 30):
+        mu = 1.0 - 0.5 * np.cos(j * np.pi / (n + 1))
+        v = np.sin(j * np.pi * np.arange(1, n + 1) / (n + 1))
+        for k in (1, 4, 9):
+            x = cycle.chebyshev_jacobi(M_, M_ @ v, a, b, k)
+            err = np.linalg.norm(x - v) / np.linalg.norm(v)
+            Tk = lambda t: np.cosh(k * np.arccosh(t)) if abs(t) >= 1 else np.cos(k * np.arccos(t))
+            pred = abs(Tk((b + a - 2 * mu) / (b - a)) / Tk((b + a) / (b - a)))
+            assert abs(err - pred) < 1e-12
+
+
+def test_fgmres_identity_is_gmres_and_exact_in_n_steps():
+    rng = np.random.default_rng(4)
+    n = 30
+    A = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    b = rng.standard_normal(n)
+    x, its, rr = krylov.gmres_identity(A, b, rtol=1e-13)
+    assert its <= n and rr < 1e-13
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) < 1e-11 * np.linalg.norm(x)
+    # an exact preconditioner converges in one iteration
+    x1, its1, rr1 = krylov.fgmres(A, b, lambda v: np.linalg.solve(A, v), rtol=1e-12)
+    assert its1 == 1 and rr1 < 1e-12
+    # the residual history of GMRES is monotone
+    h = []
+    krylov.fgmres(A, b, lambda v: v.copy(), rtol=1e-12, restart=n, history=h)
+    assert all(h[k + 1] <= h[k] * (1 + 1e-12) for k in range(len(h) - 1))
+
+
+def test_stationary_dc_iteration_contracts(c1):
+    par = cycle.Params(**{k: v for k, v in configs.TH2D_VANKA.items() if k != "omega"},
+                       omega=[configs.TH2D_VANKA["omega"]] * (c1.nlevels - 1))
+    o = cycle.Oracle(c1, par)
+    K, b = c1.K[0], c1.b
+    x = np.zeros_like(b)
+    res = []
+    for _ in range(25):
+        x = x + o.apply(b - K @ x)
+        res.append(np.linalg.norm(b - K @ x))
+    factor = (res[-1] / res[-11]) ** 0.1
+    assert factor < 0.9, factor
+
+
+def test_fgmres_dc_solves_c1_to_tolerance(c1):
+    par = cycle.Params(**{k: v for k, v in configs.TH2D_VANKA.items() if k != "omega"},
+                       omega=[configs.TH2D_VANKA["omega"]] * (c1.nlevels - 1))
+    o = cycle.Oracle(c1, par)
+    x, its, rr = krylov.fgmres(c1.K[0], c1.b, o.apply, rtol=1e-8, restart=30, maxit=100)
+    assert rr <= 1e-8 and its <= 20
+    xd = direct.solve_stokes(c1.K[0], c1.b, c1.field_off[0], 2, Mp=c1.Mp)
+    xz = direct.zero_mean_pressure(x, c1.field_off[0], 2, c1.Mp)
+    assert np.linalg.norm(xz - xd) < 1e-6 * np.linalg.norm(xd)
