@@ -33,6 +33,7 @@ class VankaLevel:
 
     def __init__(self, K, patches):
         K = K.tocsr()
+        K.sort_indices()
         self.n = K.shape[0]
         self.W = partition_of_unity(patches, self.n)
         lists = patch_lists(patches)
@@ -41,9 +42,35 @@ class VankaLevel:
         for m in np.unique(sizes):
             ids = np.nonzero(sizes == m)[0]
             idx = np.stack([lists[i] for i in ids]).astype(np.int64)  # g x m
-            mats = np.stack([K[ix][:, ix].toarray() for ix in idx])   # g x m x m
+            mats = np.concatenate([self._dense_blocks(K, idx[s:s + 4096]) for s in range(0, len(ids), 4096)])
             self.groups.append((ids, idx, mats))
         self.npatch = len(lists)
+
+    @staticmethod
+    def _dense_blocks(K, idx):
+        """K_i = V_i K V_i^T for a batch of equal-size patches (rows of idx):
+        entry (a, b) of patch i is K[idx[i, a], idx[i, b]] (0 if not stored)."""
+        g, m = idx.shape
+        assert np.all(np.diff(idx, axis=1) > 0), "patch lists ascend (velocity x, y[, z], pressure)"
+        out = np.zeros((g, m, m))
+        rows = idx.ravel()
+        cnt = np.diff(K.indptr)[rows]
+        pid = np.repeat(np.arange(g * m), cnt)              # (patch, local row) of each entry
+        starts = np.repeat(K.indptr[rows], cnt)
+        offs = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        cols = K.indices[starts + offs]
+        vals = K.data[starts + offs]
+        p = pid // m
+        a = pid % m
+        # local column: position of cols in the patch list (ascending, exact match)
+        key_tab = (np.arange(g)[:, None] * (K.shape[1] + 1) + idx).ravel()   # sorted: lists ascend
+        key = p * (K.shape[1] + 1) + cols
+        pos = np.searchsorted(key_tab, key)
+        pos = np.minimum(pos, key_tab.size - 1)
+        hit = key_tab[pos] == key
+        b = pos - p * m
+        out[p[hit], a[hit], b[hit]] = vals[hit]
+        return out
 
     def apply(self, r):
         """Return M^-1 r = sum_i V_i^T W_i K_i^-1 V_i r, summing each DoF's

@@ -1,0 +1,304 @@
+"""Python binding of libstokes_dcamg.so (include/stokes_dcamg.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+The functions carry the C names (``stokes_setup``, ``stokes_factor_patches``,
+``stokes_vcycle``, ``stokes_fgmres_solve`` ...); device vectors are passed as
+torch CUDA tensors (FP64, contiguous), problems as objects with the fields
+of ``stokes_problem`` (see ``problems.stokes.Problem``).  Importing this
+module loads the library and raises if it is missing: there is no CPU path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB, build as _build
+
+# ---------------------------------------------------------------- constants
+STOKES_OK = 0
+STOKES_NOT_CONVERGED = 1
+STOKES_ERR_INVALID_ARG = -1
+STOKES_ERR_CUDA = -2
+STOKES_ERR_OOM = -3
+STOKES_ERR_SINGULAR_PATCH = -4
+STOKES_ERR_NAN = -5
+STOKES_ERR_STATE = -6
+STOKES_TH, STOKES_SV = 0, 1
+STOKES_DC_ALL, STOKES_DC_SKIP1, STOKES_DC_SKIP0 = 0, 1, 2
+STOKES_RELAX_VANKA, STOKES_RELAX_DLSC = 0, 1
+STOKES_FP32, STOKES_FP64 = 0, 1
+(STOKES_OP_SPMV, STOKES_OP_SPMV_F64, STOKES_OP_RESIDUAL, STOKES_OP_RESTRICT,
+ STOKES_OP_PROLONG, STOKES_OP_VANKA, STOKES_OP_RELAX, STOKES_OP_COARSE) = range(8)
+
+EXPORTS = ["stokes_setup", "stokes_factor_patches", "stokes_vcycle", "stokes_fgmres_solve",
+           "stokes_fgmres_solve_host", "stokes_level_op", "stokes_num_levels", "stokes_level_size",
+           "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_destroy",
+           "stokes_status_string", "stokes_last_error"]
+
+
+# ---------------------------------------------------------------- structs
+class stokes_csr(C.Structure):
+    _fields_ = [("nrows", C.c_int32), ("ncols", C.c_int32), ("nnz", C.c_int64),
+                ("rowptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
+                ("val", C.POINTER(C.c_double))]
+
+
+class stokes_patches(C.Structure):
+    _fields_ = [("npatch", C.c_int32), ("ptr", C.POINTER(C.c_int64)), ("dof", C.POINTER(C.c_int32)),
+                ("nvel", C.POINTER(C.c_int32)), ("npres", C.POINTER(C.c_int32))]
+
+
+class stokes_problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("disc", C.c_int32), ("nlevels", C.c_int32),
+                ("field_off", C.POINTER(C.c_int64)), ("K", C.POINTER(stokes_csr)),
+                ("P", C.POINTER(stokes_csr)), ("patches", C.POINTER(stokes_patches)),
+                ("coarse_null", C.POINTER(C.c_double)), ("dirichlet", C.POINTER(C.c_uint8)),
+                ("R0p", C.POINTER(stokes_csr)), ("Mcg", C.POINTER(stokes_csr)),
+                ("mcg_lo", C.c_double), ("mcg_hi", C.c_double),
+                ("lambda_A", C.POINTER(C.c_double)), ("lambda_S", C.POINTER(C.c_double))]
+
+
+class stokes_params(C.Structure):
+    _fields_ = [("schedule", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
+                ("eta_u", C.c_double), ("eta_p", C.c_double), ("omega", C.POINTER(C.c_double)),
+                ("relax", C.POINTER(C.c_int32)), ("cheb_deg", C.c_int32 * 3), ("dlsc_sweeps", C.c_int32),
+                ("mcg_deg", C.c_int32), ("precision", C.c_int32)]
+
+
+class stokes_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("true_relres", C.c_double)]
+
+
+# ---------------------------------------------------------------- loading
+def _load():
+    if not os.path.exists(LIB):
+        raise ImportError(f"libstokes_dcamg.so is not built ({LIB}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB)
+    vp = C.c_void_p
+    lib.stokes_setup.argtypes = [C.POINTER(C.POINTER(stokes_problem)), C.c_int32, C.POINTER(stokes_params), vp,
+                                 C.POINTER(vp)]
+    lib.stokes_factor_patches.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.stokes_vcycle.argtypes = [vp, vp, vp]
+    lib.stokes_fgmres_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32, C.POINTER(stokes_solve_info)]
+    lib.stokes_fgmres_solve_host.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32,
+                                             C.POINTER(stokes_solve_info)]
+    lib.stokes_level_op.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, vp]
+    lib.stokes_num_levels.argtypes = [vp]
+    lib.stokes_level_size.argtypes = [vp, C.c_int32]
+    lib.stokes_level_size.restype = C.c_int64
+    lib.stokes_cycle_bytes.argtypes = [vp]
+    lib.stokes_cycle_bytes.restype = C.c_double
+    lib.stokes_sweep_factor_bytes.argtypes = [vp, C.c_int32]
+    lib.stokes_sweep_factor_bytes.restype = C.c_double
+    lib.stokes_destroy.argtypes = [vp]
+    lib.stokes_destroy.restype = None
+    lib.stokes_status_string.argtypes = [C.c_int]
+    lib.stokes_status_string.restype = C.c_char_p
+    lib.stokes_last_error.argtypes = []
+    lib.stokes_last_error.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib.stokes_last_error().decode()
+        super().__init__(f"{where}: {lib.stokes_status_string(code).decode()} ({code}): {msg}")
+        self.code = code
+
+
+def _check(code, where, allow_not_converged=False):
+    if code < 0 or (code > 0 and not allow_not_converged):
+        raise StokesError(code, where)
+    return code
+
+
+# ---------------------------------------------------------------- marshalling
+def _p(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class _Keep:
+    """Holds numpy arrays alive while the C structs point at them."""
+
+    def __init__(self):
+        self.refs = []
+
+    def arr(self, a, dtype):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        self.refs.append(a)
+        return a
+
+
+def _csr(keep, m):
+    m = m.tocsr()
+    m.sort_indices()
+    rp = keep.arr(m.indptr, np.int64)
+    ci = keep.arr(m.indices, np.int32)
+    v = keep.arr(m.data, np.float64)
+    return stokes_csr(m.shape[0], m.shape[1], m.nnz, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double))
+
+
+def _problem(keep, pr):
+    L = len(pr.K)
+    Ks = (stokes_csr * L)(*[_csr(keep, k) for k in pr.K])
+    Ps = (stokes_csr * (L - 1))(*[_csr(keep, p) for p in pr.P[: L - 1]])
+    pas = []
+    for pa in pr.patches[: L - 1]:
+        ptr = keep.arr(pa.ptr, np.int64)
+        dof = keep.arr(pa.dof, np.int32)
+        nv = keep.arr(np.asarray(pa.nvel).reshape(-1), np.int32)
+        npr = keep.arr(pa.npres, np.int32)
+        pas.append(stokes_patches(pa.ptr.size - 1, _p(ptr, C.c_int64), _p(dof, C.c_int32), _p(nv, C.c_int32),
+                                  _p(npr, C.c_int32)))
+    Pa = (stokes_patches * (L - 1))(*pas)
+    keep.refs += [Ks, Ps, Pa]
+    fo = keep.arr(np.concatenate([np.asarray(o, dtype=np.int64) for o in pr.field_off]), np.int64)
+    cn = keep.arr(pr.coarse_null, np.float64)
+    dr = keep.arr(pr.dirichlet.astype(np.uint8), np.uint8)
+    p = stokes_problem()
+    p.dim, p.disc, p.nlevels = pr.dim, pr.disc, L
+    p.field_off = _p(fo, C.c_int64)
+    p.K = C.cast(Ks, C.POINTER(stokes_csr))
+    p.P = C.cast(Ps, C.POINTER(stokes_csr))
+    p.patches = C.cast(Pa, C.POINTER(stokes_patches))
+    p.coarse_null = _p(cn, C.c_double)
+    p.dirichlet = _p(dr, C.c_uint8)
+    if getattr(pr, "R0p", None) is not None:
+        r0 = _csr(keep, pr.R0p)
+        mc = _csr(keep, pr.Mcg)
+        keep.refs += [r0, mc]
+        p.R0p = C.pointer(r0)
+        p.Mcg = C.pointer(mc)
+        p.mcg_lo, p.mcg_hi = pr.mcg_bounds
+    if getattr(pr, "lambda_A", None) is not None:
+        la = keep.arr(pr.lambda_A, np.float64)
+        ls = keep.arr(pr.lambda_S, np.float64)
+        p.lambda_A = _p(la, C.c_double)
+        p.lambda_S = _p(ls, C.c_double)
+    return p
+
+
+def _params(keep, prm, nlevels):
+    """prm: dict with schedule, nu1, nu2, eta_u, eta_p, omega (scalar or per
+    level; omega0 overrides level 0), relax (list or None), cheb_deg,
+    dlsc_sweeps, mcg_deg, precision."""
+    s = stokes_params()
+    s.schedule = int(prm.get("schedule", 0))
+    s.nu1 = int(prm.get("nu1", 1))
+    s.nu2 = int(prm.get("nu2", 1))
+    s.eta_u = float(prm.get("eta_u", 1.0))
+    s.eta_p = float(prm.get("eta_p", 1.0))
+    om = prm.get("omega", 1.0)
+    om = np.full(max(nlevels - 1, 1), float(om)) if np.isscalar(om) else np.asarray(om, dtype=np.float64)
+    if "omega0" in prm:
+        om = om.copy()
+        om[0] = prm["omega0"]
+    om = keep.arr(om, np.float64)
+    s.omega = _p(om, C.c_double)
+    if prm.get("relax") is not None:
+        rl = keep.arr(prm["relax"], np.int32)
+        s.relax = _p(rl, C.c_int32)
+    cd = prm.get("cheb_deg", (3, 3, 6))
+    s.cheb_deg[0], s.cheb_deg[1], s.cheb_deg[2] = (int(v) for v in cd)
+    s.dlsc_sweeps = int(prm.get("dlsc_sweeps", 2))
+    s.mcg_deg = int(prm.get("mcg_deg", 32))
+    s.precision = int(prm.get("precision", STOKES_FP32))
+    return s
+
+
+# ---------------------------------------------------------------- API
+def _dptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device FP64 contiguous tensor expected"
+    return C.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """Owns a stokes_handle; closed by ``stokes_destroy`` or garbage collection."""
+
+    def __init__(self, ptr, ninst):
+        self.ptr = ptr
+        self.ninst = ninst
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            stokes_destroy(self)
+
+
+def stokes_setup(problems, params, stream=None):
+    """Build a handle for one problem or a list of problems (batched)."""
+    if not isinstance(problems, (list, tuple)):
+        problems = [problems]
+    keep = _Keep()
+    cps = [_problem(keep, pr) for pr in problems]
+    arr = (C.POINTER(stokes_problem) * len(cps))(*[C.pointer(p) for p in cps])
+    nl = max(len(pr.K) for pr in problems)
+    prm = _params(keep, params, nl)
+    out = C.c_void_p()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib.stokes_setup(arr, len(cps), C.byref(prm), C.c_void_p(stream), C.byref(out)), "stokes_setup")
+    return Handle(out, len(cps))
+
+
+def stokes_factor_patches(h):
+    ns = C.c_int64(0)
+    _check(lib.stokes_factor_patches(h.ptr, C.byref(ns)), "stokes_factor_patches")
+    return ns.value
+
+
+def stokes_vcycle(h, r, z):
+    _check(lib.stokes_vcycle(h.ptr, _dptr(r), _dptr(z)), "stokes_vcycle")
+
+
+def stokes_fgmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=1000):
+    info = (stokes_solve_info * h.ninst)()
+    rc = _check(lib.stokes_fgmres_solve(h.ptr, _dptr(b), _dptr(x), rtol, restart, maxit, info),
+                "stokes_fgmres_solve", allow_not_converged=True)
+    return rc, [(i.iters, i.status, i.true_relres) for i in info]
+
+
+def stokes_fgmres_solve_host(h, b, x, rtol=1e-8, restart=30, maxit=1000):
+    """b, x: numpy FP64 arrays in host memory (x: initial guess in, solution out)."""
+    assert b.dtype == np.float64 and x.dtype == np.float64 and x.flags.c_contiguous
+    info = (stokes_solve_info * h.ninst)()
+    rc = _check(lib.stokes_fgmres_solve_host(h.ptr, C.c_void_p(b.ctypes.data), C.c_void_p(x.ctypes.data), rtol,
+                                             restart, maxit, info),
+                "stokes_fgmres_solve_host", allow_not_converged=True)
+    return rc, [(i.iters, i.status, i.true_relres) for i in info]
+
+
+def stokes_level_op(h, op, level, x, b, y):
+    _check(lib.stokes_level_op(h.ptr, op, level, _dptr(x), _dptr(b), _dptr(y)), "stokes_level_op")
+
+
+def stokes_num_levels(h):
+    return lib.stokes_num_levels(h.ptr)
+
+
+def stokes_level_size(h, level):
+    return lib.stokes_level_size(h.ptr, level)
+
+
+def stokes_cycle_bytes(h):
+    return lib.stokes_cycle_bytes(h.ptr)
+
+
+def stokes_sweep_factor_bytes(h, level):
+    return lib.stokes_sweep_factor_bytes(h.ptr, level)
+
+
+def stokes_destroy(h):
+    if h.ptr:
+        lib.stokes_destroy(h.ptr)
+        h.ptr = None
+
+
+def build():
+    """Compile libstokes_dcamg.so for sm_103a (in-tree)."""
+    return _build()

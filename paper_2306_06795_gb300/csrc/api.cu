@@ -1,0 +1,1202 @@
+// Host orchestration of the solve phase behind the C ABI of
+// include/stokes_dcamg.h: device setup of the hierarchy, batched patch
+// factorisation, the defect-correction cycle (Eq. TG-operator-full around
+// the Galerkin V-cycle of Eq. TG-operator), its CUDA-graph capture, and
+// FP64 flexible GMRES with per-instance scalars (Sec. 4).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "stokes_dcamg.h"
+
+using namespace sd;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                       \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess)                                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA,                  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                 \
+  } while (0)
+
+#define TRY(call)                \
+  do {                           \
+    int rc_ = (call);            \
+    if (rc_ != STOKES_OK) return rc_; \
+  } while (0)
+
+namespace {
+
+struct HostCSR {
+  int nrows = 0, ncols = 0;
+  std::vector<int> rowptr{0};
+  std::vector<int> col;
+  std::vector<double> val;
+};
+
+struct CoarseSet {
+  int nblocks = 0, max_n = 0;
+  int* boff = nullptr;
+  int* bn = nullptr;
+  int64_t* koff = nullptr;
+  double* Kinv = nullptr;
+  int64_t kinv_elems = 0;
+};
+
+struct Level {
+  int64_t n = 0;
+  DevCSR K;
+  bool hasP = false, Pident = false;
+  DevCSR P, R;
+  bool has_patches = false;
+  DevPatches pat;
+  double omega = 1.0;
+  int relax = STOKES_RELAX_VANKA;
+  void* x = nullptr;
+  void* b = nullptr;
+  void* r = nullptr;
+  void* yp = nullptr;
+  void* ta = nullptr;  // scratch for stokes_level_op
+  void* tb = nullptr;
+  CoarseSet coarse;
+  std::vector<int64_t> seg_off;  // per instance, -1 when absent
+};
+
+struct Ledger {
+  bool count = false;
+  double bytes = 0.0;
+  int launches = 0;
+};
+
+}  // namespace
+
+struct stokes_handle {
+  int ninst = 0, dim = 2, disc = STOKES_TH, prec = STOKES_FP32, L = 0;
+  int schedule = 0, nu1 = 1, nu2 = 1;
+  double eta_u = 1.0, eta_p = 1.0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;     // created here: joined with the legacy default stream per call
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<Level> lv;
+  std::vector<int> inst_levels;
+  uint8_t* kind0 = nullptr;  // level 0: 0 velocity, 1 pressure, 2 Dirichlet
+  uint8_t* dir0 = nullptr;   // level 0: 1 on Dirichlet rows
+  bool factored = false;
+  Ledger led;
+  std::map<std::pair<const void*, void*>, cudaGraphExec_t> graphs;
+  // FGMRES storage
+  int krylov_m = 0;
+  double* V = nullptr;
+  double* Z = nullptr;
+  double* w = nullptr;
+  double* partial = nullptr;
+  double* hd = nullptr;   // device h: [ninst][ldh]
+  double* yd = nullptr;   // device coefficients [ninst][ldh]
+  int* actd = nullptr;
+  int ldh = 0, ldp = 0;
+  int nchunks = 0;
+  int64_t* cbeg = nullptr;
+  int64_t* cend = nullptr;
+  int* cseg = nullptr;
+  int* sc_beg = nullptr;
+  int* sc_end = nullptr;
+  std::vector<int> h_sc_beg, h_sc_end;
+  void* flush = nullptr;
+  size_t flush_bytes = 0;
+  std::vector<void*> allocs;
+};
+
+// ------------------------------------------------------------- utilities
+namespace {
+
+template <typename T>
+int dalloc(stokes_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return STOKES_OK;
+}
+
+template <typename T>
+int upload(stokes_handle* h, T** p, const std::vector<T>& v) {
+  TRY(dalloc(h, p, v.size()));
+  if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return STOKES_OK;
+}
+
+int choose_tpr(int64_t nnz, int nrows) {
+  const double mean = nrows ? double(nnz) / nrows : 0.0;
+  if (mean <= 3) return 2;
+  if (mean <= 6) return 4;
+  if (mean <= 12) return 8;
+  if (mean <= 24) return 16;
+  return 32;
+}
+
+int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
+  d.nrows = c.nrows;
+  d.ncols = c.ncols;
+  d.nnz = (int64_t)c.col.size();
+  TRY(upload(h, &d.rowptr, c.rowptr));
+  TRY(upload(h, &d.col, c.col));
+  TRY(upload(h, &d.v64, c.val));
+  if (h->prec == STOKES_FP32) {
+    std::vector<float> v32(c.val.begin(), c.val.end());
+    TRY(upload(h, &d.v32, v32));
+  }
+  d.tpr = choose_tpr(d.nnz, d.nrows);
+  return STOKES_OK;
+}
+
+int check_csr(const stokes_csr* c, const char* what) {
+  if (!c || c->nrows < 0 || c->ncols < 0 || c->nnz < 0 || (c->nnz > 0 && (!c->col || !c->val)) || !c->rowptr)
+    return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": null or negative CSR fields");
+  if (c->nnz >= (int64_t(1) << 31)) return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": nnz >= 2^31");
+  if (c->rowptr[0] != 0 || c->rowptr[c->nrows] != c->nnz)
+    return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": rowptr does not span nnz");
+  for (int i = 0; i < c->nrows; ++i) {
+    if (c->rowptr[i + 1] < c->rowptr[i]) return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": rowptr decreases");
+    for (int64_t k = c->rowptr[i]; k < c->rowptr[i + 1]; ++k) {
+      if (c->col[k] < 0 || c->col[k] >= c->ncols)
+        return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": column index out of range");
+      if (k > c->rowptr[i] && c->col[k] <= c->col[k - 1])
+        return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": columns not sorted/unique");
+      if (!std::isfinite(c->val[k])) return fail(STOKES_ERR_NAN, std::string(what) + ": non-finite value");
+    }
+  }
+  return STOKES_OK;
+}
+
+// Append block (c) at (r0, c0) of the block-diagonal concatenation.
+void append_block(HostCSR& out, const stokes_csr* c, int64_t c0) {
+  for (int i = 0; i < c->nrows; ++i) {
+    for (int64_t k = c->rowptr[i]; k < c->rowptr[i + 1]; ++k) {
+      out.col.push_back((int)(c0 + c->col[k]));
+      out.val.push_back(c->val[k]);
+    }
+    out.rowptr.push_back((int)out.col.size());
+  }
+}
+void append_zero_rows(HostCSR& out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) out.rowptr.push_back((int)out.col.size());
+}
+
+HostCSR transpose(const HostCSR& a) {
+  HostCSR t;
+  t.nrows = a.ncols;
+  t.ncols = a.nrows;
+  t.rowptr.assign(a.ncols + 1, 0);
+  for (int c : a.col) t.rowptr[c + 1]++;
+  for (int i = 0; i < a.ncols; ++i) t.rowptr[i + 1] += t.rowptr[i];
+  t.col.resize(a.col.size());
+  t.val.resize(a.val.size());
+  std::vector<int> pos(t.rowptr.begin(), t.rowptr.end() - 1);
+  for (int i = 0; i < a.nrows; ++i)
+    for (int k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k) {
+      const int p = pos[a.col[k]]++;
+      t.col[p] = i;
+      t.val[p] = a.val[k];
+    }
+  return t;
+}
+
+bool is_identity(const stokes_csr* c) {
+  if (c->nrows != c->ncols || c->nnz != c->nrows) return false;
+  for (int i = 0; i < c->nrows; ++i)
+    if (c->rowptr[i] != i || c->col[i] != i || c->val[i] != 1.0) return false;
+  return true;
+}
+
+// Is K's velocity block of every component equal to component 0's (same
+// pattern and values, shifted), so that patch blocks can be shared?
+bool components_share_block(const stokes_csr* K, const int64_t* off, int dim) {
+  const int64_t n0 = off[1] - off[0];
+  for (int c = 1; c < dim; ++c) {
+    if (off[c + 1] - off[c] != n0) return false;
+    for (int64_t i = 0; i < n0; ++i) {
+      const int64_t r0 = off[0] + i, rc = off[c] + i;
+      // entries of each row inside its own component's column range
+      std::vector<std::pair<int64_t, double>> a, b;
+      for (int64_t k = K->rowptr[r0]; k < K->rowptr[r0 + 1]; ++k)
+        if (K->col[k] >= off[0] && K->col[k] < off[1]) a.push_back({K->col[k] - off[0], K->val[k]});
+      for (int64_t k = K->rowptr[rc]; k < K->rowptr[rc + 1]; ++k)
+        if (K->col[k] >= off[c] && K->col[k] < off[c + 1]) b.push_back({K->col[k] - off[c], K->val[k]});
+      if (a != b) return false;
+    }
+  }
+  return true;
+}
+
+// Dense inverse of the bordered coarsest matrix [K n; n^T 0] by LU with
+// partial pivoting (FP64); returns the leading n x n block row-major.
+int bordered_inverse(const stokes_csr* K, const double* nullv, std::vector<double>& out) {
+  const int n = K->nrows, nb = n + 1;
+  std::vector<double> M((size_t)nb * nb, 0.0), I((size_t)nb * nb, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int64_t k = K->rowptr[i]; k < K->rowptr[i + 1]; ++k) M[(size_t)i * nb + K->col[k]] = K->val[k];
+  for (int i = 0; i < n; ++i) {
+    M[(size_t)i * nb + n] = nullv[i];
+    M[(size_t)n * nb + i] = nullv[i];
+  }
+  for (int i = 0; i < nb; ++i) I[(size_t)i * nb + i] = 1.0;
+  double amax = 0.0;
+  for (double v : M) amax = std::max(amax, std::fabs(v));
+  for (int k = 0; k < nb; ++k) {
+    int p = k;
+    for (int i = k + 1; i < nb; ++i)
+      if (std::fabs(M[(size_t)i * nb + k]) > std::fabs(M[(size_t)p * nb + k])) p = i;
+    if (!(std::fabs(M[(size_t)p * nb + k]) > 1e-14 * amax))
+      return fail(STOKES_ERR_SINGULAR_PATCH, "coarsest bordered matrix is singular");
+    if (p != k)
+      for (int j = 0; j < nb; ++j) {
+        std::swap(M[(size_t)k * nb + j], M[(size_t)p * nb + j]);
+        std::swap(I[(size_t)k * nb + j], I[(size_t)p * nb + j]);
+      }
+    const double piv = M[(size_t)k * nb + k];
+    for (int i = k + 1; i < nb; ++i) {
+      const double f = M[(size_t)i * nb + k] / piv;
+      if (f == 0.0) continue;
+      for (int j = k; j < nb; ++j) M[(size_t)i * nb + j] -= f * M[(size_t)k * nb + j];
+      for (int j = 0; j < nb; ++j) I[(size_t)i * nb + j] -= f * I[(size_t)k * nb + j];
+    }
+  }
+  // back substitution for every column of the inverse
+  for (int k = nb - 1; k >= 0; --k) {
+    const double piv = M[(size_t)k * nb + k];
+    for (int j = 0; j < nb; ++j) {
+      double s = I[(size_t)k * nb + j];
+      for (int i = k + 1; i < nb; ++i) s -= M[(size_t)k * nb + i] * I[(size_t)i * nb + j];
+      I[(size_t)k * nb + j] = s / piv;
+    }
+  }
+  out.resize((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) out[(size_t)i * n + j] = I[(size_t)i * nb + j];
+  return STOKES_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- ledger
+namespace {
+
+inline size_t esz(const stokes_handle* h) { return h->prec == STOKES_FP32 ? 4 : 8; }
+
+template <typename T>
+const T* kval(const DevCSR& A);
+template <>
+const float* kval<float>(const DevCSR& A) { return A.v32; }
+template <>
+const double* kval<double>(const DevCSR& A) { return A.v64; }
+
+// bytes of one SpMV: values + columns + row pointers + x gathered once per
+// column + b read (residual modes) + y written (read too when adding)
+double spmv_bytes(const DevCSR& A, size_t sv, size_t sx, size_t sb, size_t sy, int mode) {
+  double b = double(A.nnz) * (sv + 4) + 4.0 * (A.nrows + 1) + double(A.ncols) * sx + double(A.nrows) * sy;
+  if (mode == SPMV_RES || mode == SPMV_SCALED_RES) b += double(A.nrows) * sb;
+  if (mode == SPMV_ADD) b += double(A.nrows) * sy;
+  if (mode == SPMV_SCALED_RES) b += double(A.nrows);  // row kinds
+  return b;
+}
+
+template <typename TA, typename TX, typename TB, typename TY, typename TACC>
+int L_spmv(stokes_handle* h, const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y, int mode,
+           double s0 = 0, double s1 = 0, const uint8_t* kind = nullptr) {
+  if (h->led.count) {
+    h->led.bytes += spmv_bytes(A, sizeof(TA), sizeof(TX), sizeof(TB), sizeof(TY), mode);
+    h->led.launches += A.nrows > 0;
+    return STOKES_OK;
+  }
+  CK((spmv<TA, TX, TB, TY, TACC>(A, val, x, b, y, mode, s0, s1, kind, h->st)));
+  return STOKES_OK;
+}
+
+template <typename T, typename TR>
+int L_apply(stokes_handle* h, const Level& lv, const TR* r, T* yp) {
+  const DevPatches& p = lv.pat;
+  if (h->led.count) {
+    // factors + patch index lists + per-patch metadata + gathered r + patch-major output
+    h->led.bytes += double(p.fac_elems) * sizeof(T) + double(p.nslots) * (4 + sizeof(TR) + sizeof(T)) +
+                    double(p.npatch) * (4 + 4 + 4 + 8 + 4);
+    h->led.launches += (p.nsmall > 0) + (p.nlarge > 0);
+    return STOKES_OK;
+  }
+  CK((vanka_apply<T, TR>(p, r, yp, h->st)));
+  return STOKES_OK;
+}
+
+template <typename T>
+int L_scatter(stokes_handle* h, const Level& lv, const T* yp, T* x, double omega, int mode,
+              const double* r64 = nullptr, double* out64 = nullptr) {
+  const DevPatches& p = lv.pat;
+  if (h->led.count) {
+    double b = 4.0 * (lv.n + 1) + double(p.nslots) * (4 + sizeof(T));
+    if (mode == 0) b += double(lv.n) * sizeof(T);
+    else if (mode == 1) b += 2.0 * lv.n * sizeof(T);
+    else b += double(lv.n) * (sizeof(T) + 1 + 8);
+    h->led.bytes += b;
+    h->led.launches += 1;
+    return STOKES_OK;
+  }
+  CK(vanka_scatter<T>(p, lv.n, yp, x, omega, mode, h->dir0, r64, out64, h->st));
+  return STOKES_OK;
+}
+
+template <typename TI, typename TO>
+int L_cast(stokes_handle* h, int64_t n, const TI* in, TO* out) {
+  if (h->led.count) {
+    h->led.bytes += double(n) * (sizeof(TI) + sizeof(TO));
+    h->led.launches += n > 0;
+    return STOKES_OK;
+  }
+  CK((cast_copy<TI, TO>(n, in, out, h->st)));
+  return STOKES_OK;
+}
+
+template <typename T, typename TI>
+int L_axpy(stokes_handle* h, int64_t n, double a, const TI* x, T* y) {
+  if (h->led.count) {
+    h->led.bytes += double(n) * (sizeof(TI) + 2 * sizeof(T));
+    h->led.launches += n > 0;
+    return STOKES_OK;
+  }
+  CK((axpy_into<T, TI>(n, a, x, y, h->st)));
+  return STOKES_OK;
+}
+
+template <typename T>
+int L_zero(stokes_handle* h, int64_t n, T* y) {
+  if (h->led.count) {
+    h->led.bytes += double(n) * sizeof(T);
+    h->led.launches += n > 0;
+    return STOKES_OK;
+  }
+  CK(fill_zero<T>(n, y, h->st));
+  return STOKES_OK;
+}
+
+template <typename T>
+int L_finalize(stokes_handle* h, int64_t n, const T* x, const double* r64, double* out) {
+  if (h->led.count) {
+    h->led.bytes += double(n) * (sizeof(T) + 1 + 8);
+    h->led.launches += n > 0;
+    return STOKES_OK;
+  }
+  CK(finalize_out<T>(n, x, h->dir0, r64, out, h->st));
+  return STOKES_OK;
+}
+
+template <typename T>
+int L_coarse(stokes_handle* h, const Level& lv, const T* b, T* y) {
+  const CoarseSet& c = lv.coarse;
+  if (c.nblocks == 0) return STOKES_OK;
+  if (h->led.count) {
+    h->led.bytes += double(c.kinv_elems) * 8.0 + 2.0 * sizeof(T) * std::sqrt(double(c.kinv_elems));
+    h->led.launches += 1;
+    return STOKES_OK;
+  }
+  CK(coarse_solve<T>(c.nblocks, c.boff, c.bn, c.koff, c.Kinv, c.max_n, b, y, h->st));
+  return STOKES_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- the cycle
+namespace {
+
+// nsweeps sweeps of x <- x + omega M^-1 (b - K x) (Eq. vanka); the first
+// sweep from a zero guess needs no residual (r = b).  When out64 is given,
+// the last scatter writes the level-0 output (Dirichlet rows take r64).
+template <typename T>
+int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_guess, const double* r64 = nullptr,
+          double* out64 = nullptr) {
+  Level& L = h->lv[l];
+  if (L.relax != STOKES_RELAX_VANKA) return fail(STOKES_ERR_INVALID_ARG, "DLSC relaxation is not available");
+  T* r = reinterpret_cast<T*>(L.r);
+  T* yp = reinterpret_cast<T*>(L.yp);
+  if (nsweeps == 0 && zero_guess) TRY(L_zero<T>(h, L.n, x));
+  for (int s = 0; s < nsweeps; ++s) {
+    const bool last_out = out64 && s == nsweeps - 1;
+    if (s == 0 && zero_guess) {
+      TRY((L_apply<T, T>(h, L, b, yp)));
+      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 0, r64, out64));
+    } else {
+      TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
+      TRY((L_apply<T, T>(h, L, r, yp)));
+      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 1, r64, out64));
+    }
+  }
+  return STOKES_OK;
+}
+
+// Galerkin V-cycle on level l >= 1 (Eq. TG-operator), zero initial guess:
+// input lv[l].b, output lv[l].x.  Instances whose coarsest level is l take
+// the exact bordered solve on their segment.
+template <typename T>
+int vcycle(stokes_handle* h, int l) {
+  Level& L = h->lv[l];
+  T* x = reinterpret_cast<T*>(L.x);
+  T* b = reinterpret_cast<T*>(L.b);
+  if (l == h->L - 1) return L_coarse<T>(h, L, b, x);
+  const bool relax_here = L.has_patches && !(h->schedule == STOKES_DC_SKIP1 && l == 1);
+  if (relax_here) TRY(relax<T>(h, l, x, b, h->nu1, true));
+  else TRY(L_zero<T>(h, L.n, x));
+  TRY(L_coarse<T>(h, L, b, x));
+  T* r = reinterpret_cast<T*>(L.r);
+  Level& C = h->lv[l + 1];
+  TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
+  TRY((L_spmv<T, T, T, T, T>(h, L.R, kval<T>(L.R), r, (const T*)nullptr, reinterpret_cast<T*>(C.b), SPMV_SET)));
+  TRY(vcycle<T>(h, l + 1));
+  TRY((L_spmv<T, T, T, T, T>(h, L.P, kval<T>(L.P), reinterpret_cast<const T*>(C.x), (const T*)nullptr, x, SPMV_ADD)));
+  if (relax_here) TRY(relax<T>(h, l, x, b, h->nu2, false));
+  return STOKES_OK;
+}
+
+// z = M_dc^-1 r (Eq. TG-operator-full, gamma = 1), zero initial guess.
+template <typename T>
+int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
+  Level& L0 = h->lv[0];
+  Level& L1 = h->lv[1];
+  T* x0 = reinterpret_cast<T*>(L0.x);
+  const T* r0;
+  if (sizeof(T) == 8) {
+    r0 = reinterpret_cast<const T*>(r64);
+  } else {
+    TRY((L_cast<double, T>(h, L0.n, r64, reinterpret_cast<T*>(L0.b))));
+    r0 = reinterpret_cast<const T*>(L0.b);
+  }
+  const bool skip0 = h->schedule == STOKES_DC_SKIP0 || !L0.has_patches;
+  if (!skip0) TRY(relax<T>(h, 0, x0, r0, h->nu1, true));
+  else TRY(L_zero<T>(h, L0.n, x0));
+  // DC residual in FP64: d = eta (r - K0 x); R0 = injection for TH
+  if (h->disc != STOKES_TH) return fail(STOKES_ERR_INVALID_ARG, "Scott-Vogelius transfers are not available");
+  TRY((L_spmv<double, T, double, T, double>(h, L0.K, L0.K.v64, x0, r64, reinterpret_cast<T*>(L1.b),
+                                            SPMV_SCALED_RES, h->eta_u, h->eta_p, h->kind0)));
+  TRY(vcycle<T>(h, 1));
+  TRY((L_axpy<T, T>(h, L0.n, 1.0, reinterpret_cast<const T*>(L1.x), x0)));  // P0 = I
+  if (!skip0 && h->nu2 > 0) TRY(relax<T>(h, 0, x0, r0, h->nu2, false, r64, z64));
+  else TRY(L_finalize<T>(h, L0.n, x0, r64, z64));
+  return STOKES_OK;
+}
+
+int run_cycle(stokes_handle* h, const double* r, double* z) {
+  return h->prec == STOKES_FP32 ? dc_cycle<float>(h, r, z) : dc_cycle<double>(h, r, z);
+}
+
+int cycle_graph(stokes_handle* h, const double* r, double* z, cudaGraphExec_t* out) {
+  auto key = std::make_pair((const void*)r, (void*)z);
+  auto it = h->graphs.find(key);
+  if (it != h->graphs.end()) {
+    *out = it->second;
+    return STOKES_OK;
+  }
+  // one plain run first (sets kernel attributes outside capture)
+  TRY(run_cycle(h, r, z));
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+  int rc = run_cycle(h, r, z);
+  cudaError_t ec = cudaStreamEndCapture(h->st, &g);
+  if (rc != STOKES_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  CK(ec);
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  CK(ei);
+  h->graphs[key] = ge;
+  *out = ge;
+  return STOKES_OK;
+}
+
+}  // namespace
+
+// With no caller stream, the handle's own stream is ordered after the work
+// already queued on the legacy default stream and before the work queued
+// there later, as if the calls ran on the default stream.
+namespace {
+int join_in(stokes_handle* h) {
+  if (!h->own_stream) return STOKES_OK;
+  CK(cudaEventRecord(h->ev_in, cudaStreamLegacy));
+  CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
+  return STOKES_OK;
+}
+int join_out(stokes_handle* h) {
+  if (!h->own_stream) return STOKES_OK;
+  CK(cudaEventRecord(h->ev_out, h->st));
+  CK(cudaStreamWaitEvent(cudaStreamLegacy, h->ev_out, 0));
+  return STOKES_OK;
+}
+}  // namespace
+
+// ------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* stokes_last_error(void) { return g_err.c_str(); }
+
+const char* stokes_status_string(int s) {
+  switch (s) {
+    case STOKES_OK: return "ok";
+    case STOKES_NOT_CONVERGED: return "not converged";
+    case STOKES_ERR_INVALID_ARG: return "invalid argument";
+    case STOKES_ERR_CUDA: return "CUDA error";
+    case STOKES_ERR_OOM: return "out of device memory";
+    case STOKES_ERR_SINGULAR_PATCH: return "singular patch";
+    case STOKES_ERR_NAN: return "non-finite value";
+    case STOKES_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+void stokes_destroy(stokes_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+  delete h;
+}
+
+int stokes_num_levels(const stokes_handle* h) { return h ? h->L : 0; }
+int64_t stokes_level_size(const stokes_handle* h, int32_t l) {
+  return (h && l >= 0 && l < h->L) ? h->lv[l].n : -1;
+}
+
+static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int ninst, const stokes_params* prm) {
+  const int dim = probs[0]->dim;
+  h->dim = dim;
+  h->disc = probs[0]->disc;
+  h->prec = prm->precision;
+  h->schedule = prm->schedule;
+  h->nu1 = prm->nu1;
+  h->nu2 = prm->nu2;
+  h->eta_u = prm->eta_u;
+  h->eta_p = prm->eta_p;
+  if (h->prec != STOKES_FP32 && h->prec != STOKES_FP64) return fail(STOKES_ERR_INVALID_ARG, "precision");
+  if (prm->nu1 < 0 || prm->nu2 < 0 || prm->schedule < 0 || prm->schedule > 2)
+    return fail(STOKES_ERR_INVALID_ARG, "schedule or sweep counts");
+  if (h->disc != STOKES_TH) return fail(STOKES_ERR_INVALID_ARG, "Scott-Vogelius K0 is not available in this build");
+  int L = 0;
+  for (int k = 0; k < ninst; ++k) {
+    const stokes_problem* p = probs[k];
+    if (!p || p->dim != dim || p->disc != h->disc || p->nlevels < 2 || !p->K || !p->P || !p->patches ||
+        !p->field_off || !p->coarse_null || !p->dirichlet)
+      return fail(STOKES_ERR_INVALID_ARG, "problem " + std::to_string(k) + ": missing fields or mismatched dim/disc");
+    if (dim != 2 && dim != 3) return fail(STOKES_ERR_INVALID_ARG, "dim must be 2 or 3");
+    h->inst_levels.push_back(p->nlevels);
+    L = std::max(L, (int)p->nlevels);
+    for (int l = 0; l < p->nlevels; ++l) {
+      TRY(check_csr(&p->K[l], "K"));
+      const int64_t* off = p->field_off + (size_t)l * (dim + 2);
+      if (off[0] != 0 || off[dim + 1] != p->K[l].nrows || p->K[l].nrows != p->K[l].ncols)
+        return fail(STOKES_ERR_INVALID_ARG, "field_off/K size mismatch on level " + std::to_string(l));
+      for (int c = 0; c <= dim; ++c)
+        if (off[c + 1] < off[c]) return fail(STOKES_ERR_INVALID_ARG, "field_off decreases");
+    }
+    for (int l = 0; l + 1 < p->nlevels; ++l) {
+      TRY(check_csr(&p->P[l], "P"));
+      if (p->P[l].nrows != p->K[l].nrows || p->P[l].ncols != p->K[l + 1].nrows)
+        return fail(STOKES_ERR_INVALID_ARG, "P size mismatch on level " + std::to_string(l));
+    }
+    if (!is_identity(&p->P[0])) return fail(STOKES_ERR_INVALID_ARG, "Taylor-Hood P0 must be the identity");
+  }
+  h->L = L;
+  h->lv.resize(L);
+  std::vector<double> omega(L, 1.0);
+  std::vector<int> relaxk(L, STOKES_RELAX_VANKA);
+  for (int l = 0; l + 1 < L; ++l) {
+    if (prm->omega) omega[l] = prm->omega[l];
+    if (prm->relax) relaxk[l] = prm->relax[l];
+    if (relaxk[l] != STOKES_RELAX_VANKA) return fail(STOKES_ERR_INVALID_ARG, "DLSC relaxation is not available");
+  }
+  const size_t T = esz(h);
+  // segment offsets per level
+  for (int l = 0; l < L; ++l) {
+    Level& lv = h->lv[l];
+    lv.seg_off.assign(ninst, -1);
+    int64_t n = 0;
+    for (int k = 0; k < ninst; ++k)
+      if (probs[k]->nlevels > l) {
+        lv.seg_off[k] = n;
+        n += probs[k]->K[l].nrows;
+      }
+    lv.n = n;
+    lv.omega = omega[l];
+    lv.relax = relaxk[l];
+    if (n >= (int64_t(1) << 31)) return fail(STOKES_ERR_INVALID_ARG, "level too large for int32 indices");
+  }
+  for (int l = 0; l < L; ++l) {
+    Level& lv = h->lv[l];
+    // K_l block diagonal over instances
+    HostCSR K;
+    K.nrows = K.ncols = (int)lv.n;
+    for (int k = 0; k < ninst; ++k)
+      if (probs[k]->nlevels > l) append_block(K, &probs[k]->K[l], lv.seg_off[k]);
+    TRY(upload_csr(h, lv.K, K));
+    // P_l: level l+1 -> l (zero rows for instances ending at l)
+    if (l + 1 < L) {
+      const Level& lc = h->lv[l + 1];
+      HostCSR P;
+      P.nrows = (int)lv.n;
+      P.ncols = (int)lc.n;
+      bool ident = true;
+      for (int k = 0; k < ninst; ++k) {
+        if (probs[k]->nlevels <= l) continue;
+        if (probs[k]->nlevels > l + 1) {
+          append_block(P, &probs[k]->P[l], lc.seg_off[k]);
+          ident = ident && is_identity(&probs[k]->P[l]);
+        } else {
+          append_zero_rows(P, probs[k]->K[l].nrows);
+          ident = false;
+        }
+      }
+      lv.hasP = true;
+      lv.Pident = ident && l == 0;
+      TRY(upload_csr(h, lv.P, P));
+      TRY(upload_csr(h, lv.R, transpose(P)));
+    }
+    // coarsest blocks of the instances ending at l
+    std::vector<int> boff, bn;
+    std::vector<int64_t> koff;
+    std::vector<double> kinv;
+    for (int k = 0; k < ninst; ++k) {
+      if (probs[k]->nlevels != l + 1) continue;
+      std::vector<double> inv;
+      TRY(bordered_inverse(&probs[k]->K[l], probs[k]->coarse_null, inv));
+      boff.push_back((int)lv.seg_off[k]);
+      bn.push_back(probs[k]->K[l].nrows);
+      koff.push_back((int64_t)kinv.size());
+      kinv.insert(kinv.end(), inv.begin(), inv.end());
+      lv.coarse.max_n = std::max(lv.coarse.max_n, probs[k]->K[l].nrows);
+    }
+    lv.coarse.nblocks = (int)boff.size();
+    if (lv.coarse.nblocks) {
+      TRY(upload(h, &lv.coarse.boff, boff));
+      TRY(upload(h, &lv.coarse.bn, bn));
+      TRY(upload(h, &lv.coarse.koff, koff));
+      TRY(upload(h, &lv.coarse.Kinv, kinv));
+      lv.coarse.kinv_elems = (int64_t)kinv.size();
+    }
+    // Vanka patches of the instances relaxing on l
+    std::vector<int> pptr{0}, pdof, pnv, pnp, small, large;
+    std::vector<int64_t> foff;
+    int64_t fac = 0;
+    bool shared = true;
+    int max_m = 0, max_np = 0, max_m_large = 0;
+    const int align = 16 / (int)T;
+    for (int k = 0; k < ninst; ++k) {
+      const stokes_problem* p = probs[k];
+      if (p->nlevels - 1 <= l) continue;
+      const stokes_patches* pa = &p->patches[l];
+      const int64_t* off = p->field_off + (size_t)l * (dim + 2);
+      if (pa->npatch < 0 || (pa->npatch > 0 && (!pa->ptr || !pa->dof || !pa->nvel || !pa->npres)))
+        return fail(STOKES_ERR_INVALID_ARG, "patches: null arrays");
+      bool sh = components_share_block(&p->K[l], off, dim);
+      for (int i = 0; i < pa->npatch; ++i) {
+        const int m = pa->nvel[(size_t)i * dim];
+        const int np = pa->npres[i];
+        for (int c = 1; c < dim; ++c)
+          if (pa->nvel[(size_t)i * dim + c] != m)
+            return fail(STOKES_ERR_INVALID_ARG, "patches: components must hold the same number of DoFs");
+        if (np < 1 || np > 4 || m < 0) return fail(STOKES_ERR_INVALID_ARG, "patches: 1..4 pressure seeds per patch");
+        const int64_t b0 = pa->ptr[i], b1 = pa->ptr[i + 1];
+        if (b1 - b0 != (int64_t)dim * m + np) return fail(STOKES_ERR_INVALID_ARG, "patches: ptr does not match nvel/npres");
+        for (int c = 0; c <= dim; ++c) {
+          const int cnt = c < dim ? m : np;
+          const int64_t s0 = b0 + (int64_t)c * m;
+          for (int a = 0; a < cnt; ++a) {
+            const int g = pa->dof[s0 + a];
+            if (g < off[c] || g >= off[c + 1])
+              return fail(STOKES_ERR_INVALID_ARG, "patches: DoF outside its field range");
+            if (a > 0 && g <= pa->dof[s0 + a - 1]) return fail(STOKES_ERR_INVALID_ARG, "patches: DoFs not ascending");
+            if (l == 0 && p->dirichlet[g]) return fail(STOKES_ERR_INVALID_ARG, "patches: Dirichlet DoF in a patch");
+            if (c > 0 && c < dim && g - off[c] != pa->dof[b0 + a] - off[0]) sh = false;
+          }
+        }
+        const int id = (int)pnv.size();
+        for (int64_t q = b0; q < b1; ++q) pdof.push_back((int)(pa->dof[q] + lv.seg_off[k]));
+        pptr.push_back((int)pdof.size());
+        pnv.push_back(m);
+        pnp.push_back(np);
+        (m <= 32 ? small : large).push_back(id);
+        max_m = std::max(max_m, m);
+        max_np = std::max(max_np, np);
+        if (m > 32) max_m_large = std::max(max_m_large, m);
+        foff.push_back(fac);
+      }
+      shared = shared && sh;
+    }
+    if (pnv.empty()) continue;
+    if (max_m > 512) return fail(STOKES_ERR_INVALID_ARG, "patches: more than 512 velocity DoFs per component");
+    // factor offsets
+    fac = 0;
+    const int nblk = shared ? 1 : dim;
+    for (size_t i = 0; i < pnv.size(); ++i) {
+      foff[i] = fac;
+      const int64_t m = pnv[i], np = pnp[i];
+      const int64_t pkp = (m * (m + 1) / 2 + align - 1) / align * align;  // blocks start 16-byte aligned
+      int64_t sz = nblk * pkp + dim * m * np + np * np;
+      sz = (sz + align - 1) / align * align;
+      fac += sz;
+    }
+    // transpose map: DoF -> slots in ascending patch order
+    std::vector<int> tptr(lv.n + 1, 0), tslot(pdof.size());
+    for (int g : pdof) tptr[g + 1]++;
+    for (int64_t j = 0; j < lv.n; ++j) tptr[j + 1] += tptr[j];
+    std::vector<int> pos(tptr.begin(), tptr.end() - 1);
+    for (size_t s = 0; s < pdof.size(); ++s) tslot[pos[pdof[s]]++] = (int)s;
+    DevPatches& dp = lv.pat;
+    dp.npatch = (int)pnv.size();
+    dp.dim = dim;
+    dp.shared = shared ? 1 : 0;
+    dp.nsmall = (int)small.size();
+    dp.nlarge = (int)large.size();
+    dp.max_m = max_m;
+    dp.max_np = max_np;
+    dp.max_m_large = max_m_large;
+    dp.fac_elems = fac;
+    dp.nslots = (int64_t)pdof.size();
+    TRY(upload(h, &dp.ptr, pptr));
+    TRY(upload(h, &dp.dof, pdof));
+    TRY(upload(h, &dp.nvel, pnv));
+    TRY(upload(h, &dp.npres, pnp));
+    TRY(upload(h, &dp.foff, foff));
+    TRY(upload(h, &dp.small, small));
+    TRY(upload(h, &dp.large, large));
+    TRY(upload(h, &dp.tptr, tptr));
+    TRY(upload(h, &dp.tslot, tslot));
+    char* facp = nullptr;
+    TRY(dalloc(h, &facp, (size_t)fac * T));
+    dp.fac = facp;
+    char* yp = nullptr;
+    TRY(dalloc(h, &yp, (size_t)dp.nslots * T));
+    lv.yp = yp;
+    lv.has_patches = true;
+  }
+  // level vectors
+  for (int l = 0; l < L; ++l) {
+    Level& lv = h->lv[l];
+    char *x, *b, *r, *ta, *tb;
+    TRY(dalloc(h, &x, (size_t)lv.n * T));
+    TRY(dalloc(h, &b, (size_t)lv.n * T));
+    TRY(dalloc(h, &r, (size_t)lv.n * T));
+    TRY(dalloc(h, &ta, (size_t)lv.n * T));
+    TRY(dalloc(h, &tb, (size_t)lv.n * T));
+    lv.x = x; lv.b = b; lv.r = r; lv.ta = ta; lv.tb = tb;
+  }
+  // level-0 row kinds and Dirichlet mask
+  {
+    std::vector<uint8_t> kind(h->lv[0].n), dir(h->lv[0].n);
+    for (int k = 0; k < ninst; ++k) {
+      const stokes_problem* p = probs[k];
+      const int64_t* off = p->field_off;
+      const int64_t o = h->lv[0].seg_off[k];
+      for (int64_t i = 0; i < p->K[0].nrows; ++i) {
+        dir[o + i] = p->dirichlet[i] ? 1 : 0;
+        kind[o + i] = p->dirichlet[i] ? 2 : (i >= off[dim] ? 1 : 0);
+      }
+    }
+    TRY(upload(h, &h->kind0, kind));
+    TRY(upload(h, &h->dir0, dir));
+  }
+  // FGMRES chunks (never straddling an instance)
+  {
+    std::vector<int64_t> cb, ce;
+    std::vector<int> cs;
+    h->h_sc_beg.assign(ninst, 0);
+    h->h_sc_end.assign(ninst, 0);
+    const int64_t CH = 16384;
+    for (int k = 0; k < ninst; ++k) {
+      const int64_t o = h->lv[0].seg_off[k], n = probs[k]->K[0].nrows;
+      h->h_sc_beg[k] = (int)cb.size();
+      for (int64_t s = 0; s < n; s += CH) {
+        cb.push_back(o + s);
+        ce.push_back(o + std::min(n, s + CH));
+        cs.push_back(k);
+      }
+      h->h_sc_end[k] = (int)cb.size();
+    }
+    h->nchunks = (int)cb.size();
+    TRY(upload(h, &h->cbeg, cb));
+    TRY(upload(h, &h->cend, ce));
+    TRY(upload(h, &h->cseg, cs));
+    TRY(upload(h, &h->sc_beg, h->h_sc_beg));
+    TRY(upload(h, &h->sc_end, h->h_sc_end));
+  }
+  return STOKES_OK;
+}
+
+int stokes_setup(const stokes_problem* const* probs, int32_t ninstances, const stokes_params* params,
+                 void* cuda_stream, stokes_handle** out) {
+  if (!out) return fail(STOKES_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!probs || ninstances < 1 || !params) return fail(STOKES_ERR_INVALID_ARG, "no problems or params");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(STOKES_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  stokes_handle* h = new stokes_handle();
+  h->ninst = ninstances;
+  if (cuda_stream) {
+    h->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(STOKES_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    h->own_stream = true;
+    if (cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      stokes_destroy(h);
+      return fail(STOKES_ERR_CUDA, "cudaEventCreate failed");
+    }
+  }
+  int rc = setup_impl(h, probs, ninstances, params);
+  if (rc != STOKES_OK) {
+    stokes_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return STOKES_OK;
+}
+
+int stokes_factor_patches(stokes_handle* h, int64_t* nsingular) {
+  if (!h) return fail(STOKES_ERR_INVALID_ARG, "null handle");
+  int* dsing = nullptr;
+  TRY(join_in(h));
+  TRY(dalloc(h, &dsing, 1));
+  CK(cudaMemsetAsync(dsing, 0, sizeof(int), h->st));
+  for (int l = 0; l < h->L; ++l) {
+    Level& lv = h->lv[l];
+    if (!lv.has_patches) continue;
+    if (h->prec == STOKES_FP32) CK(vanka_factor<float>(lv.pat, lv.K, dsing, h->st));
+    else CK(vanka_factor<double>(lv.pat, lv.K, dsing, h->st));
+  }
+  int ns = 0;
+  CK(cudaMemcpyAsync(&ns, dsing, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (nsingular) *nsingular = ns;
+  h->factored = true;
+  if (ns > 0) return fail(STOKES_ERR_SINGULAR_PATCH, std::to_string(ns) + " singular patches");
+  return STOKES_OK;
+}
+
+int stokes_vcycle(stokes_handle* h, const double* r_dev, double* z_dev) {
+  if (!h || !r_dev || !z_dev) return fail(STOKES_ERR_INVALID_ARG, "null argument");
+  if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
+  if ((const void*)r_dev == (void*)z_dev) return fail(STOKES_ERR_INVALID_ARG, "r and z alias");
+  cudaGraphExec_t g;
+  TRY(join_in(h));
+  TRY(cycle_graph(h, r_dev, z_dev, &g));
+  CK(cudaGraphLaunch(g, h->st));
+  return join_out(h);
+}
+
+double stokes_cycle_bytes(const stokes_handle* hc) {
+  stokes_handle* h = const_cast<stokes_handle*>(hc);
+  if (!h) return 0.0;
+  h->led = Ledger();
+  h->led.count = true;
+  run_cycle(h, nullptr, reinterpret_cast<double*>(16));
+  const double b = h->led.bytes;
+  h->led.count = false;
+  return b;
+}
+
+double stokes_sweep_factor_bytes(const stokes_handle* h, int32_t l) {
+  if (!h || l < 0 || l >= h->L || !h->lv[l].has_patches) return 0.0;
+  return double(h->lv[l].pat.fac_elems) * esz(h);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- FGMRES
+namespace {
+
+int ensure_krylov(stokes_handle* h, int m) {
+  if (h->krylov_m >= m && h->V) return STOKES_OK;
+  const int64_t n = h->lv[0].n;
+  h->krylov_m = m;
+  h->ldh = m + 2;
+  h->ldp = m + 2;
+  TRY(dalloc(h, &h->V, (size_t)(m + 1) * n));
+  TRY(dalloc(h, &h->Z, (size_t)m * n));
+  TRY(dalloc(h, &h->w, (size_t)n));
+  TRY(dalloc(h, &h->partial, (size_t)h->nchunks * h->ldp));
+  TRY(dalloc(h, &h->hd, (size_t)h->ninst * h->ldh));
+  TRY(dalloc(h, &h->yd, (size_t)h->ninst * h->ldh));
+  TRY(dalloc(h, &h->actd, (size_t)h->ninst));
+  return STOKES_OK;
+}
+
+// per-segment dots h[s][0..ncols) = V_k . w  (fresh or accumulated)
+int seg_dots(stokes_handle* h, const double* V, int64_t ldv, int ncols, const double* w, int accumulate) {
+  CK(multidot_partial(h->nchunks, h->cbeg, h->cend, ncols, V, ldv, w, h->partial, h->ldp, h->st));
+  CK(multidot_finish(h->ninst, h->sc_beg, h->sc_end, ncols, h->partial, h->ldp, h->hd, h->ldh, accumulate, h->st));
+  return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x, double rtol, int32_t restart,
+                                   int32_t maxit, stokes_solve_info* info) {
+  if (!h || !b || !x || restart < 1 || maxit < 0 || !(rtol > 0)) return fail(STOKES_ERR_INVALID_ARG, "fgmres arguments");
+  if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
+  const int m = restart;
+  TRY(ensure_krylov(h, m));
+  const int ni = h->ninst;
+  const int64_t n = h->lv[0].n;
+  Level& L0 = h->lv[0];
+  std::vector<double> bnorm(ni), beta(ni), hbuf((size_t)ni * h->ldh);
+  std::vector<int> its(ni, 0), done(ni, 0), active(ni, 0);
+  std::vector<std::vector<double>> H(ni, std::vector<double>((size_t)(m + 1) * m)), cs(ni, std::vector<double>(m)),
+      sn(ni, std::vector<double>(m)), g(ni, std::vector<double>(m + 1));
+  std::vector<int> kcol(ni, 0), running(ni, 0);
+  TRY(join_in(h));
+  // ||b|| per instance
+  TRY(seg_dots(h, b, 0, 1, b, 0));
+  CK(cudaMemcpyAsync(hbuf.data(), h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  for (int s = 0; s < ni; ++s) bnorm[s] = std::sqrt(hbuf[(size_t)s * h->ldh]);
+  int status = STOKES_OK;
+  while (true) {
+    // true residual r = b - K0 x into V_0
+    CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, x, b, h->V, SPMV_RES, 0, 0, nullptr, h->st)));
+    TRY(seg_dots(h, h->V, 0, 1, h->V, 0));
+    CK(cudaMemcpyAsync(hbuf.data(), h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    bool any = false;
+    for (int s = 0; s < ni; ++s) {
+      beta[s] = std::sqrt(hbuf[(size_t)s * h->ldh]);
+      if (!std::isfinite(beta[s])) return fail(STOKES_ERR_NAN, "non-finite residual");
+      done[s] = (bnorm[s] == 0.0) || beta[s] <= rtol * bnorm[s];
+      active[s] = !done[s] && its[s] < maxit;
+      any = any || active[s];
+    }
+    if (!any) break;
+    CK(cudaMemcpyAsync(h->actd, active.data(), sizeof(int) * ni, cudaMemcpyHostToDevice, h->st));
+    // V_0 = r / beta (inactive instances get zero)
+    CK(seg_scale(h->nchunks, h->cbeg, h->cend, h->cseg, h->V, h->V, h->hd, h->ldh, 0, h->actd, 1, h->st));
+    for (int s = 0; s < ni; ++s) {
+      std::fill(g[s].begin(), g[s].end(), 0.0);
+      g[s][0] = beta[s];
+      kcol[s] = 0;
+      running[s] = active[s];
+    }
+    for (int j = 0; j < m; ++j) {
+      double* vj = h->V + (size_t)j * n;
+      double* zj = h->Z + (size_t)j * n;
+      cudaGraphExec_t ge;
+      TRY(cycle_graph(h, vj, zj, &ge));
+      CK(cudaGraphLaunch(ge, h->st));
+      CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, zj, zj, h->w, SPMV_SET, 0, 0, nullptr, h->st)));
+      // classical Gram-Schmidt, twice
+      TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+      CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+      CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
+      TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+      CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+      // h = first pass + second pass; column j+1 holds ||w||^2
+      CK(multidot_partial(h->nchunks, h->cbeg, h->cend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
+      CK(multidot_finish(ni, h->sc_beg, h->sc_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
+      CK(cudaMemcpyAsync(hbuf.data(), h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
+      std::vector<double> first((size_t)ni * h->ldh);
+      CK(cudaMemcpyAsync(first.data(), h->yd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      // per-instance Arnoldi column and Givens update (host)
+      bool any_running = false;
+      std::vector<int> act2(ni, 0);
+      std::vector<double> hnorm(ni, 0.0);
+      for (int s = 0; s < ni; ++s) {
+        if (!running[s]) continue;
+        double* Hs = H[s].data();
+        for (int i = 0; i <= j; ++i) Hs[(size_t)i * m + j] = first[(size_t)s * h->ldh + i] + hbuf[(size_t)s * h->ldh + i];
+        const double hn = std::sqrt(first[(size_t)s * h->ldh + j + 1]);
+        hnorm[s] = hn;
+        Hs[(size_t)(j + 1) * m + j] = hn;
+        double hmax = 0.0;
+        for (int i = 0; i <= j; ++i) hmax = std::max(hmax, std::fabs(Hs[(size_t)i * m + j]));
+        const bool breakdown = !(hn > 1e-14 * std::max(hmax, 1e-300));
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[s][i] * Hs[(size_t)i * m + j] + sn[s][i] * Hs[(size_t)(i + 1) * m + j];
+          Hs[(size_t)(i + 1) * m + j] = -sn[s][i] * Hs[(size_t)i * m + j] + cs[s][i] * Hs[(size_t)(i + 1) * m + j];
+          Hs[(size_t)i * m + j] = t;
+        }
+        const double den = std::hypot(Hs[(size_t)j * m + j], Hs[(size_t)(j + 1) * m + j]);
+        cs[s][j] = Hs[(size_t)j * m + j] / den;
+        sn[s][j] = Hs[(size_t)(j + 1) * m + j] / den;
+        Hs[(size_t)j * m + j] = den;
+        Hs[(size_t)(j + 1) * m + j] = 0.0;
+        g[s][j + 1] = -sn[s][j] * g[s][j];
+        g[s][j] = cs[s][j] * g[s][j];
+        its[s]++;
+        kcol[s] = j + 1;
+        if (!std::isfinite(g[s][j + 1])) return fail(STOKES_ERR_NAN, "non-finite Arnoldi value");
+        if (std::fabs(g[s][j + 1]) <= rtol * bnorm[s] || breakdown || its[s] >= maxit) running[s] = 0;
+        act2[s] = running[s];
+        any_running = any_running || running[s];
+      }
+      if (!any_running || j + 1 == m) break;
+      // V_{j+1} = w / ||w|| for the instances still running
+      CK(cudaMemcpyAsync(h->actd, act2.data(), sizeof(int) * ni, cudaMemcpyHostToDevice, h->st));
+      CK(seg_scale(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->yd, h->ldh, j + 1,
+                   h->actd, 1, h->st));
+    }
+    // x += Z y per instance (y from the triangular system)
+    int kmax = 0;
+    std::vector<double> ycoef((size_t)ni * h->ldh, 0.0);
+    for (int s = 0; s < ni; ++s) {
+      if (!active[s]) continue;
+      const int k = kcol[s];
+      kmax = std::max(kmax, k);
+      std::vector<double> y(k, 0.0);
+      for (int i = k - 1; i >= 0; --i) {
+        double v = g[s][i];
+        for (int q = i + 1; q < k; ++q) v -= H[s][(size_t)i * m + q] * y[q];
+        y[i] = v / H[s][(size_t)i * m + i];
+      }
+      for (int i = 0; i < k; ++i) ycoef[(size_t)s * h->ldh + i] = y[i];
+    }
+    CK(cudaMemcpyAsync(h->yd, ycoef.data(), sizeof(double) * ni * h->ldh, cudaMemcpyHostToDevice, h->st));
+    CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, kmax, h->Z, n, h->yd, h->ldh, 1.0, x, h->st));
+  }
+  // final true residuals
+  CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, x, b, h->w, SPMV_RES, 0, 0, nullptr, h->st)));
+  TRY(seg_dots(h, h->w, 0, 1, h->w, 0));
+  CK(cudaMemcpyAsync(hbuf.data(), h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  for (int s = 0; s < ni; ++s) {
+    const double rr = bnorm[s] > 0 ? std::sqrt(hbuf[(size_t)s * h->ldh]) / bnorm[s] : 0.0;
+    const int st = rr <= rtol ? STOKES_OK : STOKES_NOT_CONVERGED;
+    if (st != STOKES_OK) status = STOKES_NOT_CONVERGED;
+    if (info) {
+      info[s].iters = its[s];
+      info[s].status = st;
+      info[s].true_relres = rr;
+    }
+  }
+  TRY(join_out(h));
+  return status;
+}
+
+extern "C" int stokes_fgmres_solve_host(stokes_handle* h, const double* b_host, double* x_host, double rtol,
+                                        int32_t restart, int32_t maxit, stokes_solve_info* info) {
+  if (!h || !b_host || !x_host) return fail(STOKES_ERR_INVALID_ARG, "null argument");
+  const int64_t n = h->lv[0].n;
+  double *bd = nullptr, *xd = nullptr;
+  CK(cudaMallocAsync(&bd, sizeof(double) * n, h->st));
+  CK(cudaMallocAsync(&xd, sizeof(double) * n, h->st));
+  CK(cudaMemcpyAsync(bd, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(xd, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->st));
+  int rc = stokes_fgmres_solve(h, bd, xd, rtol, restart, maxit, info);
+  if (rc >= 0) {
+    CK(cudaMemcpyAsync(x_host, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st));
+  }
+  cudaFreeAsync(bd, h->st);
+  cudaFreeAsync(xd, h->st);
+  CK(cudaStreamSynchronize(h->st));
+  return rc;
+}
+
+// ------------------------------------------------------------- level ops
+static int level_op_impl(stokes_handle* h, int32_t op, int32_t l, const double* x, const double* b, double* y);
+
+extern "C" int stokes_level_op(stokes_handle* h, int32_t op, int32_t l, const double* x, const double* b, double* y) {
+  if (!h || l < 0 || l >= h->L || !y) return fail(STOKES_ERR_INVALID_ARG, "level_op arguments");
+  TRY(join_in(h));
+  TRY(level_op_impl(h, op, l, x, b, y));
+  return join_out(h);
+}
+
+static int level_op_impl(stokes_handle* h, int32_t op, int32_t l, const double* x, const double* b, double* y) {
+  Level& lv = h->lv[l];
+  const bool f32 = h->prec == STOKES_FP32;
+  auto in_cast = [&](int64_t n, const double* src, void* dst) -> int {
+    if (f32) CK((cast_copy<double, float>(n, src, reinterpret_cast<float*>(dst), h->st)));
+    else CK((cast_copy<double, double>(n, src, reinterpret_cast<double*>(dst), h->st)));
+    return STOKES_OK;
+  };
+  auto out_cast = [&](int64_t n, const void* src, double* dst) -> int {
+    if (f32) CK((cast_copy<float, double>(n, reinterpret_cast<const float*>(src), dst, h->st)));
+    else CK((cast_copy<double, double>(n, reinterpret_cast<const double*>(src), dst, h->st)));
+    return STOKES_OK;
+  };
+  switch (op) {
+    case STOKES_OP_SPMV_F64:
+      CK((spmv<double, double, double, double, double>(lv.K, lv.K.v64, x, x, y, SPMV_SET, 0, 0, nullptr, h->st)));
+      return STOKES_OK;
+    case STOKES_OP_SPMV:
+    case STOKES_OP_RESIDUAL: {
+      TRY(in_cast(lv.n, x, lv.ta));
+      if (op == STOKES_OP_RESIDUAL) TRY(in_cast(lv.n, b, lv.b));
+      const int mode = op == STOKES_OP_SPMV ? SPMV_SET : SPMV_RES;
+      if (f32) CK((spmv<float, float, float, float, float>(lv.K, lv.K.v32, (float*)lv.ta, (float*)lv.b, (float*)lv.tb, mode, 0, 0, nullptr, h->st)));
+      else CK((spmv<double, double, double, double, double>(lv.K, lv.K.v64, (double*)lv.ta, (double*)lv.b, (double*)lv.tb, mode, 0, 0, nullptr, h->st)));
+      return out_cast(lv.n, lv.tb, y);
+    }
+    case STOKES_OP_RESTRICT:
+    case STOKES_OP_PROLONG: {
+      if (l + 1 >= h->L) return fail(STOKES_ERR_INVALID_ARG, "no coarser level");
+      Level& lc = h->lv[l + 1];
+      const bool restr = op == STOKES_OP_RESTRICT;
+      const DevCSR& M = restr ? lv.R : lv.P;
+      void* tin = restr ? lv.ta : lc.ta;
+      void* tout = restr ? lc.tb : lv.tb;
+      TRY(in_cast(restr ? lv.n : lc.n, x, tin));
+      if (f32) CK((spmv<float, float, float, float, float>(M, M.v32, (float*)tin, (float*)nullptr, (float*)tout, SPMV_SET, 0, 0, nullptr, h->st)));
+      else CK((spmv<double, double, double, double, double>(M, M.v64, (double*)tin, (double*)nullptr, (double*)tout, SPMV_SET, 0, 0, nullptr, h->st)));
+      return out_cast(restr ? lc.n : lv.n, tout, y);
+    }
+    case STOKES_OP_VANKA:
+    case STOKES_OP_RELAX: {
+      if (!lv.has_patches) return fail(STOKES_ERR_INVALID_ARG, "level has no patches");
+      if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
+      if (op == STOKES_OP_VANKA) {
+        TRY(in_cast(lv.n, x, lv.ta));
+        if (f32) {
+          CK((vanka_apply<float, float>(lv.pat, (float*)lv.ta, (float*)lv.yp, h->st)));
+          CK(vanka_scatter<float>(lv.pat, lv.n, (float*)lv.yp, (float*)lv.tb, 1.0, 0, nullptr, nullptr, nullptr, h->st));
+        } else {
+          CK((vanka_apply<double, double>(lv.pat, (double*)lv.ta, (double*)lv.yp, h->st)));
+          CK(vanka_scatter<double>(lv.pat, lv.n, (double*)lv.yp, (double*)lv.tb, 1.0, 0, nullptr, nullptr, nullptr, h->st));
+        }
+        return out_cast(lv.n, lv.tb, y);
+      }
+      TRY(in_cast(lv.n, x, lv.tb));
+      TRY(in_cast(lv.n, b, lv.ta));
+      if (f32) TRY(relax<float>(h, l, (float*)lv.tb, (const float*)lv.ta, 1, false));
+      else TRY(relax<double>(h, l, (double*)lv.tb, (const double*)lv.ta, 1, false));
+      return out_cast(lv.n, lv.tb, y);
+    }
+    case STOKES_OP_COARSE: {
+      if (lv.coarse.nblocks == 0) return fail(STOKES_ERR_INVALID_ARG, "no coarsest blocks on this level");
+      TRY(in_cast(lv.n, x, lv.ta));
+      if (f32) CK(coarse_solve<float>(lv.coarse.nblocks, lv.coarse.boff, lv.coarse.bn, lv.coarse.koff, lv.coarse.Kinv, lv.coarse.max_n, (float*)lv.ta, (float*)lv.tb, h->st));
+      else CK(coarse_solve<double>(lv.coarse.nblocks, lv.coarse.boff, lv.coarse.bn, lv.coarse.koff, lv.coarse.Kinv, lv.coarse.max_n, (double*)lv.ta, (double*)lv.tb, h->st));
+      return out_cast(lv.n, lv.tb, y);
+    }
+    default:
+      return fail(STOKES_ERR_INVALID_ARG, "unknown op");
+  }
+}

@@ -1,0 +1,204 @@
+// Elementwise kernels, the coarsest exact solve (step a9) and the
+// segmented deterministic reductions of the FP64 FGMRES (step a11).
+// Every reduction has a fixed decomposition (chunks of rows, then a fixed
+// tree inside a block, then chunks summed in ascending order), so results
+// are bitwise reproducible run to run.
+#include "common.cuh"
+
+namespace sd {
+
+template <typename TI, typename TO>
+__global__ void k_cast(int64_t n, const TI* __restrict__ in, TO* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = TO(in[j]);
+}
+template <typename TI, typename TO>
+cudaError_t cast_copy(int64_t n, const TI* in, TO* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_cast<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, out);
+  return cudaGetLastError();
+}
+template cudaError_t cast_copy<double, float>(int64_t, const double*, float*, cudaStream_t);
+template cudaError_t cast_copy<float, double>(int64_t, const float*, double*, cudaStream_t);
+template cudaError_t cast_copy<double, double>(int64_t, const double*, double*, cudaStream_t);
+template cudaError_t cast_copy<float, float>(int64_t, const float*, float*, cudaStream_t);
+
+template <typename T, typename TI>
+__global__ void k_axpy(int64_t n, T a, const TI* __restrict__ x, T* __restrict__ y) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) y[j] += a * T(x[j]);
+}
+template <typename T, typename TI>
+cudaError_t axpy_into(int64_t n, double a, const TI* x, T* y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, T(a), x, y);
+  return cudaGetLastError();
+}
+template cudaError_t axpy_into<float, float>(int64_t, double, const float*, float*, cudaStream_t);
+template cudaError_t axpy_into<double, double>(int64_t, double, const double*, double*, cudaStream_t);
+template cudaError_t axpy_into<double, float>(int64_t, double, const float*, double*, cudaStream_t);
+
+template <typename T>
+__global__ void k_zero(int64_t n, T* __restrict__ y) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) y[j] = T(0);
+}
+template <typename T>
+cudaError_t fill_zero(int64_t n, T* y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_zero<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, y);
+  return cudaGetLastError();
+}
+template cudaError_t fill_zero<float>(int64_t, float*, cudaStream_t);
+template cudaError_t fill_zero<double>(int64_t, double*, cudaStream_t);
+
+template <typename T>
+__global__ void k_finalize(int64_t n, const T* __restrict__ x, const uint8_t* __restrict__ dir,
+                           const double* __restrict__ r64, double* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = dir[j] ? r64[j] : double(x[j]);
+}
+template <typename T>
+cudaError_t finalize_out(int64_t n, const T* x, const uint8_t* dir, const double* r64, double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, dir, r64, out);
+  return cudaGetLastError();
+}
+template cudaError_t finalize_out<float>(int64_t, const float*, const uint8_t*, const double*, double*, cudaStream_t);
+template cudaError_t finalize_out<double>(int64_t, const double*, const uint8_t*, const double*, double*, cudaStream_t);
+
+__global__ void k_flush(int4* buf, int64_t n, int v) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    buf[j] = make_int4(v, v, v, v);
+}
+cudaError_t l2_flush(void* buf, size_t bytes, cudaStream_t st) {
+  k_flush<<<152 * 8, 256, 0, st>>>(reinterpret_cast<int4*>(buf), (int64_t)(bytes / 16), 1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ coarse solve
+// One warp per output row; grid.y runs over the coarse blocks (instances).
+template <typename T>
+__global__ void __launch_bounds__(128) k_coarse(const int* __restrict__ boff, const int* __restrict__ bn,
+                                                const int64_t* __restrict__ koff, const double* __restrict__ Kinv,
+                                                const T* __restrict__ b, T* __restrict__ y) {
+  const int kb = blockIdx.y;
+  const int n = bn[kb];
+  const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const int off = boff[kb];
+  const double* Krow = Kinv + koff[kb] + (int64_t)row * n;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += Krow[j] * double(b[off + j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[off + row] = T(s);
+}
+template <typename T>
+cudaError_t coarse_solve(int nblocks, const int* boff, const int* bn, const int64_t* koff, const double* Kinv,
+                         int max_n, const T* b, T* y, cudaStream_t st) {
+  if (nblocks == 0) return cudaSuccess;
+  dim3 grid((unsigned)((max_n + 3) / 4), (unsigned)nblocks);
+  k_coarse<T><<<grid, 128, 0, st>>>(boff, bn, koff, Kinv, b, y);
+  return cudaGetLastError();
+}
+template cudaError_t coarse_solve<float>(int, const int*, const int*, const int64_t*, const double*, int,
+                                         const float*, float*, cudaStream_t);
+template cudaError_t coarse_solve<double>(int, const int*, const int*, const int64_t*, const double*, int,
+                                          const double*, double*, cudaStream_t);
+
+// ------------------------------------------------------------ reductions
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kRedThreads / 32; ++k) s += sh[k];
+  return s;  // valid in thread 0
+}
+
+// grid: (nchunks, ncols)
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const int64_t* __restrict__ cbeg,
+    const int64_t* __restrict__ cend, const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+    double* __restrict__ partial, int ldp) {
+  __shared__ double sh[kRedThreads / 32];
+  const int c = blockIdx.x, k = blockIdx.y;
+  const double* v = V + (int64_t)k * ldv;
+  double s = 0.0;
+  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kRedThreads) s += v[r] * w[r];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[(int64_t)c * ldp + k] = s;
+}
+cudaError_t multidot_partial(int nchunks, const int64_t* cbeg, const int64_t* cend, int ncols, const double* V,
+                             int64_t ldv, const double* w, double* partial, int ldp, cudaStream_t st) {
+  if (nchunks == 0 || ncols == 0) return cudaSuccess;
+  k_multidot<<<dim3((unsigned)nchunks, (unsigned)ncols), kRedThreads, 0, st>>>(cbeg, cend, V, ldv, w, partial, ldp);
+  return cudaGetLastError();
+}
+
+__global__ void k_multidot_finish(int nseg, const int* __restrict__ sc_beg, const int* __restrict__ sc_end,
+                                  int ncols, const double* __restrict__ partial, int ldp, double* __restrict__ h,
+                                  int ldh, int accumulate) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nseg * ncols) return;
+  const int s = idx / ncols, k = idx - s * ncols;
+  double v = 0.0;
+  for (int c = sc_beg[s]; c < sc_end[s]; ++c) v += partial[(int64_t)c * ldp + k];
+  if (accumulate) h[s * ldh + k] += v;
+  else h[s * ldh + k] = v;
+}
+cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int ncols, const double* partial,
+                            int ldp, double* h, int ldh, int accumulate, cudaStream_t st) {
+  const int tot = nseg * ncols;
+  if (tot == 0) return cudaSuccess;
+  k_multidot_finish<<<(tot + 127) / 128, 128, 0, st>>>(nseg, sc_beg, sc_end, ncols, partial, ldp, h, ldh, accumulate);
+  return cudaGetLastError();
+}
+
+// grid: nchunks; w[row] += sign * sum_k coef[seg*ldh + k] * V_k[row]
+__global__ void __launch_bounds__(kRedThreads) k_multiaxpy(const int64_t* __restrict__ cbeg,
+    const int64_t* __restrict__ cend, const int* __restrict__ cseg, int ncols, const double* __restrict__ V,
+    int64_t ldv, const double* __restrict__ coef, int ldh, double sign, double* __restrict__ w) {
+  const int c = blockIdx.x;
+  const double* cf = coef + cseg[c] * ldh;
+  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kRedThreads) {
+    double s = 0.0;
+    for (int k = 0; k < ncols; ++k) s += cf[k] * V[(int64_t)k * ldv + r];
+    w[r] += sign * s;
+  }
+}
+cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
+                      const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
+                      cudaStream_t st) {
+  if (nchunks == 0 || ncols == 0) return cudaSuccess;
+  k_multiaxpy<<<nchunks, kRedThreads, 0, st>>>(cbeg, cend, cseg, ncols, V, ldv, coef, ldh, sign, w);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_seg_scale(const int64_t* __restrict__ cbeg,
+    const int64_t* __restrict__ cend, const int* __restrict__ cseg, const double* __restrict__ in,
+    double* __restrict__ out, const double* __restrict__ den, int ldd, int kd, const int* __restrict__ active,
+    int sqrt_den) {
+  const int c = blockIdx.x;
+  const int s = cseg[c];
+  double d = den[s * ldd + kd];
+  if (sqrt_den) d = sqrt(d);
+  const double f = (active[s] && d > 0.0) ? 1.0 / d : 0.0;
+  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kRedThreads) out[r] = in[r] * f;
+}
+cudaError_t seg_scale(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, const double* in,
+                      double* out, const double* den, int ldd, int kd, const int* active, int sqrt_den,
+                      cudaStream_t st) {
+  if (nchunks == 0) return cudaSuccess;
+  k_seg_scale<<<nchunks, kRedThreads, 0, st>>>(cbeg, cend, cseg, in, out, den, ldd, kd, active, sqrt_den);
+  return cudaGetLastError();
+}
+
+}  // namespace sd

@@ -1,0 +1,108 @@
+// Shared definitions of the CUDA solve path (device structures, launch
+// wrappers).  Everything here is internal to libstokes_dcamg.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+namespace sd {
+
+// CSR matrix on the device: int32 row pointers and columns (nnz < 2^31),
+// FP64 values and, for an FP32 cycle, an FP32 copy of the values.
+struct DevCSR {
+  int nrows = 0, ncols = 0;
+  int64_t nnz = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  int tpr = 4;  // threads per row of the vector-CSR SpMV
+};
+
+// SpMV modes
+enum { SPMV_SET = 0, SPMV_RES = 1, SPMV_ADD = 2, SPMV_SCALED_RES = 3 };
+
+// y = A x (SET), y = b - A x (RES), y += A x (ADD),
+// y = s(row) (b - A x) with s = s1 where kind[row] == 1 else s0 (SCALED_RES).
+// Accumulation in TACC.  TA: value type, TX/TB/TY: vector types.
+template <typename TA, typename TX, typename TB, typename TY, typename TACC>
+cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y, int mode,
+                 double s0, double s1, const uint8_t* kind, cudaStream_t st);
+
+// Vanka patch data of one level on the device.
+struct DevPatches {
+  int npatch = 0;
+  int dim = 2;
+  int* ptr = nullptr;     // [npatch+1] offsets into dof (int32)
+  int* dof = nullptr;     // [ptr[npatch]]
+  int* nvel = nullptr;    // [npatch] velocity DoFs per component
+  int* npres = nullptr;   // [npatch]
+  int64_t* foff = nullptr;  // [npatch] factor offsets (elements)
+  int64_t fac_elems = 0;
+  void* fac = nullptr;    // factors, float or double
+  int shared = 1;         // one velocity block shared by all components
+  int* small = nullptr;   // patch ids with m <= 32
+  int nsmall = 0;
+  int* large = nullptr;   // patch ids with m > 32
+  int nlarge = 0;
+  int max_m = 0, max_np = 0, max_m_large = 0;
+  int* tptr = nullptr;    // [n+1] transpose map: DoF -> patch-major slots
+  int* tslot = nullptr;
+  int64_t nslots = 0;
+};
+
+template <typename T>
+cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st);
+
+// Patch solves of Eqs. vanka_fact1/2 for every patch: yp (patch-major) =
+// K_i^-1 V_i r.
+template <typename T, typename TR>
+cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st);
+
+// Weighted scatter of Eq. vanka: s_j = sum over the patch slots of DoF j in
+// ascending patch order; mode 0: x_j = omega s_j / cnt_j; mode 1: x_j +=
+// omega s_j / cnt_j; mode 2 (final level-0 output): out_j = dir_j ? r64_j :
+// double(x_j + omega s_j / cnt_j).
+template <typename T>
+cudaError_t vanka_scatter(const DevPatches& p, int64_t n, const T* yp, T* x, double omega, int mode,
+                          const uint8_t* dir, const double* r64, double* out64, cudaStream_t st);
+
+// Elementwise helpers
+template <typename TI, typename TO>
+cudaError_t cast_copy(int64_t n, const TI* in, TO* out, cudaStream_t st);
+template <typename T, typename TI>
+cudaError_t axpy_into(int64_t n, double a, const TI* xin, T* y, cudaStream_t st);   // y += a x
+template <typename T>
+cudaError_t fill_zero(int64_t n, T* y, cudaStream_t st);
+// out_j = dir_j ? r64_j : double(x_j)
+template <typename T>
+cudaError_t finalize_out(int64_t n, const T* x, const uint8_t* dir, const double* r64, double* out, cudaStream_t st);
+// Write (flush) a buffer larger than L2.
+cudaError_t l2_flush(void* buf, size_t bytes, cudaStream_t st);
+
+// Coarsest exact solve: for each block k, y[off_k + i] = sum_j Kinv_k[i][j] b[off_k + j]
+// (Kinv_k: n_k x n_k leading block of the bordered inverse, FP64 row-major).
+template <typename T>
+cudaError_t coarse_solve(int nblocks, const int* boff, const int* bn, const int64_t* koff,
+                         const double* Kinv, int max_n, const T* b, T* y, cudaStream_t st);
+
+// Segmented deterministic reductions for FGMRES (FP64).  Rows are cut into
+// chunks that never straddle a segment (instance).  partial[c*ldp + k] =
+// sum_{rows of chunk c} V_k[row] * w[row] for k < ncols (V_k = V + k*ldv).
+cudaError_t multidot_partial(int nchunks, const int64_t* cbeg, const int64_t* cend, int ncols,
+                             const double* V, int64_t ldv, const double* w, double* partial, int ldp,
+                             cudaStream_t st);
+// h[s*ldh + k] = (accumulate ? h : 0) + sum over chunks of segment s (in order) of partial
+cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int ncols,
+                            const double* partial, int ldp, double* h, int ldh, int accumulate,
+                            cudaStream_t st);
+// w[row] += sign * sum_k coef[seg(row)*ldh + k] * V_k[row]
+cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
+                      const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
+                      cudaStream_t st);
+// out[row] = in[row] * scale_inv(seg)  where scale_inv = (den[seg*ldd + kd] > 0 && active[seg]) ? 1/den : 0
+cudaError_t seg_scale(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg,
+                      const double* in, double* out, const double* den, int ldd, int kd,
+                      const int* active, int sqrt_den, cudaStream_t st);
+
+}  // namespace sd

@@ -1,0 +1,443 @@
+// Additive Vanka relaxation on the device (Sec. 3.3.1): batched patch
+// factorisation (step a5), gather + block-factorised patch solve (a4, a6)
+// and the deterministic weighted scatter (a7).
+//
+// Patch factor layout (elements of T, block start 16-byte aligned):
+//   nblk packed lower triangles of A_c^-1 (nblk = 1 when all velocity
+//   components share one block, else dim), each m(m+1)/2 entries, row by
+//   row; then U = A^-1 B^T stored seed-major (np columns of dim*m); then
+//   S^-1 (np x np, row-major) with S = -B A^-1 B^T.
+// The patch solve computes, for b = V_i r (Eqs. vanka_fact1/2),
+//   y_u = A^-1 b_u,  y_p = S^-1 (b_p - U^T b_u),  x_u = y_u - U y_p,
+// which is [I U^; 0 I][A^-1 0; B^ S^-1] b with U^ = -U and
+// B^ = -S^-1 B A^-1 = -S^-1 U^T (A is symmetric), so B^ needs no storage.
+#include "common.cuh"
+
+namespace sd {
+
+constexpr int kMaxNp = 4;     // seeds per patch supported by the apply kernels
+constexpr int kWarpM = 32;    // velocity DoFs per component handled by the warp kernel
+constexpr int kWarpPk = kWarpM * (kWarpM + 1) / 2;
+
+__device__ __forceinline__ int packed_index(int a, int b) {
+  return a >= b ? a * (a + 1) / 2 + b : b * (b + 1) / 2 + a;
+}
+
+// Packed block length rounded up to 16 bytes, so every block starts aligned.
+template <typename T>
+__host__ __device__ __forceinline__ int padded_pk(int m) {
+  constexpr int V = 16 / sizeof(T);
+  return (m * (m + 1) / 2 + V - 1) / V * V;
+}
+
+// -------------------------------------------------------------- factorise
+__device__ __forceinline__ int bsearch_int(const int* v, int n, int key) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int x = v[mid];
+    if (x == key) return mid;
+    if (x < key) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_vanka_factor(int npatch, int dim, int shared,
+    const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
+    const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing,
+    int max_m, int max_np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int i = blockIdx.x;
+  if (i >= npatch) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int base = ptr[i], m = nvel[i], np = npres[i];
+  const int mu = dim * m, mt = mu + np;
+  // shared layout
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* BT = A + (size_t)max_m * max_m;
+  T* U = BT + (size_t)dim * max_m * max_np;
+  T* colk = U + (size_t)dim * max_m * max_np;
+  T* rowk = colk + max_m;
+  T* S = rowk + max_m;               // kMaxNp^2
+  T* misc = S + kMaxNp * kMaxNp;     // [0]: diag max, [1]: singular flag
+  int* sdof = reinterpret_cast<int*>(misc + 4);
+
+  for (int k = tid; k < mt; k += nt) sdof[k] = dof[base + k];
+  for (int k = tid; k < mu * np; k += nt) BT[k] = T(0);
+  if (tid == 0) misc[1] = T(0);
+  __syncthreads();
+  // B^T columns: entries of velocity rows in the seed (pressure) columns
+  for (int r = tid; r < mu; r += nt) {
+    const int g = sdof[r];
+    for (int e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+      const int c = col[e];
+      for (int k = 0; k < np; ++k)
+        if (sdof[mu + k] == c) BT[r * np + k] = T(Kval[e]);
+    }
+  }
+  const int nblk = shared ? 1 : dim;
+  const int pkp = padded_pk<T>(m);
+  T* out = fac + foff[i];
+  for (int cb = 0; cb < nblk; ++cb) {
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) A[e] = T(0);
+    __syncthreads();
+    for (int a = tid; a < m; a += nt) {
+      const int g = sdof[cb * m + a];
+      for (int e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+        const int pos = bsearch_int(sdof + cb * m, m, col[e]);
+        if (pos >= 0) A[a * m + pos] = T(Kval[e]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T dm = T(0);
+      for (int a = 0; a < m; ++a) dm = fmax(dm, fabs(A[a * m + a]));
+      misc[0] = dm;
+    }
+    __syncthreads();
+    // Gauss-Jordan inversion in place; the block is SPD so no pivoting
+    for (int k = 0; k < m; ++k) {
+      T piv = A[k * m + k];
+      const bool bad = !(fabs(piv) > T(1e-12) * misc[0]);
+      if (bad) piv = T(1);  // keeps the arithmetic finite; the patch is flagged
+      const T p = T(1) / piv;
+      for (int j = tid; j < m; j += nt) {
+        colk[j] = A[j * m + k];
+        rowk[j] = (j == k) ? p : A[k * m + j] * p;
+      }
+      if (tid == 0 && bad) misc[1] = T(1);
+      __syncthreads();
+      for (int e = tid; e < m * m; e += nt) {
+        const int ii = e / m, jj = e - ii * m;
+        if (ii == k) A[e] = rowk[jj];
+        else if (jj == k) A[e] = -colk[ii] * p;
+        else A[e] -= colk[ii] * rowk[jj];
+      }
+      __syncthreads();
+    }
+    // packed lower triangle of the (symmetrised) inverse
+    for (int a = tid; a < m; a += nt)
+      for (int b = 0; b <= a; ++b) out[cb * pkp + a * (a + 1) / 2 + b] = T(0.5) * (A[a * m + b] + A[b * m + a]);
+    // U rows of the components this block serves
+    const int c0 = shared ? 0 : cb, c1 = shared ? dim : cb + 1;
+    for (int c = c0; c < c1; ++c)
+      for (int idx = tid; idx < m * np; idx += nt) {
+        const int a = idx / np, k = idx - a * np;
+        T s = T(0);
+        for (int b = 0; b < m; ++b) s += A[a * m + b] * BT[(c * m + b) * np + k];
+        U[(c * m + a) * np + k] = s;
+      }
+  }
+  __syncthreads();
+  if (tid < np * np) {
+    const int k = tid / np, k2 = tid - k * np;
+    T s = T(0);
+    for (int r = 0; r < mu; ++r) s += BT[r * np + k] * U[r * np + k2];
+    S[k * kMaxNp + k2] = -s;
+  }
+  __syncthreads();
+  T* Uout = out + nblk * pkp;
+  T* Sout = Uout + mu * np;
+  for (int idx = tid; idx < mu * np; idx += nt) {
+    const int r = idx / np, k = idx - r * np;
+    Uout[k * mu + r] = U[r * np + k];
+  }
+  if (tid == 0) {
+    // S^-1 by Gauss-Jordan with partial pivoting (np <= 4)
+    T M[kMaxNp][2 * kMaxNp];
+    T smax = T(0);
+    for (int a = 0; a < np; ++a)
+      for (int b = 0; b < np; ++b) {
+        M[a][b] = S[a * kMaxNp + b];
+        M[a][np + b] = a == b ? T(1) : T(0);
+        smax = fmax(smax, fabs(M[a][b]));
+      }
+    bool sing = misc[1] != T(0);
+    for (int k = 0; k < np; ++k) {
+      int pr = k;
+      for (int a = k + 1; a < np; ++a)
+        if (fabs(M[a][k]) > fabs(M[pr][k])) pr = a;
+      if (!(fabs(M[pr][k]) > T(1e-12) * smax)) { sing = true; break; }
+      if (pr != k)
+        for (int b = 0; b < 2 * np; ++b) { T t = M[k][b]; M[k][b] = M[pr][b]; M[pr][b] = t; }
+      const T p = T(1) / M[k][k];
+      for (int b = 0; b < 2 * np; ++b) M[k][b] *= p;
+      for (int a = 0; a < np; ++a)
+        if (a != k) {
+          const T f = M[a][k];
+          for (int b = 0; b < 2 * np; ++b) M[a][b] -= f * M[k][b];
+        }
+    }
+    for (int a = 0; a < np; ++a)
+      for (int b = 0; b < np; ++b) Sout[a * np + b] = sing ? T(0) : M[a][np + b];
+    if (sing) atomicAdd(nsing, 1);
+  }
+}
+
+template <typename T>
+cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st) {
+  if (p.npatch == 0) return cudaSuccess;
+  const int dm = p.dim;
+  size_t shm = sizeof(T) * ((size_t)p.max_m * p.max_m + 2 * (size_t)dm * p.max_m * p.max_np + 2 * p.max_m +
+                            kMaxNp * kMaxNp + 4) +
+               sizeof(int) * ((size_t)dm * p.max_m + p.max_np) + 16;
+  if (shm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_vanka_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+  }
+  k_vanka_factor<T><<<p.npatch, 128, shm, st>>>(p.npatch, dm, p.shared, p.ptr, p.dof, p.nvel, p.npres, p.foff,
+                                                K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac), nsingular,
+                                                p.max_m, p.max_np);
+  return cudaGetLastError();
+}
+template cudaError_t vanka_factor<float>(const DevPatches&, const DevCSR&, int*, cudaStream_t);
+template cudaError_t vanka_factor<double>(const DevPatches&, const DevCSR&, int*, cudaStream_t);
+
+// -------------------------------------------------------------- apply
+// Copy n elements of T from global (16-byte aligned) to shared memory with
+// 16-byte streaming loads (evict-first: the factors are read once per sweep
+// and must not push the level vectors and index maps out of L2).
+template <typename T>
+__device__ __forceinline__ void group_copy(T* __restrict__ dst, const T* __restrict__ src, int n, int lane, int nl) {
+  constexpr int V = 16 / sizeof(T);
+  const int nv = n / V;
+  const int4* s4 = reinterpret_cast<const int4*>(src);
+  int4* d4 = reinterpret_cast<int4*>(dst);
+  for (int k = lane; k < nv; k += nl) d4[k] = __ldcs(s4 + k);
+  for (int k = nv * V + lane; k < n; k += nl) dst[k] = __ldcs(src + k);
+}
+
+template <typename T, typename TR, int DIM>
+__global__ void __launch_bounds__(128) k_vanka_apply_warp(int nlist, const int* __restrict__ list,
+    const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
+    const int* __restrict__ npres, const int64_t* __restrict__ foff, int shared, const T* __restrict__ fac,
+    const TR* __restrict__ r, T* __restrict__ yp) {
+  __shared__ __align__(16) T sA[4][kWarpPk + 4];
+  __shared__ T sb[4][DIM * kWarpM + kMaxNp];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 4 + warp;
+  if (gw >= nlist) return;
+  const int i = list ? list[gw] : gw;
+  const int base = ptr[i], m = nvel[i], np = npres[i];
+  const int mu = DIM * m, mt = mu + np;
+  const int64_t fo = foff[i];
+  const int pk = m * (m + 1) / 2;
+  T* A = sA[warp];
+  T* b = sb[warp];
+  for (int k = lane; k < mt; k += 32) b[k] = T(r[dof[base + k]]);
+  T yu[DIM];
+  const int nblk = shared ? 1 : DIM;
+  for (int cb = 0; cb < nblk; ++cb) {
+    __syncwarp();
+    group_copy(A, fac + fo + (int64_t)cb * padded_pk<T>(m), pk, lane, 32);
+    __syncwarp();
+    if (lane < m) {
+      const int c0 = shared ? 0 : cb, c1 = shared ? DIM : cb + 1;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        if (c < c0 || c >= c1) continue;
+        T acc = T(0);
+        for (int bb = 0; bb < m; ++bb) acc += A[packed_index(lane, bb)] * b[c * m + bb];
+        yu[c] = acc;
+      }
+    }
+  }
+  const T* U = fac + fo + (int64_t)nblk * padded_pk<T>(m);
+  const T* Sinv = U + (int64_t)mu * np;
+  T u[DIM][kMaxNp];
+  T ypk[kMaxNp];
+  T t[kMaxNp];
+#pragma unroll
+  for (int k = 0; k < kMaxNp; ++k) {
+    if (k >= np) break;
+    T part = T(0);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      u[c][k] = lane < m ? __ldcs(U + (int64_t)k * mu + c * m + lane) : T(0);
+      if (lane < m) part += u[c][k] * b[c * m + lane];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    t[k] = b[mu + k] - part;
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxNp; ++k) {
+    if (k >= np) break;
+    T s = T(0);
+    for (int k2 = 0; k2 < np; ++k2) s += Sinv[k * np + k2] * t[k2];
+    ypk[k] = s;
+  }
+  if (lane < m) {
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T x = yu[c];
+      for (int k = 0; k < np; ++k) x -= u[c][k] * ypk[k];
+      yp[base + c * m + lane] = x;
+    }
+  }
+  if (lane < np) {
+    T v = ypk[0];
+    for (int k = 1; k < np; ++k)
+      if (lane == k) v = ypk[k];
+    yp[base + mu + lane] = v;
+  }
+}
+
+// One CTA of 128 threads per patch for patches with more than 32 velocity
+// DoFs per component (coarse levels, 3D).
+template <typename T, typename TR, int DIM>
+__global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* __restrict__ list,
+    const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
+    const int* __restrict__ npres, const int64_t* __restrict__ foff, int shared, const T* __restrict__ fac,
+    const TR* __restrict__ r, T* __restrict__ yp, int max_m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NT = 128, RPT = 4;  // rows per thread: m <= 512
+  const int bi = blockIdx.x;
+  if (bi >= nlist) return;
+  const int i = list[bi];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int base = ptr[i], m = nvel[i], np = npres[i];
+  const int mu = DIM * m, mt = mu + np;
+  const int64_t fo = foff[i];
+  const int pk = m * (m + 1) / 2;
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* b = A + ((max_m * (max_m + 1) / 2 + 3) & ~3);
+  T* red = b + DIM * max_m + kMaxNp;  // [4 warps][kMaxNp]
+  for (int k = tid; k < mt; k += NT) b[k] = T(r[dof[base + k]]);
+  T yu[DIM][RPT];
+  const int nblk = shared ? 1 : DIM;
+  for (int cb = 0; cb < nblk; ++cb) {
+    __syncthreads();
+    group_copy(A, fac + fo + (int64_t)cb * padded_pk<T>(m), pk, tid, NT);
+    __syncthreads();
+    const int c0 = shared ? 0 : cb, c1 = shared ? DIM : cb + 1;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int a = tid + q * NT;
+      if (a >= m) break;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        if (c < c0 || c >= c1) continue;
+        T acc = T(0);
+        for (int bb = 0; bb < m; ++bb) acc += A[packed_index(a, bb)] * b[c * m + bb];
+        yu[c][q] = acc;
+      }
+    }
+  }
+  const T* U = fac + fo + (int64_t)nblk * padded_pk<T>(m);
+  const T* Sinv = U + (int64_t)mu * np;
+  T t[kMaxNp], ypk[kMaxNp];
+  for (int k = 0; k < np; ++k) {
+    T part = T(0);
+    for (int rr = tid; rr < mu; rr += NT) part += U[(int64_t)k * mu + rr] * b[rr];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (lane == 0) red[warp * kMaxNp + k] = part;
+  }
+  __syncthreads();
+  for (int k = 0; k < np; ++k) {
+    T s = red[k];
+    for (int w = 1; w < NT / 32; ++w) s += red[w * kMaxNp + k];
+    t[k] = b[mu + k] - s;
+  }
+  for (int k = 0; k < np; ++k) {
+    T s = T(0);
+    for (int k2 = 0; k2 < np; ++k2) s += Sinv[k * np + k2] * t[k2];
+    ypk[k] = s;
+  }
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int a = tid + q * NT;
+    if (a >= m) break;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T x = yu[c][q];
+      for (int k = 0; k < np; ++k) x -= U[(int64_t)k * mu + c * m + a] * ypk[k];
+      yp[base + c * m + a] = x;
+    }
+  }
+  if (tid < np) yp[base + mu + tid] = ypk[tid];
+}
+
+template <typename T, typename TR>
+cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
+  if (p.nsmall > 0) {
+    const unsigned blocks = (unsigned)((p.nsmall + 3) / 4);
+    if (p.dim == 2)
+      k_vanka_apply_warp<T, TR, 2><<<blocks, 128, 0, st>>>(p.nsmall, p.small, p.ptr, p.dof, p.nvel, p.npres, p.foff,
+                                                           p.shared, reinterpret_cast<const T*>(p.fac), r, yp);
+    else
+      k_vanka_apply_warp<T, TR, 3><<<blocks, 128, 0, st>>>(p.nsmall, p.small, p.ptr, p.dof, p.nvel, p.npres, p.foff,
+                                                           p.shared, reinterpret_cast<const T*>(p.fac), r, yp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (p.nlarge > 0) {
+    const int mm = p.max_m_large;
+    size_t shm = sizeof(T) * (((size_t)mm * (mm + 1) / 2 + 3) / 4 * 4 + (size_t)p.dim * mm + kMaxNp + 4 * kMaxNp) + 16;
+    cudaError_t e;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    const bool attr = shm > 48 * 1024 && cs == cudaStreamCaptureStatusNone;
+    if (p.dim == 2) {
+      if (attr) {
+        e = cudaFuncSetAttribute(k_vanka_apply_cta<T, TR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+      }
+      k_vanka_apply_cta<T, TR, 2><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
+                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm);
+    } else {
+      if (attr) {
+        e = cudaFuncSetAttribute(k_vanka_apply_cta<T, TR, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+      }
+      k_vanka_apply_cta<T, TR, 3><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
+                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+template cudaError_t vanka_apply<float, float>(const DevPatches&, const float*, float*, cudaStream_t);
+template cudaError_t vanka_apply<double, double>(const DevPatches&, const double*, double*, cudaStream_t);
+template cudaError_t vanka_apply<float, double>(const DevPatches&, const double*, float*, cudaStream_t);
+
+// -------------------------------------------------------------- scatter
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_vanka_scatter(int64_t n, const int* __restrict__ tptr,
+    const int* __restrict__ tslot, const T* __restrict__ yp, T* __restrict__ x, T omega,
+    const uint8_t* __restrict__ dir, const double* __restrict__ r64, double* __restrict__ out64) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int b = tptr[j], e = tptr[j + 1];
+  T s = T(0);
+  for (int k = b; k < e; ++k) s += yp[tslot[k]];
+  const T upd = e > b ? omega * s / T(e - b) : T(0);
+  if (MODE == 0) x[j] = upd;
+  else if (MODE == 1) x[j] += upd;
+  else out64[j] = dir[j] ? r64[j] : double(x[j] + upd);
+}
+
+template <typename T>
+cudaError_t vanka_scatter(const DevPatches& p, int64_t n, const T* yp, T* x, double omega, int mode,
+                          const uint8_t* dir, const double* r64, double* out64, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (mode == 0)
+    k_vanka_scatter<T, 0><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64);
+  else if (mode == 1)
+    k_vanka_scatter<T, 1><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64);
+  else
+    k_vanka_scatter<T, 2><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64);
+  return cudaGetLastError();
+}
+template cudaError_t vanka_scatter<float>(const DevPatches&, int64_t, const float*, float*, double, int,
+                                          const uint8_t*, const double*, double*, cudaStream_t);
+template cudaError_t vanka_scatter<double>(const DevPatches&, int64_t, const double*, double*, double, int,
+                                           const uint8_t*, const double*, double*, cudaStream_t);
+
+}  // namespace sd
