@@ -1,0 +1,359 @@
+"""Benchmark of the GB300 solve phase: FP32-preconditioned defect-correction
+AMG + FP64 FGMRES on the 2D Taylor-Hood P2/P1 256x256 manufactured-solution
+problem (592,387 DoFs, 6 levels).
+
+One step = one full solve of K0 x = b to a 1e-8 relative true residual from
+x0 = 0: batched Vanka factorisation of every level (stokes_factor_patches)
+followed by stokes_fgmres_solve (FGMRES(30), every iteration one captured
+DC-cycle graph + FP64 SpMV + CGS2 orthogonalisation).  Inputs stay resident
+in HBM; the cycle's working set (~1 GB) is far above L2, so no flush is
+needed between steps.
+
+Lines: the default arm prints the GPU line (value = solves/s over all ranks;
+N > 1 runs N independent replicas, scaling "weak").  --impl reference times
+the FP64 CPU oracle on a bounded sample on rank 0 only.
+"""
+import os
+
+# the CPU oracle runs single-threaded so that its core count is exact
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("2D Taylor-Hood P2/P1 Stokes, unit square 256x256 squares split by the (x,y)-(x+h,y+h) diagonal, "
+            "manufactured u = curl(sin^2(pi x) sin^2(pi y)), p = cos(pi x) cos(pi y); FP32 DC-all V(1,1) "
+            "additive-Vanka cycle on the P1isoP2/P1 SA hierarchy, FGMRES(30) to 1e-8 true relative residual")
+METRIC = "Stokes solves/s to 1e-8 rel-res (FP32 DC-AMG preconditioned FGMRES)"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(pr, prm, iters=2):
+    """Time the FP64 oracle on a bounded sample of one solve: its setup
+    (dense patch matrices) and `iters` FGMRES iterations."""
+    from oracle import krylov
+    from tests.helpers import make_oracle
+
+    t0 = time.perf_counter()
+    o = make_oracle(pr, prm)
+    t1 = time.perf_counter()
+    krylov.fgmres(pr.K[0], pr.b, o.apply, rtol=1e-30, restart=30, maxit=iters)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / iters
+
+
+def cpu_line(pr, prm, solve_iters, iters=2):
+    setup_s, iter_s = oracle_sample(pr, prm, iters)
+    per_solve = setup_s + solve_iters * iter_s
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle setup + {iters} FGMRES iterations on the same problem, scaled to a "
+                      f"{solve_iters}-iteration solve ({setup_s:.1f} s setup, {iter_s:.2f} s/iteration)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from problems import configs
+    pr = configs.c2()
+    prm = dict(configs.TH2D_VANKA)
+    solve_iters = args.ref_iters
+    vals = []
+    for s in range(args.warmup + args.steps):
+        setup_s, iter_s = oracle_sample(pr, prm, iters=1)
+        if s >= args.warmup:
+            vals.append(setup_s + solve_iters * iter_s)
+    per = float(np.mean(vals))
+    v = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "single process, host cores"},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: oracle setup + 1 FGMRES iteration, scaled to a "
+                                       f"{solve_iters}-iteration solve"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    import paper_2306_06795_gb300 as sd
+    from problems import configs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    pr = configs.c2()
+    prm = dict(configs.TH2D_VANKA)
+    n = pr.b.size
+    handles = {}
+    for prec in (sd.STOKES_FP32, sd.STOKES_FP64):
+        handles[prec] = sd.stokes_setup(pr, dict(prm, precision=prec), stream=stream.cuda_stream)
+    h = handles[sd.STOKES_FP32]
+    b = torch.tensor(pr.b, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+    rtol, restart, maxit = 1e-8, 30, 600
+
+    def step(hh, xx):
+        sd.stokes_factor_patches(hh)
+        xx.zero_()
+        rc, info = sd.stokes_fgmres_solve(hh, b, xx, rtol=rtol, restart=restart, maxit=maxit)
+        if rc != sd.STOKES_OK:
+            raise RuntimeError(f"solve did not converge: {info}")
+        return info[0]
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            info32 = step(h, x)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        l0 = sd.stokes_kernel_launches(h)
+        clocks = ClockSampler(local)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            info32 = step(h, x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+        launches = (sd.stokes_kernel_launches(h) - l0) // args.steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        x32 = x.cpu().numpy()
+
+        # FP64-preconditioned form of the same solve
+        h64 = handles[sd.STOKES_FP64]
+        x64 = torch.zeros_like(b)
+        for _ in range(2):
+            info64 = step(h64, x64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        k64 = max(1, args.steps // 2)
+        for _ in range(k64):
+            info64 = step(h64, x64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / k64
+        x64h = x64.cpu().numpy()
+
+        # batched patch factorisation alone
+        fct = {}
+        for prec, hh in handles.items():
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(3):
+                sd.stokes_factor_patches(hh)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            fct[prec] = a0.elapsed_time(a1) / 3
+
+        # V-cycle alone: graph replays, FP32 and FP64
+        vc = {}
+        r = torch.randn(n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
+        z = torch.empty_like(r)
+        for prec, hh in handles.items():
+            for _ in range(5):
+                sd.stokes_vcycle(hh, r, z)
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            reps = 20
+            c0.record(stream)
+            for _ in range(reps):
+                sd.stokes_vcycle(hh, r, z)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            cms = c0.elapsed_time(c1) / reps
+            cb = sd.stokes_cycle_bytes(hh)
+            vc[prec] = (cms, cb)
+
+        # dominant kernel: level-0 Vanka gather + patch solve, alone, L2 flushed
+        kms, kbytes = sd.stokes_time_kernel(h, sd.STOKES_KERNEL_VANKA_APPLY, 0, reps=20)
+
+        # end to end through the host-pointer entry point (pinned host memory)
+        bh = torch.tensor(pr.b, dtype=torch.float64).pin_memory()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        bnp = bh.numpy()
+        xnp = xh.numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke = max(1, args.steps // 2)
+        for _ in range(ke):
+            sd.stokes_factor_patches(h)
+            xnp[:] = 0.0
+            sd.stokes_fgmres_solve_host(h, bnp, xnp, rtol=rtol, restart=restart, maxit=maxit)
+        e2e_s = (time.perf_counter() - t0) / ke
+        e2e_res = float(np.linalg.norm(pr.b - pr.K[0] @ xnp) / np.linalg.norm(pr.b))
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peak()
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    value = ws * 1000.0 / ms
+    err32 = float(np.linalg.norm(x32 - x64h) / np.linalg.norm(x64h))
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dofs": int(n), "levels": int(pr.nlevels),
+                   "precision": "FP32 V-cycle, patch factors and applies; FP64 FGMRES, K0 residual, coarsest solve",
+                   "step": "stokes_factor_patches + stokes_fgmres_solve from x0 = 0",
+                   "l2": "no flush: the cycle's working set (~1 GB) is larger than L2",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "iters": {"fp32": int(info32[0]), "fp64": int(info64[0])},
+        "true_relres": {"fp32": float(info32[2]), "fp64": float(info64[2])},
+        "fp64_precond": {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_step": ms64},
+        "fp32_vs_fp64_solution_relerr": err32,
+        "factor_ms": {"fp32": fct[sd.STOKES_FP32], "fp64": fct[sd.STOKES_FP64]},
+        "vcycle": {"fp32_ms": vc[sd.STOKES_FP32][0], "fp64_ms": vc[sd.STOKES_FP64][0],
+                   "fp32_bytes": vc[sd.STOKES_FP32][1], "fp64_bytes": vc[sd.STOKES_FP64][1],
+                   "fp32_GBps": vc[sd.STOKES_FP32][1] / vc[sd.STOKES_FP32][0] / 1e6,
+                   "fp64_GBps": vc[sd.STOKES_FP64][1] / vc[sd.STOKES_FP64][0] / 1e6,
+                   "fp32_frac_of_measured_hbm": vc[sd.STOKES_FP32][1] / vc[sd.STOKES_FP32][0] / 1e6 / peak},
+        "roofline": {"kernel": "k_vanka_apply_warp (level 0, FP32)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": None, "bytes_per_launch": kbytes, "avg_launch_ms": kms},
+        "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(16 * n),
+                "d2h_bytes_per_step": int(8 * n), "true_relres": e2e_res},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_line(pr, prm, int(info64[0]))
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_profile(args):
+    """Kernel launches for ncu: factorisation, then DC cycles (graph replays)."""
+    import torch
+
+    import paper_2306_06795_gb300 as sd
+    from problems import configs
+
+    pr = configs.c2()
+    stream = torch.cuda.Stream()
+    h = sd.stokes_setup(pr, dict(configs.TH2D_VANKA, precision=sd.STOKES_FP32), stream=stream.cuda_stream)
+    sd.stokes_factor_patches(h)
+    r = torch.tensor(pr.b, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    for _ in range(args.profile_cycles):
+        sd.stokes_vcycle(h, r, z)
+    torch.cuda.synchronize()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--profile-cycles", type=int, default=0,
+                    help="profiling driver: set up, factorise and run this many DC cycles, print nothing")
+    ap.add_argument("--ref-iters", type=int, default=34,
+                    help="iterations a full oracle solve takes (scales the reference sample)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.profile_cycles:
+        run_profile(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -206,6 +206,25 @@ int64_t stokes_level_size(const stokes_handle* h, int32_t level);
 double stokes_cycle_bytes(const stokes_handle* h);
 double stokes_sweep_factor_bytes(const stokes_handle* h, int32_t level);
 
+/* Measurement support.
+ * stokes_time_kernel runs one hot kernel of level l alone `reps` times on
+ * the handle's stream; before each launch it overwrites a 256 MiB buffer
+ * (untimed) so that no launch finds its data in L2, brackets the launch
+ * with CUDA events and returns the mean duration in ms and the algorithmic
+ * bytes of one launch (the same count stokes_cycle_bytes uses).  The first
+ * call allocates the flush buffer.
+ *   STOKES_KERNEL_VANKA_APPLY  gather + block-factorised patch solves of level l
+ *   STOKES_KERNEL_SCATTER      weighted scatter of level l
+ *   STOKES_KERNEL_SPMV         residual SpMV of level l in the cycle precision
+ *   STOKES_KERNEL_DC_RESIDUAL  the FP64 K0 residual of the DC step (l = 0)
+ * stokes_kernel_launches returns the number of kernels the handle has
+ * launched so far (graph replays count every kernel node). */
+enum { STOKES_KERNEL_VANKA_APPLY = 0, STOKES_KERNEL_SCATTER = 1, STOKES_KERNEL_SPMV = 2,
+       STOKES_KERNEL_DC_RESIDUAL = 3 };
+int stokes_time_kernel(stokes_handle* h, int32_t which, int32_t level, int32_t reps,
+                       double* avg_ms, double* bytes);
+int64_t stokes_kernel_launches(const stokes_handle* h);
+
 /* Release all device memory of the handle (NULL is allowed). */
 void stokes_destroy(stokes_handle* h);
 

@@ -27,12 +27,14 @@ STOKES_TH, STOKES_SV = 0, 1
 STOKES_DC_ALL, STOKES_DC_SKIP1, STOKES_DC_SKIP0 = 0, 1, 2
 STOKES_RELAX_VANKA, STOKES_RELAX_DLSC = 0, 1
 STOKES_FP32, STOKES_FP64 = 0, 1
+STOKES_KERNEL_VANKA_APPLY, STOKES_KERNEL_SCATTER, STOKES_KERNEL_SPMV, STOKES_KERNEL_DC_RESIDUAL = range(4)
 (STOKES_OP_SPMV, STOKES_OP_SPMV_F64, STOKES_OP_RESIDUAL, STOKES_OP_RESTRICT,
  STOKES_OP_PROLONG, STOKES_OP_VANKA, STOKES_OP_RELAX, STOKES_OP_COARSE) = range(8)
 
 EXPORTS = ["stokes_setup", "stokes_factor_patches", "stokes_vcycle", "stokes_fgmres_solve",
            "stokes_fgmres_solve_host", "stokes_level_op", "stokes_num_levels", "stokes_level_size",
-           "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_destroy",
+           "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_time_kernel",
+           "stokes_kernel_launches", "stokes_destroy",
            "stokes_status_string", "stokes_last_error"]
 
 
@@ -90,6 +92,10 @@ def _load():
     lib.stokes_cycle_bytes.restype = C.c_double
     lib.stokes_sweep_factor_bytes.argtypes = [vp, C.c_int32]
     lib.stokes_sweep_factor_bytes.restype = C.c_double
+    lib.stokes_time_kernel.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]
+    lib.stokes_kernel_launches.argtypes = [vp]
+    lib.stokes_kernel_launches.restype = C.c_int64
     lib.stokes_destroy.argtypes = [vp]
     lib.stokes_destroy.restype = None
     lib.stokes_status_string.argtypes = [C.c_int]
@@ -291,6 +297,19 @@ def stokes_cycle_bytes(h):
 
 def stokes_sweep_factor_bytes(h, level):
     return lib.stokes_sweep_factor_bytes(h.ptr, level)
+
+
+def stokes_time_kernel(h, which, level, reps=10):
+    """Mean duration (ms) of one hot kernel launched alone after an L2
+    flush, and its algorithmic bytes per launch."""
+    ms = C.c_double(0)
+    by = C.c_double(0)
+    _check(lib.stokes_time_kernel(h.ptr, which, level, reps, C.byref(ms), C.byref(by)), "stokes_time_kernel")
+    return ms.value, by.value
+
+
+def stokes_kernel_launches(h):
+    return lib.stokes_kernel_launches(h.ptr)
 
 
 def stokes_destroy(h):

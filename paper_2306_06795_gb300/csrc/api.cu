@@ -115,6 +115,8 @@ struct stokes_handle {
   std::vector<int> h_sc_beg, h_sc_end;
   void* flush = nullptr;
   size_t flush_bytes = 0;
+  int64_t launches = 0;       // kernels launched so far
+  int cycle_launches = -1;    // kernels in one DC cycle (from the ledger)
   std::vector<void*> allocs;
 };
 
@@ -508,8 +510,17 @@ int cycle_graph(stokes_handle* h, const double* r, double* z, cudaGraphExec_t* o
     *out = it->second;
     return STOKES_OK;
   }
+  if (h->cycle_launches < 0) {
+    h->led = Ledger();
+    h->led.count = true;
+    int rc0 = run_cycle(h, r, z);
+    h->led.count = false;
+    TRY(rc0);
+    h->cycle_launches = h->led.launches;
+  }
   // one plain run first (sets kernel attributes outside capture)
   TRY(run_cycle(h, r, z));
+  h->launches += h->cycle_launches;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
   int rc = run_cycle(h, r, z);
@@ -579,6 +590,7 @@ void stokes_destroy(stokes_handle* h) {
 }
 
 int stokes_num_levels(const stokes_handle* h) { return h ? h->L : 0; }
+int64_t stokes_kernel_launches(const stokes_handle* h) { return h ? h->launches : 0; }
 int64_t stokes_level_size(const stokes_handle* h, int32_t l) {
   return (h && l >= 0 && l < h->L) ? h->lv[l].n : -1;
 }
@@ -826,7 +838,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     std::vector<int> cs;
     h->h_sc_beg.assign(ninst, 0);
     h->h_sc_end.assign(ninst, 0);
-    const int64_t CH = 16384;
+    const int64_t CH = 2048;  // ~300 chunks for 0.6 M rows: every SM busy
     for (int k = 0; k < ninst; ++k) {
       const int64_t o = h->lv[0].seg_off[k], n = probs[k]->K[0].nrows;
       h->h_sc_beg[k] = (int)cb.size();
@@ -910,6 +922,7 @@ int stokes_vcycle(stokes_handle* h, const double* r_dev, double* z_dev) {
   TRY(join_in(h));
   TRY(cycle_graph(h, r_dev, z_dev, &g));
   CK(cudaGraphLaunch(g, h->st));
+  h->launches += h->cycle_launches;
   return join_out(h);
 }
 
@@ -1010,6 +1023,7 @@ extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x,
       cudaGraphExec_t ge;
       TRY(cycle_graph(h, vj, zj, &ge));
       CK(cudaGraphLaunch(ge, h->st));
+      h->launches += h->cycle_launches + 14;  // cycle + SpMV, 2x(dots, finish, axpy), norm, copies, scale
       CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, zj, zj, h->w, SPMV_SET, 0, 0, nullptr, h->st)));
       // classical Gram-Schmidt, twice
       TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
@@ -1121,6 +1135,64 @@ extern "C" int stokes_fgmres_solve_host(stokes_handle* h, const double* b_host, 
 
 // ------------------------------------------------------------- level ops
 static int level_op_impl(stokes_handle* h, int32_t op, int32_t l, const double* x, const double* b, double* y);
+
+template <typename T>
+static int launch_one(stokes_handle* h, int which, int l) {
+  Level& lv = h->lv[l];
+  T* x = reinterpret_cast<T*>(lv.x);
+  T* b = reinterpret_cast<T*>(lv.b);
+  T* r = reinterpret_cast<T*>(lv.r);
+  T* yp = reinterpret_cast<T*>(lv.yp);
+  switch (which) {
+    case STOKES_KERNEL_VANKA_APPLY: return L_apply<T, T>(h, lv, r, yp);
+    case STOKES_KERNEL_SCATTER: return L_scatter<T>(h, lv, yp, x, lv.omega, 1);
+    case STOKES_KERNEL_SPMV: return L_spmv<T, T, T, T, T>(h, lv.K, kval<T>(lv.K), x, b, r, SPMV_RES);
+    default: {
+      Level& l1 = h->lv[1];
+      return L_spmv<double, T, double, T, double>(h, lv.K, lv.K.v64, x, reinterpret_cast<const double*>(lv.ta),
+                                                  reinterpret_cast<T*>(l1.b), SPMV_SCALED_RES, h->eta_u, h->eta_p,
+                                                  h->kind0);
+    }
+  }
+}
+
+extern "C" int stokes_time_kernel(stokes_handle* h, int32_t which, int32_t l, int32_t reps, double* avg_ms,
+                                  double* bytes) {
+  if (!h || l < 0 || l >= h->L || reps < 1 || which < 0 || which > 3) return fail(STOKES_ERR_INVALID_ARG, "time_kernel arguments");
+  if ((which <= 1) && (!h->lv[l].has_patches || !h->factored)) return fail(STOKES_ERR_STATE, "level has no factored patches");
+  if (which == 3 && (l != 0 || h->L < 2)) return fail(STOKES_ERR_INVALID_ARG, "DC residual is a level-0 kernel");
+  const bool f32 = h->prec == STOKES_FP32;
+  // byte count from the ledger
+  h->led = Ledger();
+  h->led.count = true;
+  int rc = f32 ? launch_one<float>(h, which, l) : launch_one<double>(h, which, l);
+  h->led.count = false;
+  TRY(rc);
+  if (bytes) *bytes = h->led.bytes;
+  if (!h->flush) {
+    h->flush_bytes = size_t(256) << 20;
+    TRY(dalloc(h, reinterpret_cast<char**>(&h->flush), h->flush_bytes));
+  }
+  TRY(join_in(h));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double tot = 0.0;
+  for (int k = 0; k < reps; ++k) {
+    CK(l2_flush(h->flush, h->flush_bytes, h->st));
+    CK(cudaEventRecord(e0, h->st));
+    TRY(f32 ? launch_one<float>(h, which, l) : launch_one<double>(h, which, l));
+    CK(cudaEventRecord(e1, h->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    tot += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (avg_ms) *avg_ms = tot / reps;
+  return join_out(h);
+}
 
 extern "C" int stokes_level_op(stokes_handle* h, int32_t op, int32_t l, const double* x, const double* b, double* y) {
   if (!h || l < 0 || l >= h->L || !y) return fail(STOKES_ERR_INVALID_ARG, "level_op arguments");
