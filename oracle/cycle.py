@@ -57,21 +57,7 @@ def chebyshev_jacobi(M, b, lo, hi, degree):
     """x ~= M^-1 b by `degree` steps of the Chebyshev semi-iteration for the
     Jacobi-preconditioned system D^-1 M x = D^-1 b, eigenvalues of D^-1 M in
     [lo, hi], zero initial guess (Saad, Iterative Methods, Alg. 12.1)."""
-    dinv = 1.0 / M.diagonal()
-    theta = 0.5 * (hi + lo)
-    delta = 0.5 * (hi - lo)
-    sigma = theta / delta
-    rho = 1.0 / sigma
-    x = np.zeros_like(b)
-    r = dinv * b
-    d = r / theta
-    for _ in range(degree):
-        x = x + d
-        r = r - dinv * (M @ d)
-        rho_new = 1.0 / (2.0 * sigma - rho)
-        d = rho_new * rho * d + 2.0 * rho_new / delta * r
-        rho = rho_new
-    return x
+    return _dlsc.chebyshev(lambda y: M @ y, b, lo, hi, degree, dinv=1.0 / M.diagonal())
 
 
 class Oracle:

@@ -55,6 +55,16 @@ struct CoarseSet {
   int64_t kinv_elems = 0;
 };
 
+// DLSC relaxation data of one level (Sec. 3.3.2, Alg. 2, Mu = I): the
+// velocity block A, B and B^T as level-sized CSRs (rows outside the block
+// are empty), the row kinds and the Chebyshev bounds.
+struct DLSCData {
+  DevCSR A, B, BT;
+  uint8_t* kind = nullptr;  // 0 velocity, 1 pressure, 2 rows not relaxed here
+  double lamA = 0, lamS = 0;
+  void* v[9] = {nullptr};   // res, v, q, dp, t1, t2, r, d0, d1
+};
+
 struct Level {
   int64_t n = 0;
   DevCSR K;
@@ -72,6 +82,8 @@ struct Level {
   void* tb = nullptr;
   CoarseSet coarse;
   std::vector<int64_t> seg_off;  // per instance, -1 when absent
+  bool dlsc = false;
+  DLSCData dl;
 };
 
 struct Ledger {
@@ -92,6 +104,17 @@ struct stokes_handle {
   std::vector<Level> lv;
   std::vector<int> inst_levels;
   uint8_t* kind0 = nullptr;  // level 0: 0 velocity, 1 pressure, 2 Dirichlet
+  int cheb_deg[3] = {3, 3, 6};
+  int dlsc_sweeps = 2;
+  // Scott-Vogelius restriction R0 = blockdiag(I, Mcg^-1 Pi^T M_dg)
+  DevCSR R0v, R0q, Mcg;
+  int64_t ncg = 0;
+  int* prow1 = nullptr;      // level-1 row of each compressed pressure entry
+  double* mdinv = nullptr;   // 1 / diag(Mcg)
+  double* cv[5] = {nullptr}; // Chebyshev-Jacobi: rhs, x, r, d0, d1
+  double* d0buf = nullptr;   // FP64 DC residual of level 0
+  double mcg_lo = 0.5, mcg_hi = 2.0;
+  int mcg_deg = 32;
   uint8_t* dir0 = nullptr;   // level 0: 1 on Dirichlet rows
   bool factored = false;
   Ledger led;
@@ -419,19 +442,119 @@ int L_coarse(stokes_handle* h, const Level& lv, const T* b, T* y) {
   return STOKES_OK;
 }
 
+template <typename T>
+int L_cheb_init(stokes_handle* h, int64_t n, const T* b, const T* dinv, const uint8_t* mask, uint8_t want, double s,
+                double theta, T* r, T* d, T* x) {
+  if (h->led.count) {
+    h->led.bytes += double(n) * (4 * sizeof(T) + (dinv ? sizeof(T) : 0) + (mask ? 1 : 0));
+    h->led.launches += n > 0;
+    return STOKES_OK;
+  }
+  CK(cheb_init<T>(n, b, dinv, mask, want, s, theta, r, d, x, h->st));
+  return STOKES_OK;
+}
+
+template <typename T>
+int L_cheb_step(stokes_handle* h, const DevCSR& M, const T* val, const T* w, const T* dinv, T* x, T* r, const T* din,
+                T* dout, double alpha, double beta) {
+  if (h->led.count) {
+    h->led.bytes += double(M.nnz) * (sizeof(T) + 4) + 4.0 * (M.nrows + 1) + double(M.ncols) * sizeof(T) +
+                    double(M.nrows) * sizeof(T) * (6 + (dinv ? 1 : 0));
+    h->led.launches += M.nrows > 0;
+    return STOKES_OK;
+  }
+  CK(cheb_step<T>(M, val, w, dinv, x, r, din, dout, alpha, beta, h->st));
+  return STOKES_OK;
+}
+
+template <typename TI, typename TO>
+int L_scatter_rows(stokes_handle* h, int64_t n, const TI* in, const int* rows, TO* out) {
+  if (h->led.count) {
+    h->led.bytes += double(n) * (sizeof(TI) + 4 + sizeof(TO));
+    h->led.launches += n > 0;
+    return STOKES_OK;
+  }
+  CK((scatter_rows<TI, TO>(n, in, rows, out, h->st)));
+  return STOKES_OK;
+}
+
+// Chebyshev semi-iteration from a zero guess for rhs (masked rows, scaled by
+// s) on the interval [lo, hi]: x ~= M^-1 rhs.  For the Schur operator
+// B B^T (isS) every step applies B^T into tS and then B.
+template <typename T>
+int cheb_run(stokes_handle* h, const DevCSR& M, const T* mval, const DevCSR* BT, const T* btval, T* tS,
+             const T* dinv, const T* rhs, const uint8_t* mask, uint8_t want, double s, double lo, double hi,
+             int degree, T* x, T* r, T* d0, T* d1, int64_t n) {
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  TRY(L_cheb_init<T>(h, n, rhs, dinv, mask, want, s, theta, r, d0, x));
+  T* dc = d0;
+  T* dn = d1;
+  for (int k = 0; k < degree; ++k) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    const double alpha = rho_new * rho, beta = 2.0 * rho_new / delta;
+    const T* w = dc;
+    if (BT) {
+      TRY((L_spmv<T, T, T, T, T>(h, *BT, btval, dc, (const T*)nullptr, tS, SPMV_SET)));
+      w = tS;
+    }
+    TRY(L_cheb_step<T>(h, M, mval, w, dinv, x, r, dc, dn, alpha, beta));
+    std::swap(dc, dn);
+    rho = rho_new;
+  }
+  return STOKES_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- the cycle
 namespace {
 
+// One DLSC sweep (Alg. 2) on level l with Mu = I: momentum, continuity and
+// pressure-correction Chebyshev solves, then the velocity correction.
+template <typename T>
+int dlsc_sweep(stokes_handle* h, int l, T* x, const T* b) {
+  Level& L = h->lv[l];
+  DLSCData& D = L.dl;
+  T** v = reinterpret_cast<T**>(D.v);
+  T *res = v[0], *vs = v[1], *q = v[2], *dp = v[3], *t1 = v[4], *t2 = v[5], *cr = v[6], *c0 = v[7], *c1 = v[8];
+  const int64_t n = L.n;
+  const double fa = std::pow(0.5, h->dim);
+  // res = [f - A u - B^T p; g - B u]
+  TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, res, SPMV_RES)));
+  // v* ~ A^-1 (f - A u - B^T p)
+  TRY(cheb_run<T>(h, D.A, kval<T>(D.A), nullptr, nullptr, nullptr, nullptr, res, D.kind, 0, 1.0, fa * D.lamA,
+                  1.1 * D.lamA, h->cheb_deg[0], vs, cr, c0, c1, n));
+  // q ~ S^-1 (g - B (u + v*)),  S = B B^T
+  TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), vs, res, t1, SPMV_RES)));
+  TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), t2, nullptr, t1, D.kind, 1, 1.0, fa * D.lamS,
+                  1.1 * D.lamS, h->cheb_deg[1], q, cr, c0, c1, n));
+  // dp ~ S^-1 ( -(B A B^T) q )
+  TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), q, (const T*)nullptr, t1, SPMV_SET)));
+  TRY((L_spmv<T, T, T, T, T>(h, D.A, kval<T>(D.A), t1, (const T*)nullptr, t2, SPMV_SET)));
+  TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), t2, (const T*)nullptr, t1, SPMV_SET)));
+  TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), t2, nullptr, t1, D.kind, 1, -1.0, fa * D.lamS,
+                  1.1 * D.lamS, h->cheb_deg[2], dp, cr, c0, c1, n));
+  // u += v* + B^T q ;  p += dp
+  TRY((L_axpy<T, T>(h, n, 1.0, vs, x)));
+  TRY((L_axpy<T, T>(h, n, 1.0, dp, x)));
+  TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), q, (const T*)nullptr, x, SPMV_ADD)));
+  return STOKES_OK;
+}
+
 // nsweeps sweeps of x <- x + omega M^-1 (b - K x) (Eq. vanka); the first
 // sweep from a zero guess needs no residual (r = b).  When out64 is given,
 // the last scatter writes the level-0 output (Dirichlet rows take r64).
+// A DLSC level runs nsweeps calls of dlsc_sweeps DLSC sweeps instead.
 template <typename T>
 int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_guess, const double* r64 = nullptr,
           double* out64 = nullptr) {
   Level& L = h->lv[l];
-  if (L.relax != STOKES_RELAX_VANKA) return fail(STOKES_ERR_INVALID_ARG, "DLSC relaxation is not available");
+  if (L.dlsc) {
+    if (zero_guess) TRY(L_zero<T>(h, L.n, x));
+    for (int s = 0; s < nsweeps * h->dlsc_sweeps; ++s) TRY(dlsc_sweep<T>(h, l, x, b));
+    return STOKES_OK;
+  }
   T* r = reinterpret_cast<T*>(L.r);
   T* yp = reinterpret_cast<T*>(L.yp);
   if (nsweeps == 0 && zero_guess) TRY(L_zero<T>(h, L.n, x));
@@ -458,7 +581,7 @@ int vcycle(stokes_handle* h, int l) {
   T* x = reinterpret_cast<T*>(L.x);
   T* b = reinterpret_cast<T*>(L.b);
   if (l == h->L - 1) return L_coarse<T>(h, L, b, x);
-  const bool relax_here = L.has_patches && !(h->schedule == STOKES_DC_SKIP1 && l == 1);
+  const bool relax_here = (L.has_patches || L.dlsc) && !(h->schedule == STOKES_DC_SKIP1 && l == 1);
   if (relax_here) TRY(relax<T>(h, l, x, b, h->nu1, true));
   else TRY(L_zero<T>(h, L.n, x));
   TRY(L_coarse<T>(h, L, b, x));
@@ -469,6 +592,26 @@ int vcycle(stokes_handle* h, int l) {
   TRY(vcycle<T>(h, l + 1));
   TRY((L_spmv<T, T, T, T, T>(h, L.P, kval<T>(L.P), reinterpret_cast<const T*>(C.x), (const T*)nullptr, x, SPMV_ADD)));
   if (relax_here) TRY(relax<T>(h, l, x, b, h->nu2, false));
+  return STOKES_OK;
+}
+
+// Scott-Vogelius: d = eta (r - K0 x) in FP64; level-1 right-hand side =
+// velocity injection of d, pressure = Mcg^-1 Pi^T M_dg d_p by mcg_deg
+// Chebyshev-Jacobi steps on the interval [mcg_lo, mcg_hi] (FP64).
+template <typename T>
+int restrict0_sv(stokes_handle* h, const T* x0, const double* r64) {
+  Level& L0 = h->lv[0];
+  Level& L1 = h->lv[1];
+  T* b1 = reinterpret_cast<T*>(L1.b);
+  TRY((L_spmv<double, T, double, double, double>(h, L0.K, L0.K.v64, x0, r64, h->d0buf, SPMV_SCALED_RES, h->eta_u,
+                                                 h->eta_p, h->kind0)));
+  TRY((L_spmv<double, double, double, T, double>(h, h->R0v, h->R0v.v64, h->d0buf, (const double*)nullptr, b1,
+                                                 SPMV_SET)));
+  TRY((L_spmv<double, double, double, double, double>(h, h->R0q, h->R0q.v64, h->d0buf, (const double*)nullptr,
+                                                      h->cv[0], SPMV_SET)));
+  TRY(cheb_run<double>(h, h->Mcg, h->Mcg.v64, nullptr, nullptr, nullptr, h->mdinv, h->cv[0], nullptr, 0, 1.0,
+                       h->mcg_lo, h->mcg_hi, h->mcg_deg, h->cv[1], h->cv[2], h->cv[3], h->cv[4], h->ncg));
+  TRY((L_scatter_rows<double, T>(h, h->ncg, h->cv[1], h->prow1, b1)));
   return STOKES_OK;
 }
 
@@ -488,12 +631,16 @@ int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
   const bool skip0 = h->schedule == STOKES_DC_SKIP0 || !L0.has_patches;
   if (!skip0) TRY(relax<T>(h, 0, x0, r0, h->nu1, true));
   else TRY(L_zero<T>(h, L0.n, x0));
-  // DC residual in FP64: d = eta (r - K0 x); R0 = injection for TH
-  if (h->disc != STOKES_TH) return fail(STOKES_ERR_INVALID_ARG, "Scott-Vogelius transfers are not available");
-  TRY((L_spmv<double, T, double, T, double>(h, L0.K, L0.K.v64, x0, r64, reinterpret_cast<T*>(L1.b),
-                                            SPMV_SCALED_RES, h->eta_u, h->eta_p, h->kind0)));
+  // DC residual in FP64: d = eta (r - K0 x), then R0 (Eq. interp)
+  if (h->disc == STOKES_TH) {  // R0 = injection, fused into the residual
+    TRY((L_spmv<double, T, double, T, double>(h, L0.K, L0.K.v64, x0, r64, reinterpret_cast<T*>(L1.b),
+                                              SPMV_SCALED_RES, h->eta_u, h->eta_p, h->kind0)));
+  } else {
+    TRY(restrict0_sv<T>(h, x0, r64));
+  }
   TRY(vcycle<T>(h, 1));
-  TRY((L_axpy<T, T>(h, L0.n, 1.0, reinterpret_cast<const T*>(L1.x), x0)));  // P0 = I
+  if (L0.Pident) TRY((L_axpy<T, T>(h, L0.n, 1.0, reinterpret_cast<const T*>(L1.x), x0)));  // P0 = I
+  else TRY((L_spmv<T, T, T, T, T>(h, L0.P, kval<T>(L0.P), reinterpret_cast<const T*>(L1.x), (const T*)nullptr, x0, SPMV_ADD)));
   if (!skip0 && h->nu2 > 0) TRY(relax<T>(h, 0, x0, r0, h->nu2, false, r64, z64));
   else TRY(L_finalize<T>(h, L0.n, x0, r64, z64));
   return STOKES_OK;
@@ -595,6 +742,108 @@ int64_t stokes_level_size(const stokes_handle* h, int32_t l) {
   return (h && l >= 0 && l < h->L) ? h->lv[l].n : -1;
 }
 
+// DLSC level: the A, B and B^T blocks as level-sized CSRs, row kinds, bounds
+// and nine work vectors.
+static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* probs, int ninst, int l, int dim) {
+  HostCSR A, B, BT;
+  A.nrows = B.nrows = BT.nrows = A.ncols = B.ncols = BT.ncols = (int)lv.n;
+  std::vector<uint8_t> kind(lv.n, 2);
+  for (int k = 0; k < ninst; ++k) {
+    const stokes_problem* p = probs[k];
+    if (p->nlevels <= l) continue;
+    const stokes_csr* K = &p->K[l];
+    const int64_t* off = p->field_off + (size_t)l * (dim + 2);
+    const int64_t o = lv.seg_off[k];
+    const bool relaxes = p->nlevels - 1 > l;
+    for (int i = 0; i < K->nrows; ++i) {
+      const bool vel = i < off[dim];
+      if (relaxes) kind[o + i] = vel ? 0 : 1;
+      for (int64_t e = K->rowptr[i]; relaxes && e < K->rowptr[i + 1]; ++e) {
+        const int c = K->col[e];
+        const bool cvel = c < off[dim];
+        HostCSR& dst = vel ? (cvel ? A : BT) : (cvel ? B : A);
+        if (!vel && !cvel) continue;  // zero block
+        dst.col.push_back((int)(o + c));
+        dst.val.push_back(K->val[e]);
+      }
+      A.rowptr.push_back((int)A.col.size());
+      B.rowptr.push_back((int)B.col.size());
+      BT.rowptr.push_back((int)BT.col.size());
+    }
+  }
+  TRY(upload_csr(h, lv.dl.A, A));
+  TRY(upload_csr(h, lv.dl.B, B));
+  TRY(upload_csr(h, lv.dl.BT, BT));
+  TRY(upload(h, &lv.dl.kind, kind));
+  for (int k = 0; k < ninst; ++k)
+    if (probs[k]->nlevels - 1 > l) {
+      lv.dl.lamA = probs[k]->lambda_A[l];
+      lv.dl.lamS = probs[k]->lambda_S[l];
+      break;
+    }
+  if (!(lv.dl.lamA > 0 && lv.dl.lamS > 0)) return fail(STOKES_ERR_INVALID_ARG, "DLSC eigenvalue bounds must be positive");
+  for (int q = 0; q < 9; ++q) {
+    char* p = nullptr;
+    TRY(dalloc(h, &p, (size_t)lv.n * esz(h)));
+    lv.dl.v[q] = p;
+  }
+  lv.dlsc = true;
+  return STOKES_OK;
+}
+
+// Scott-Vogelius restriction data: velocity injection R0v (level 1 x level
+// 0), the projection right-hand side R0q = Pi^T M_dg and Mcg on the
+// compressed pressure rows, the level-1 row of each, 1/diag(Mcg).
+static int setup_sv(stokes_handle* h, const stokes_problem* const* probs, int ninst, int dim) {
+  Level& L0 = h->lv[0];
+  Level& L1 = h->lv[1];
+  HostCSR R0v, R0q, Mc;
+  R0v.nrows = (int)L1.n;
+  R0v.ncols = (int)L0.n;
+  std::vector<int> prow;
+  std::vector<double> dinv;
+  int64_t ncg = 0;
+  for (int k = 0; k < ninst; ++k) ncg += probs[k]->Mcg->nrows;
+  R0q.nrows = Mc.nrows = Mc.ncols = (int)ncg;
+  R0q.ncols = (int)L0.n;
+  int64_t cg0 = 0;
+  for (int k = 0; k < ninst; ++k) {
+    const stokes_problem* p = probs[k];
+    const int64_t* o0 = p->field_off;
+    const int64_t* o1 = p->field_off + (dim + 2);
+    const int64_t s0 = L0.seg_off[k], s1 = L1.seg_off[k];
+    for (int64_t i = 0; i < o1[dim + 1]; ++i) {
+      if (i < o1[dim]) {
+        R0v.col.push_back((int)(s0 + i));
+        R0v.val.push_back(1.0);
+      }
+      R0v.rowptr.push_back((int)R0v.col.size());
+    }
+    append_block(R0q, p->R0p, s0 + o0[dim]);
+    append_block(Mc, p->Mcg, cg0);
+    for (int i = 0; i < p->Mcg->nrows; ++i) {
+      prow.push_back((int)(s1 + o1[dim] + i));
+      double dg = 0.0;
+      for (int64_t e = p->Mcg->rowptr[i]; e < p->Mcg->rowptr[i + 1]; ++e)
+        if (p->Mcg->col[e] == i) dg = p->Mcg->val[e];
+      if (!(dg > 0)) return fail(STOKES_ERR_INVALID_ARG, "Mcg needs a positive diagonal");
+      dinv.push_back(1.0 / dg);
+    }
+    cg0 += p->Mcg->nrows;
+  }
+  TRY(upload_csr(h, h->R0v, R0v));
+  TRY(upload_csr(h, h->R0q, R0q));
+  TRY(upload_csr(h, h->Mcg, Mc));
+  TRY(upload(h, &h->prow1, prow));
+  TRY(upload(h, &h->mdinv, dinv));
+  for (int q = 0; q < 5; ++q) TRY(dalloc(h, &h->cv[q], (size_t)ncg));
+  TRY(dalloc(h, &h->d0buf, (size_t)L0.n));
+  h->ncg = ncg;
+  h->mcg_lo = probs[0]->mcg_lo;
+  h->mcg_hi = probs[0]->mcg_hi;
+  return STOKES_OK;
+}
+
 static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int ninst, const stokes_params* prm) {
   const int dim = probs[0]->dim;
   h->dim = dim;
@@ -608,7 +857,12 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
   if (h->prec != STOKES_FP32 && h->prec != STOKES_FP64) return fail(STOKES_ERR_INVALID_ARG, "precision");
   if (prm->nu1 < 0 || prm->nu2 < 0 || prm->schedule < 0 || prm->schedule > 2)
     return fail(STOKES_ERR_INVALID_ARG, "schedule or sweep counts");
-  if (h->disc != STOKES_TH) return fail(STOKES_ERR_INVALID_ARG, "Scott-Vogelius K0 is not available in this build");
+  if (h->disc != STOKES_TH && h->disc != STOKES_SV) return fail(STOKES_ERR_INVALID_ARG, "disc must be TH or SV");
+  for (int c = 0; c < 3; ++c) h->cheb_deg[c] = prm->cheb_deg[c];
+  h->dlsc_sweeps = prm->dlsc_sweeps;
+  h->mcg_deg = prm->mcg_deg;
+  if (h->dlsc_sweeps < 0 || h->mcg_deg < 0 || h->cheb_deg[0] < 0 || h->cheb_deg[1] < 0 || h->cheb_deg[2] < 0)
+    return fail(STOKES_ERR_INVALID_ARG, "negative Chebyshev degree or sweep count");
   int L = 0;
   for (int k = 0; k < ninst; ++k) {
     const stokes_problem* p = probs[k];
@@ -631,7 +885,21 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       if (p->P[l].nrows != p->K[l].nrows || p->P[l].ncols != p->K[l + 1].nrows)
         return fail(STOKES_ERR_INVALID_ARG, "P size mismatch on level " + std::to_string(l));
     }
-    if (!is_identity(&p->P[0])) return fail(STOKES_ERR_INVALID_ARG, "Taylor-Hood P0 must be the identity");
+    if (h->disc == STOKES_TH && !is_identity(&p->P[0]))
+      return fail(STOKES_ERR_INVALID_ARG, "Taylor-Hood P0 must be the identity");
+    if (h->disc == STOKES_SV) {
+      if (!p->R0p || !p->Mcg) return fail(STOKES_ERR_INVALID_ARG, "Scott-Vogelius problems need R0p and Mcg");
+      TRY(check_csr(p->R0p, "R0p"));
+      TRY(check_csr(p->Mcg, "Mcg"));
+      const int64_t* o0 = p->field_off;
+      const int64_t* o1 = p->field_off + (dim + 2);
+      if (o1[dim] != o0[dim] || p->R0p->ncols != o0[dim + 1] - o0[dim] || p->R0p->nrows != o1[dim + 1] - o1[dim] ||
+          p->Mcg->nrows != p->R0p->nrows || p->Mcg->ncols != p->Mcg->nrows)
+        return fail(STOKES_ERR_INVALID_ARG, "R0p/Mcg sizes do not match levels 0 and 1");
+      if (!(p->mcg_lo > 0 && p->mcg_hi > p->mcg_lo)) return fail(STOKES_ERR_INVALID_ARG, "mcg interval");
+      if (k > 0 && (p->mcg_lo != probs[0]->mcg_lo || p->mcg_hi != probs[0]->mcg_hi))
+        return fail(STOKES_ERR_INVALID_ARG, "instances must share the Mcg interval");
+    }
   }
   h->L = L;
   h->lv.resize(L);
@@ -640,7 +908,18 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
   for (int l = 0; l + 1 < L; ++l) {
     if (prm->omega) omega[l] = prm->omega[l];
     if (prm->relax) relaxk[l] = prm->relax[l];
-    if (relaxk[l] != STOKES_RELAX_VANKA) return fail(STOKES_ERR_INVALID_ARG, "DLSC relaxation is not available");
+    if (relaxk[l] != STOKES_RELAX_VANKA && relaxk[l] != STOKES_RELAX_DLSC)
+      return fail(STOKES_ERR_INVALID_ARG, "unknown relaxation");
+    if (relaxk[l] == STOKES_RELAX_DLSC) {
+      if (l == 0) return fail(STOKES_ERR_INVALID_ARG, "DLSC is available on levels >= 1 (Mu = I)");
+      for (int k = 0; k < ninst; ++k) {
+        if (probs[k]->nlevels - 1 <= l) continue;
+        if (!probs[k]->lambda_A || !probs[k]->lambda_S)
+          return fail(STOKES_ERR_INVALID_ARG, "DLSC needs lambda_A and lambda_S");
+        if (probs[k]->lambda_A[l] != probs[0]->lambda_A[l] || probs[k]->lambda_S[l] != probs[0]->lambda_S[l])
+          return fail(STOKES_ERR_INVALID_ARG, "DLSC instances must share their Chebyshev bounds");
+      }
+    }
   }
   const size_t T = esz(h);
   // segment offsets per level
@@ -710,12 +989,13 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       TRY(upload(h, &lv.coarse.Kinv, kinv));
       lv.coarse.kinv_elems = (int64_t)kinv.size();
     }
-    // Vanka patches of the instances relaxing on l
-    std::vector<int> pptr{0}, pdof, pnv, pnp, small, large;
-    std::vector<int64_t> foff;
-    int64_t fac = 0;
+    if (l + 1 < L && relaxk[l] == STOKES_RELAX_DLSC) {
+      TRY(setup_dlsc(h, lv, probs, ninst, l, dim));
+      continue;
+    }
+    // Vanka patches of the instances relaxing on l, validated, in original order
+    std::vector<int> optr{0}, odof, onv, onp;
     bool shared = true;
-    int max_m = 0, max_np = 0, max_m_large = 0;
     const int align = 16 / (int)T;
     for (int k = 0; k < ninst; ++k) {
       const stokes_problem* p = probs[k];
@@ -731,7 +1011,8 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
         for (int c = 1; c < dim; ++c)
           if (pa->nvel[(size_t)i * dim + c] != m)
             return fail(STOKES_ERR_INVALID_ARG, "patches: components must hold the same number of DoFs");
-        if (np < 1 || np > 4 || m < 0) return fail(STOKES_ERR_INVALID_ARG, "patches: 1..4 pressure seeds per patch");
+        if (np < 1 || np > 4) return fail(STOKES_ERR_INVALID_ARG, "patches: 1..4 pressure seeds per patch");
+        if (m < 1 || m > 512) return fail(STOKES_ERR_INVALID_ARG, "patches: 1..512 velocity DoFs per component");
         const int64_t b0 = pa->ptr[i], b1 = pa->ptr[i + 1];
         if (b1 - b0 != (int64_t)dim * m + np) return fail(STOKES_ERR_INVALID_ARG, "patches: ptr does not match nvel/npres");
         for (int c = 0; c <= dim; ++c) {
@@ -746,40 +1027,62 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
             if (c > 0 && c < dim && g - off[c] != pa->dof[b0 + a] - off[0]) sh = false;
           }
         }
-        const int id = (int)pnv.size();
-        for (int64_t q = b0; q < b1; ++q) pdof.push_back((int)(pa->dof[q] + lv.seg_off[k]));
-        pptr.push_back((int)pdof.size());
-        pnv.push_back(m);
-        pnp.push_back(np);
-        (m <= 32 ? small : large).push_back(id);
-        max_m = std::max(max_m, m);
-        max_np = std::max(max_np, np);
-        if (m > 32) max_m_large = std::max(max_m_large, m);
-        foff.push_back(fac);
+        for (int64_t q = b0; q < b1; ++q) odof.push_back((int)(pa->dof[q] + lv.seg_off[k]));
+        optr.push_back((int)odof.size());
+        onv.push_back(m);
+        onp.push_back(np);
       }
       shared = shared && sh;
     }
-    if (pnv.empty()) continue;
-    if (max_m > 512) return fail(STOKES_ERR_INVALID_ARG, "patches: more than 512 velocity DoFs per component");
-    // factor offsets
-    fac = 0;
+    if (onv.empty()) continue;
+    // storage order: patches with m <= 32 first (TMA tiles), then the rest
+    const int npatch = (int)onv.size();
+    std::vector<int> order;
+    for (int i = 0; i < npatch; ++i)
+      if (onv[i] <= 32) order.push_back(i);
+    const int nsmall = (int)order.size();
+    for (int i = 0; i < npatch; ++i)
+      if (onv[i] > 32) order.push_back(i);
+    std::vector<int> pptr{0}, pdof, pnv, pnp, small, large, stor(npatch);
+    std::vector<int64_t> foff;
+    int64_t fac = 0;
     const int nblk = shared ? 1 : dim;
-    for (size_t i = 0; i < pnv.size(); ++i) {
-      foff[i] = fac;
-      const int64_t m = pnv[i], np = pnp[i];
+    int max_m = 0, max_np = 0, max_m_large = 0, max_np_small = 0;
+    for (int si = 0; si < npatch; ++si) {
+      const int i = order[si];
+      stor[i] = si;
+      for (int q = optr[i]; q < optr[i + 1]; ++q) pdof.push_back(odof[q]);
+      pptr.push_back((int)pdof.size());
+      const int64_t m = onv[i], np = onp[i];
+      pnv.push_back((int)m);
+      pnp.push_back((int)np);
+      foff.push_back(fac);
       const int64_t pkp = (m * (m + 1) / 2 + align - 1) / align * align;  // blocks start 16-byte aligned
       int64_t sz = nblk * pkp + dim * m * np + np * np;
-      sz = (sz + align - 1) / align * align;
-      fac += sz;
+      fac += (sz + align - 1) / align * align;
+      (si < nsmall ? small : large).push_back(si);
+      max_m = std::max(max_m, (int)m);
+      max_np = std::max(max_np, (int)np);
+      if (m > 32) max_m_large = std::max(max_m_large, (int)m);
+      else max_np_small = std::max(max_np_small, (int)np);
     }
-    // transpose map: DoF -> slots in ascending patch order
+    foff.push_back(fac);  // sentinel
+    // transpose map: DoF -> slots, in ascending ORIGINAL patch order
     std::vector<int> tptr(lv.n + 1, 0), tslot(pdof.size());
     for (int g : pdof) tptr[g + 1]++;
     for (int64_t j = 0; j < lv.n; ++j) tptr[j + 1] += tptr[j];
     std::vector<int> pos(tptr.begin(), tptr.end() - 1);
-    for (size_t s = 0; s < pdof.size(); ++s) tslot[pos[pdof[s]]++] = (int)s;
+    for (int i = 0; i < npatch; ++i) {
+      const int si = stor[i];
+      for (int q = pptr[si]; q < pptr[si + 1]; ++q) tslot[pos[pdof[q]]++] = q;
+    }
+    // per-patch metadata for the bulk-copy tiles
+    std::vector<int4> meta(npatch);
+    for (int si = 0; si < npatch; ++si)
+      meta[si] = make_int4(pptr[si], pnv[si] | (pnp[si] << 16), (int)(uint32_t)(foff[si] & 0xffffffffu),
+                           (int)(foff[si] >> 32));
     DevPatches& dp = lv.pat;
-    dp.npatch = (int)pnv.size();
+    dp.npatch = npatch;
     dp.dim = dim;
     dp.shared = shared ? 1 : 0;
     dp.nsmall = (int)small.size();
@@ -787,10 +1090,36 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     dp.max_m = max_m;
     dp.max_np = max_np;
     dp.max_m_large = max_m_large;
+    dp.max_np_small = max_np_small;
     dp.fac_elems = fac;
     dp.nslots = (int64_t)pdof.size();
+    // tiles: about 8 KB of factors per stage, 3 stages
+    if (nsmall > 0) {
+      int64_t maxblk = 0;
+      for (int si = 0; si < nsmall; ++si) maxblk = std::max(maxblk, (foff[si + 1] - foff[si]) * (int64_t)T);
+      int tp = (int)std::max<int64_t>(4, std::min<int64_t>(64, 8192 / std::max<int64_t>(maxblk, 1)));
+      dp.tp = tp;
+      dp.stages = 3;
+      dp.ntiles = (nsmall + tp - 1) / tp;
+      int64_t fb = 0, db = 0, rh = 0;
+      for (int t = 0; t < dp.ntiles; ++t) {
+        const int i0 = t * tp, i1 = std::min(i0 + tp, nsmall);
+        fb = std::max(fb, (foff[i1] - foff[i0]) * (int64_t)T);
+        db = std::max<int64_t>(db, (int64_t)(((pptr[i1] + 3) & ~3) - (pptr[i0] & ~3)) * 4);
+        const int cnt = i1 - i0, per = (cnt + 3) / 4;
+        for (int w = 0; w < 4; ++w) {
+          const int j0 = std::min(i0 + w * per, i1), j1 = std::min(j0 + per, i1);
+          rh = std::max<int64_t>(rh, pptr[j1] - pptr[j0]);
+        }
+      }
+      dp.tile_fac_bytes = (int)fb;
+      dp.tile_dof_bytes = (int)db;
+      dp.rhs_elems = (int)((rh + 3) / 4 * 4);
+    }
+    std::vector<int> pdof_pad(pdof);
+    pdof_pad.resize(pdof.size() + 8, 0);  // bulk copies may read up to 16 bytes past the last list
     TRY(upload(h, &dp.ptr, pptr));
-    TRY(upload(h, &dp.dof, pdof));
+    TRY(upload(h, &dp.dof, pdof_pad));
     TRY(upload(h, &dp.nvel, pnv));
     TRY(upload(h, &dp.npres, pnp));
     TRY(upload(h, &dp.foff, foff));
@@ -798,6 +1127,19 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     TRY(upload(h, &dp.large, large));
     TRY(upload(h, &dp.tptr, tptr));
     TRY(upload(h, &dp.tslot, tslot));
+    TRY(upload(h, &dp.meta, meta));
+    TRY(dalloc(h, &dp.err, 1));
+    CK(cudaMemset(dp.err, 0, sizeof(int)));
+    if (nsmall > 0) {
+      const size_t shm = vanka_tma_smem(dp, T);
+      if (shm > 220 * 1024) return fail(STOKES_ERR_INVALID_ARG, "patch tiles exceed shared memory");
+      const int nb = vanka_tma_blocks_per_sm(dp, T);
+      int nsm = 0, dev = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      if (nb < 1) return fail(STOKES_ERR_INVALID_ARG, "patch tiles do not fit on an SM");
+      dp.tma_grid = std::min(dp.ntiles, nsm * nb);
+    }
     char* facp = nullptr;
     TRY(dalloc(h, &facp, (size_t)fac * T));
     dp.fac = facp;
@@ -817,6 +1159,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     TRY(dalloc(h, &tb, (size_t)lv.n * T));
     lv.x = x; lv.b = b; lv.r = r; lv.ta = ta; lv.tb = tb;
   }
+  if (h->disc == STOKES_SV) TRY(setup_sv(h, probs, ninst, dim));
   // level-0 row kinds and Dirichlet mask
   {
     std::vector<uint8_t> kind(h->lv[0].n), dir(h->lv[0].n);
@@ -884,6 +1227,11 @@ int stokes_setup(const stokes_problem* const* probs, int32_t ninstances, const s
       return fail(STOKES_ERR_CUDA, "cudaEventCreate failed");
     }
   }
+  e = vanka_prepare_kernels();
+  if (e != cudaSuccess) {
+    stokes_destroy(h);
+    return fail(STOKES_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  }
   int rc = setup_impl(h, probs, ninstances, params);
   if (rc != STOKES_OK) {
     stokes_destroy(h);
@@ -946,6 +1294,19 @@ double stokes_sweep_factor_bytes(const stokes_handle* h, int32_t l) {
 
 // ------------------------------------------------------------- FGMRES
 namespace {
+
+// The bulk-copy pipelines record a flag instead of waiting forever; a set
+// flag means a result is unusable.
+int check_pipeline_errors(stokes_handle* h) {
+  for (int l = 0; l < h->L; ++l) {
+    if (!h->lv[l].has_patches) continue;
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->lv[l].pat.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (e) return fail(STOKES_ERR_CUDA, "a patch pipeline wait timed out on level " + std::to_string(l));
+  }
+  return STOKES_OK;
+}
 
 int ensure_krylov(stokes_handle* h, int m) {
   if (h->krylov_m >= m && h->V) return STOKES_OK;
@@ -1095,6 +1456,7 @@ extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x,
     CK(cudaMemcpyAsync(h->yd, ycoef.data(), sizeof(double) * ni * h->ldh, cudaMemcpyHostToDevice, h->st));
     CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, kmax, h->Z, n, h->yd, h->ldh, 1.0, x, h->st));
   }
+  TRY(check_pipeline_errors(h));
   // final true residuals
   CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, x, b, h->w, SPMV_RES, 0, 0, nullptr, h->st)));
   TRY(seg_dots(h, h->w, 0, 1, h->w, 0));

@@ -76,6 +76,82 @@ cudaError_t l2_flush(void* buf, size_t bytes, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ Chebyshev
+template <typename T>
+__global__ void k_cheb_init(int64_t n, const T* __restrict__ b, const T* __restrict__ dinv,
+                            const uint8_t* __restrict__ mask, uint8_t want, T s, T inv_theta, T* __restrict__ r,
+                            T* __restrict__ d, T* __restrict__ x) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  T v = (!mask || mask[j] == want) ? s * b[j] : T(0);
+  if (dinv) v *= dinv[j];
+  r[j] = v;
+  d[j] = v * inv_theta;
+  x[j] = T(0);
+}
+template <typename T>
+cudaError_t cheb_init(int64_t n, const T* b, const T* dinv, const uint8_t* mask, uint8_t want, double s, double theta,
+                      T* r, T* d, T* x, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_cheb_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, b, dinv, mask, want, T(s), T(1.0 / theta), r, d, x);
+  return cudaGetLastError();
+}
+template cudaError_t cheb_init<float>(int64_t, const float*, const float*, const uint8_t*, uint8_t, double, double,
+                                      float*, float*, float*, cudaStream_t);
+template cudaError_t cheb_init<double>(int64_t, const double*, const double*, const uint8_t*, uint8_t, double, double,
+                                       double*, double*, double*, cudaStream_t);
+
+template <typename T, int TPR>
+__global__ void __launch_bounds__(256) k_cheb_step(int nrows, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const T* __restrict__ val,
+                                                   const T* __restrict__ w, const T* __restrict__ dinv,
+                                                   T* __restrict__ x, T* __restrict__ r, const T* __restrict__ din,
+                                                   T* __restrict__ dout, T alpha, T beta) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = tid / TPR;
+  const int lane = (int)(tid % TPR);
+  const bool valid = row < nrows;
+  T sum = T(0);
+  if (valid)
+    for (int k = rowptr[row] + lane; k < rowptr[row + 1]; k += TPR) sum += val[k] * w[col[k]];
+#pragma unroll
+  for (int off = TPR / 2; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off, TPR);
+  if (valid && lane == 0) {
+    const T dv = din[row];
+    x[row] += dv;
+    const T rv = r[row] - (dinv ? dinv[row] * sum : sum);
+    r[row] = rv;
+    dout[row] = alpha * dv + beta * rv;
+  }
+}
+template <typename T>
+cudaError_t cheb_step(const DevCSR& M, const T* val, const T* w, const T* dinv, T* x, T* r, const T* d_in, T* d_out,
+                      double alpha, double beta, cudaStream_t st) {
+  if (M.nrows == 0) return cudaSuccess;
+  const int64_t total = (int64_t)M.nrows * 8;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  k_cheb_step<T, 8><<<blocks, 256, 0, st>>>(M.nrows, M.rowptr, M.col, val, w, dinv, x, r, d_in, d_out, T(alpha), T(beta));
+  return cudaGetLastError();
+}
+template cudaError_t cheb_step<float>(const DevCSR&, const float*, const float*, const float*, float*, float*,
+                                      const float*, float*, double, double, cudaStream_t);
+template cudaError_t cheb_step<double>(const DevCSR&, const double*, const double*, const double*, double*, double*,
+                                       const double*, double*, double, double, cudaStream_t);
+
+template <typename TI, typename TO>
+__global__ void k_scatter_rows(int64_t n, const TI* __restrict__ in, const int* __restrict__ rows, TO* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[rows[j]] = TO(in[j]);
+}
+template <typename TI, typename TO>
+cudaError_t scatter_rows(int64_t n, const TI* in, const int* rows, TO* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_scatter_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, rows, out);
+  return cudaGetLastError();
+}
+template cudaError_t scatter_rows<double, float>(int64_t, const double*, const int*, float*, cudaStream_t);
+template cudaError_t scatter_rows<double, double>(int64_t, const double*, const int*, double*, cudaStream_t);
+
 // ------------------------------------------------------------ coarse solve
 // One warp per output row; grid.y runs over the coarse blocks (instances).
 template <typename T>

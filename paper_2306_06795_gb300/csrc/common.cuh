@@ -49,7 +49,16 @@ struct DevPatches {
   int* tptr = nullptr;    // [n+1] transpose map: DoF -> patch-major slots
   int* tslot = nullptr;
   int64_t nslots = 0;
+  // TMA tiles of the small bin (storage order: small patches first)
+  int4* meta = nullptr;   // [npatch] {ptr, m | np << 16, foff lo, foff hi}
+  int tp = 0, stages = 0, ntiles = 0, tma_grid = 0;
+  int tile_fac_bytes = 0, tile_dof_bytes = 0, rhs_elems = 0, max_np_small = 0;
+  int* err = nullptr;     // device error flags of the pipelines
 };
+
+size_t vanka_tma_smem(const DevPatches& p, size_t elem);
+cudaError_t vanka_prepare_kernels();
+int vanka_tma_blocks_per_sm(const DevPatches& p, size_t elem);
 
 template <typename T>
 cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st);
@@ -79,6 +88,20 @@ template <typename T>
 cudaError_t finalize_out(int64_t n, const T* x, const uint8_t* dir, const double* r64, double* out, cudaStream_t st);
 // Write (flush) a buffer larger than L2.
 cudaError_t l2_flush(void* buf, size_t bytes, cudaStream_t st);
+
+// Chebyshev semi-iteration pieces (Saad, Alg. 12.1), zero initial guess:
+//   init:  r = mask ? s * (dinv ? dinv*b : b) : 0;  d = r / theta;  x = 0
+//   step:  y = M w;  x += d;  r -= (dinv ? dinv*y : y);  d_out = alpha d + beta r
+// (w = d for a plain operator; w = B^T d for the B B^T products of DLSC).
+template <typename T>
+cudaError_t cheb_init(int64_t n, const T* b, const T* dinv, const uint8_t* mask, uint8_t want, double s, double theta,
+                      T* r, T* d, T* x, cudaStream_t st);
+template <typename T>
+cudaError_t cheb_step(const DevCSR& M, const T* val, const T* w, const T* dinv, T* x, T* r, const T* d_in, T* d_out,
+                      double alpha, double beta, cudaStream_t st);
+// out[rows[i]] = T(in[i])
+template <typename TI, typename TO>
+cudaError_t scatter_rows(int64_t n, const TI* in, const int* rows, TO* out, cudaStream_t st);
 
 // Coarsest exact solve: for each block k, y[off_k + i] = sum_j Kinv_k[i][j] b[off_k + j]
 // (Kinv_k: n_k x n_k leading block of the bordered inverse, FP64 row-major).

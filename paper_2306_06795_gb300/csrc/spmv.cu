@@ -81,6 +81,7 @@ SD_SPMV(double, float, double, float, double)   // FP64 DC residual of an FP32 c
 SD_SPMV(double, float, float, float, double)
 SD_SPMV(double, double, double, float, double)
 SD_SPMV(float, float, double, float, float)
+SD_SPMV(double, float, double, double, double)   // FP64 DC residual into an FP64 buffer
 #undef SD_SPMV
 
 }  // namespace sd

@@ -12,6 +12,7 @@
 // which is [I U^; 0 I][A^-1 0; B^ S^-1] b with U^ = -U and
 // B^ = -S^-1 B A^-1 = -S^-1 U^T (A is symmetric), so B^ needs no storage.
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace sd {
 
@@ -184,10 +185,6 @@ cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, c
   size_t shm = sizeof(T) * ((size_t)p.max_m * p.max_m + 2 * (size_t)dm * p.max_m * p.max_np + 2 * p.max_m +
                             kMaxNp * kMaxNp + 4) +
                sizeof(int) * ((size_t)dm * p.max_m + p.max_np) + 16;
-  if (shm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_vanka_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    if (e != cudaSuccess) return e;
-  }
   k_vanka_factor<T><<<p.npatch, 128, shm, st>>>(p.npatch, dm, p.shared, p.ptr, p.dof, p.nvel, p.npres, p.foff,
                                                 K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac), nsingular,
                                                 p.max_m, p.max_np);
@@ -362,9 +359,242 @@ __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* _
   if (tid < np) yp[base + mu + tid] = ypk[tid];
 }
 
+// Persistent, warp-specialised patch solves for patches with at most 32
+// velocity DoFs per component.  Patches are stored small-bin first, so the
+// factor blocks, index lists and metadata of `tp` consecutive patches (a
+// tile) are three contiguous ranges: one producer thread moves each tile
+// into a shared-memory ring of `stages` buffers with 1D bulk copies
+// (cp.async.bulk, evict-first in L2) completing on an mbarrier, while
+// kNCW consumer warps solve the previous tiles.  A consumer warp gathers
+// the right-hand side of its contiguous share of the tile into registers
+// (all loads in flight at once), then each half-warp solves one patch with
+// two matrix rows per lane.
+constexpr int kNCW = 4;
+
+template <typename T, typename TR, int DIM, int NPM>
+__global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
+    int nsmall, int ntiles, int tp, int stages, int fac_bytes, int dof_bytes, int rhs_elems, int shared,
+    const int4* __restrict__ meta, const int* __restrict__ pptr, const int64_t* __restrict__ foff,
+    const int* __restrict__ dof, const T* __restrict__ fac, const TR* __restrict__ r, T* __restrict__ yp,
+    int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + stages;
+  const int stage_bytes = fac_bytes + dof_bytes + tp * 16;
+  unsigned char* stage0 = smem + 128;
+  T* rhsb = reinterpret_cast<T*>(stage0 + (size_t)stages * stage_bytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, kNCW);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (warp == kNCW) {
+    if (lane == 0) {
+      const uint64_t pol = policy_evict_first();
+      int k = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k % stages;
+        if (k >= stages && !mbar_wait(empty + s, ((k / stages) - 1) & 1)) {
+          atomicOr(err, 1);
+          break;
+        }
+        const int i0 = t * tp, i1 = min(i0 + tp, nsmall);
+        const int64_t f0 = foff[i0], f1 = foff[i1];
+        const int d0 = pptr[i0] & ~3, d1 = (pptr[i1] + 3) & ~3;
+        const uint32_t fb = (uint32_t)((f1 - f0) * (int64_t)sizeof(T));
+        const uint32_t db = (uint32_t)(d1 - d0) * 4u, mb = (uint32_t)(i1 - i0) * 16u;
+        unsigned char* st = stage0 + (size_t)s * stage_bytes;
+        mbar_expect_tx(full + s, fb + db + mb);
+        bulk_g2s(st, fac + f0, fb, full + s, pol);
+        bulk_g2s(st + fac_bytes, dof + d0, db, full + s, pol);
+        bulk_g2s(st + fac_bytes + dof_bytes, meta + i0, mb, full + s, pol);
+      }
+      // every copy issued has landed before this CTA may finish
+      for (int kk = max(0, k - stages); kk < k; ++kk)
+        if (!mbar_wait(full + (kk % stages), (kk / stages) & 1)) atomicOr(err, 4);
+    }
+    return;
+  }
+  T* myrhs = rhsb + (size_t)warp * rhs_elems;
+  const int half = lane >> 4, l16 = lane & 15;
+  const int nblk = shared ? 1 : DIM;
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int s = k % stages;
+    if (!mbar_wait(full + s, (k / stages) & 1)) {
+      atomicOr(err, 2);
+      return;
+    }
+    const unsigned char* st = stage0 + (size_t)s * stage_bytes;
+    const T* sfac = reinterpret_cast<const T*>(st);
+    const int* sdof = reinterpret_cast<const int*>(st + fac_bytes);
+    const int4* smeta = reinterpret_cast<const int4*>(st + fac_bytes + dof_bytes);
+    const int cnt = min(tp, nsmall - t * tp);
+    const int per = (cnt + kNCW - 1) / kNCW;
+    const int j0 = min(warp * per, cnt), j1 = min(j0 + per, cnt);
+    const int4 mf = smeta[0];
+    const int a0 = mf.x & ~3;
+    const int64_t ftile = (int64_t)(uint32_t)mf.z | ((int64_t)mf.w << 32);
+    if (j0 < j1) {
+      const int sb = smeta[j0].x;
+      const int4 ml = smeta[j1 - 1];
+      const int ns = ml.x + DIM * (ml.y & 0xffff) + (ml.y >> 16) - sb;
+      constexpr int G = 8;
+      for (int q0 = 0; q0 < ns; q0 += 32 * G) {
+        TR v[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int q = q0 + g * 32 + lane;
+          v[g] = q < ns ? r[sdof[sb - a0 + q]] : TR(0);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int q = q0 + g * 32 + lane;
+          if (q < ns) myrhs[q] = T(v[g]);
+        }
+      }
+      __syncwarp();
+      for (int pp = 0; j0 + 2 * pp < j1; ++pp) {
+        const int j = j0 + 2 * pp + half;
+        const bool valid = j < j1;
+        const int4 mt = smeta[valid ? j : j0];
+        const int m = mt.y & 0xffff, np = mt.y >> 16, base = mt.x;
+        const int mu = DIM * m;
+        const int64_t fo = ((int64_t)(uint32_t)mt.z | ((int64_t)mt.w << 32)) - ftile;
+        const int pkp = padded_pk<T>(m);
+        const T* A = sfac + fo;
+        const T* U = A + nblk * pkp;
+        const T* Sv = U + mu * np;
+        const T* bb = myrhs + (base - sb);
+        const int ra = l16, rb = l16 + 16;
+        const int ca = min(ra, m - 1), cb = min(rb, m - 1);
+        const int ta = ca * (ca + 1) / 2, tb2 = cb * (cb + 1) / 2;
+        T acc[DIM][2];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c][0] = acc[c][1] = T(0);
+        for (int blk = 0; blk < nblk; ++blk) {
+          const T* Ab = A + blk * pkp;
+          int tb = 0;
+          for (int b = 0; b < m; ++b) {
+            const T va = Ab[ca >= b ? ta + b : tb + ca];
+            const T vb = Ab[cb >= b ? tb2 + b : tb + cb];
+            if (shared) {
+#pragma unroll
+              for (int c = 0; c < DIM; ++c) {
+                const T x = bb[c * m + b];
+                acc[c][0] += va * x;
+                acc[c][1] += vb * x;
+              }
+            } else {
+              const T x = bb[blk * m + b];
+#pragma unroll
+              for (int c = 0; c < DIM; ++c)
+                if (c == blk) {
+                  acc[c][0] += va * x;
+                  acc[c][1] += vb * x;
+                }
+            }
+            tb += b + 1;
+          }
+        }
+        T tk[NPM], yk[NPM];
+#pragma unroll
+        for (int kk = 0; kk < NPM; ++kk) {
+          T part = T(0);
+          if (kk < np)
+            for (int row = l16; row < mu; row += 16) part += U[kk * mu + row] * bb[row];
+          part += __shfl_xor_sync(0xffffffffu, part, 8);
+          part += __shfl_xor_sync(0xffffffffu, part, 4);
+          part += __shfl_xor_sync(0xffffffffu, part, 2);
+          part += __shfl_xor_sync(0xffffffffu, part, 1);
+          tk[kk] = kk < np ? bb[mu + kk] - part : T(0);
+        }
+#pragma unroll
+        for (int kk = 0; kk < NPM; ++kk) {
+          T v = T(0);
+#pragma unroll
+          for (int k2 = 0; k2 < NPM; ++k2)
+            if (kk < np && k2 < np) v += Sv[kk * np + k2] * tk[k2];
+          yk[kk] = v;
+        }
+        if (valid) {
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            if (ra < m) {
+              T x = acc[c][0];
+#pragma unroll
+              for (int kk = 0; kk < NPM; ++kk)
+                if (kk < np) x -= U[kk * mu + c * m + ra] * yk[kk];
+              yp[base + c * m + ra] = x;
+            }
+            if (rb < m) {
+              T x = acc[c][1];
+#pragma unroll
+              for (int kk = 0; kk < NPM; ++kk)
+                if (kk < np) x -= U[kk * mu + c * m + rb] * yk[kk];
+              yp[base + c * m + rb] = x;
+            }
+          }
+#pragma unroll
+          for (int kk = 0; kk < NPM; ++kk)
+            if (kk < np && l16 == kk) yp[base + mu + kk] = yk[kk];
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + s);
+  }
+}
+
+template <typename T, typename TR, int DIM, int NPM>
+static cudaError_t launch_tma(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
+  auto kern = k_vanka_apply_tma<T, TR, DIM, NPM>;
+  const size_t shm = 128 + (size_t)p.stages * (p.tile_fac_bytes + p.tile_dof_bytes + p.tp * 16) +
+                     (size_t)kNCW * p.rhs_elems * sizeof(T);
+  kern<<<p.tma_grid, 32 * (kNCW + 1), shm, st>>>(p.nsmall, p.ntiles, p.tp, p.stages, p.tile_fac_bytes,
+                                                 p.tile_dof_bytes, p.rhs_elems, p.shared, p.meta, p.ptr, p.foff,
+                                                 p.dof, reinterpret_cast<const T*>(p.fac), r, yp, p.err);
+  return cudaGetLastError();
+}
+
+template <typename T, typename TR>
+static cudaError_t apply_small_tma(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
+  const bool one = p.max_np_small <= 1;
+  if (p.dim == 2) return one ? launch_tma<T, TR, 2, 1>(p, r, yp, st) : launch_tma<T, TR, 2, 4>(p, r, yp, st);
+  return one ? launch_tma<T, TR, 3, 1>(p, r, yp, st) : launch_tma<T, TR, 3, 4>(p, r, yp, st);
+}
+
+// Shared-memory bytes of the TMA kernel for a tile configuration.
+size_t vanka_tma_smem(const DevPatches& p, size_t elem) {
+  return 128 + (size_t)p.stages * (p.tile_fac_bytes + p.tile_dof_bytes + p.tp * 16) + (size_t)kNCW * p.rhs_elems * elem;
+}
+
+int vanka_tma_blocks_per_sm(const DevPatches& p, size_t elem) {
+  int nb = 0;
+  const size_t shm = vanka_tma_smem(p, elem);
+  cudaError_t e;
+  if (elem == 4) {
+    auto kern = p.max_np_small <= 1 ? (p.dim == 2 ? k_vanka_apply_tma<float, float, 2, 1> : k_vanka_apply_tma<float, float, 3, 1>)
+                                    : (p.dim == 2 ? k_vanka_apply_tma<float, float, 2, 4> : k_vanka_apply_tma<float, float, 3, 4>);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * (kNCW + 1), shm);
+  } else {
+    auto kern = p.max_np_small <= 1 ? (p.dim == 2 ? k_vanka_apply_tma<double, double, 2, 1> : k_vanka_apply_tma<double, double, 3, 1>)
+                                    : (p.dim == 2 ? k_vanka_apply_tma<double, double, 2, 4> : k_vanka_apply_tma<double, double, 3, 4>);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * (kNCW + 1), shm);
+  }
+  return e == cudaSuccess ? nb : 0;
+}
+
 template <typename T, typename TR>
 cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
-  if (p.nsmall > 0) {
+  if (p.nsmall > 0 && p.ntiles > 0) {
+    cudaError_t e = apply_small_tma<T, TR>(p, r, yp, st);
+    if (e != cudaSuccess) return e;
+  } else if (p.nsmall > 0) {
     const unsigned blocks = (unsigned)((p.nsmall + 3) / 4);
     if (p.dim == 2)
       k_vanka_apply_warp<T, TR, 2><<<blocks, 128, 0, st>>>(p.nsmall, p.small, p.ptr, p.dof, p.nvel, p.npres, p.foff,
@@ -379,21 +609,10 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
     const int mm = p.max_m_large;
     size_t shm = sizeof(T) * (((size_t)mm * (mm + 1) / 2 + 3) / 4 * 4 + (size_t)p.dim * mm + kMaxNp + 4 * kMaxNp) + 16;
     cudaError_t e;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(st, &cs);
-    const bool attr = shm > 48 * 1024 && cs == cudaStreamCaptureStatusNone;
     if (p.dim == 2) {
-      if (attr) {
-        e = cudaFuncSetAttribute(k_vanka_apply_cta<T, TR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        if (e != cudaSuccess) return e;
-      }
       k_vanka_apply_cta<T, TR, 2><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
                                                              p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm);
     } else {
-      if (attr) {
-        e = cudaFuncSetAttribute(k_vanka_apply_cta<T, TR, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        if (e != cudaSuccess) return e;
-      }
       k_vanka_apply_cta<T, TR, 3><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
                                                              p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm);
     }
@@ -405,6 +624,32 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
 template cudaError_t vanka_apply<float, float>(const DevPatches&, const float*, float*, cudaStream_t);
 template cudaError_t vanka_apply<double, double>(const DevPatches&, const double*, double*, cudaStream_t);
 template cudaError_t vanka_apply<float, double>(const DevPatches&, const double*, float*, cudaStream_t);
+
+// Allow every kernel with large dynamic shared memory the device's opt-in
+// maximum once, so launches inside graph capture never need the attribute.
+cudaError_t vanka_prepare_kernels() {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const void* ks[] = {
+      (const void*)k_vanka_factor<float>, (const void*)k_vanka_factor<double>,
+      (const void*)k_vanka_apply_tma<float, float, 2, 1>, (const void*)k_vanka_apply_tma<float, float, 2, 4>,
+      (const void*)k_vanka_apply_tma<float, float, 3, 1>, (const void*)k_vanka_apply_tma<float, float, 3, 4>,
+      (const void*)k_vanka_apply_tma<double, double, 2, 1>, (const void*)k_vanka_apply_tma<double, double, 2, 4>,
+      (const void*)k_vanka_apply_tma<double, double, 3, 1>, (const void*)k_vanka_apply_tma<double, double, 3, 4>,
+      (const void*)k_vanka_apply_tma<float, double, 2, 1>, (const void*)k_vanka_apply_tma<float, double, 2, 4>,
+      (const void*)k_vanka_apply_tma<float, double, 3, 1>, (const void*)k_vanka_apply_tma<float, double, 3, 4>,
+      (const void*)k_vanka_apply_cta<float, float, 2>, (const void*)k_vanka_apply_cta<float, float, 3>,
+      (const void*)k_vanka_apply_cta<double, double, 2>, (const void*)k_vanka_apply_cta<double, double, 3>,
+      (const void*)k_vanka_apply_cta<float, double, 2>, (const void*)k_vanka_apply_cta<float, double, 3>};
+  for (const void* k : ks) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 // -------------------------------------------------------------- scatter
 template <typename T, int MODE>

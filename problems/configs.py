@@ -29,3 +29,14 @@ def c2(n=256):
     """2D Taylor-Hood 256x256, manufactured smooth solution, ~6 levels."""
     return stokes.build_th(M.unit_square(n), nu=1.0, bc="noslip", rhs="manufactured",
                            max_levels=6, name=f"C2 TH2D {n}^2 manufactured")
+
+
+def c3(n=128):
+    """2D Scott-Vogelius P2/P1disc on the Alfeld split of a 128x128 mesh,
+    interior vertices perturbed by U(-0.2h, 0.2h), f nodal N(0,1)."""
+    return stokes.build_sv(n, nu=1.0, perturb=0.2, seed_perturb=3001, seed_f=3002, name=f"C3 SV2D {n}^2")
+
+
+def sv_vanka_dlsc(nlevels):
+    """Vanka on level 0, DLSC on levels >= 1 (Table p2p1disc_params)."""
+    return dict(SV2D_VANKA_DLSC, relax=[0] + [1] * (nlevels - 2))

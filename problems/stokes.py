@@ -283,6 +283,21 @@ def make_patches(K, off, d, seeds=None, rel_tol=1e-14, exclude=None, Bpattern=No
                    np.array(nv, dtype=np.int32), np.array(npr, dtype=np.int32))
 
 
+def dlsc_bounds(K, field_off, d, steps=20, seed=4242):
+    """Largest-eigenvalue estimates of the velocity block A and of B B^T
+    (Mu = I) on every level, by seeded Lanczos (the Chebyshev intervals of
+    the DLSC stages, Table lsd_dgs_config)."""
+    lamA, lamS = [], []
+    for l, Kl in enumerate(K):
+        off = field_off[l]
+        nv = off[d]
+        A = Kl[:nv, :nv].tocsr()
+        B = Kl[nv:, :nv].tocsr()
+        lamA.append(sa.lanczos_max(A, steps=steps, seed=seed + l))
+        lamS.append(sa.lanczos_max((B @ B.T).tocsr(), steps=steps, seed=seed + 100 + l))
+    return np.array(lamA), np.array(lamS)
+
+
 # --------------------------------------------------------------- problems
 def manufactured_2d(nu=1.0):
     """u = curl psi, psi = sin^2(pi x) sin^2(pi y); p = cos(pi x) cos(pi y);
@@ -347,5 +362,95 @@ def build_th(mesh, nu=1.0, bc="lid", rhs="zero", seed=None, max_levels=10,
                    patches=patches, b=b, coarse_null=cn,
                    dirichlet=np.concatenate([bnd] * d + [np.zeros(npres, bool)]),
                    Mp=k0["Mp"], exact=exact)
+    prob.lambda_A, prob.lambda_S = dlsc_bounds(K, field_off, d)
     prob.info = dict(mesh=mesh, V=V, n2=n2, npres=npres, Mu=k0["Mu"])
     return prob
+
+
+def perturb_interior(mesh, amount, seed):
+    """Move every interior vertex of a unit-square/cube mesh by independent
+    U(-amount, amount) offsets per coordinate (seeded)."""
+    s = mesh.scale
+    interior = np.all((mesh.key > 0) & (mesh.key < s), axis=1)
+    d = mesh.dim
+    u = rng.uniform(seed, mesh.nv * d, -amount, amount).reshape(mesh.nv, d)
+    x = mesh.x.copy()
+    x[interior] += u[interior]
+    out = M.Mesh(x, mesh.cells, mesh.key, mesh.scale)
+    return out
+
+
+def build_sv(n, nu=1.0, perturb=0.2, seed_perturb=3001, seed_f=3002, max_levels=10, max_coarse=50,
+             name="sv"):
+    """Scott-Vogelius P2/P1disc on the Alfeld split R_B of an n x n mesh
+    (Sec. 2.1), no-slip walls, f with i.i.d. N(0,1) P2 nodal values per
+    component.  K1 is P1isoP2/P1 with P1 velocity on R_U(R_B) and continuous
+    P1 pressure on R_B (Sec. 3.1); P0 = blockdiag(I, Pi) where Pi duplicates
+    a vertex value into the discontinuous DoFs at that vertex; the pressure
+    restriction is R0^p = Mcg^-1 Pi^T M_dg (the L2 projection)."""
+    base = M.unit_square(n)
+    if perturb:
+        base = perturb_interior(base, perturb / n, seed_perturb)
+    mesh = M.barycentric_refine(base)
+    vol = M.cell_measure(mesh.x, mesh.cells)
+    assert vol.min() > 0.0
+    d = 2
+    V = M.P2Space(mesh)
+    n2 = V.n
+    nc = mesh.nc
+    ndg = 3 * nc
+    pdg = np.arange(ndg).reshape(nc, 3)       # P1disc DoF (c, k) = 3c + k
+    b2 = fem.p2_basis(d)
+    b1 = fem.p1_basis(d)
+    A = fem.assemble_stiffness(mesh.x, mesh.cells, V.cell_nodes, fem.stiffness_tensor(b2, d), n2, coef=nu)
+    Bs = fem.assemble_div(mesh.x, mesh.cells, pdg, V.cell_nodes, fem.div_tensor(b1, b2, d), ndg, n2)
+    bnd = M.p2_boundary_nodes(V)
+    uD = [np.zeros(n2), np.zeros(n2)]
+    Mu = fem.assemble_mass(mesh.x, mesh.cells, V.cell_nodes, V.cell_nodes, fem.mass_tensor(b2, b2, d), n2, n2)
+    z = rng.normal(seed_f, d * n2)
+    F = [Mu @ z[c * n2:(c + 1) * n2] for c in range(d)]
+    A_in, B_in, F_in, g = dirichlet_eliminate(A, Bs, bnd, uD, F)
+    K0 = saddle([A_in] * d, [nonzero_only(B) for B in B_in])
+    b = np.concatenate(F_in + [g])
+    # transfers and masses
+    ncg = mesh.nv
+    Pi = _csr(sp.csr_matrix((np.ones(ndg), (pdg.ravel(), mesh.cells.ravel())), shape=(ndg, ncg)))
+    Mdg = fem.assemble_mass(mesh.x, mesh.cells, pdg, pdg, fem.mass_tensor(b1, b1, d), ndg, ndg)
+    Mcg = fem.assemble_mass(mesh.x, mesh.cells, mesh.cells, mesh.cells, fem.mass_tensor(b1, b1, d), ncg, ncg)
+    R0p = _csr(Pi.T @ Mdg)
+    # K1 and hierarchy
+    K1, A1, B1pat = p1iso_K1(V, mesh.cells, None, ncg, bnd, nu)
+    Ap = pressure_laplacian(mesh)
+    Ks, Ps, offs, Bp = build_hierarchy(K1, A1, Ap, d, n2, ncg, max_levels - 1, max_coarse)
+    off0 = field_offsets(n2, ndg, d)
+    K = [K0] + Ks
+    P0 = _blockdiag([sp.identity(n2, format="csr")] * d + [Pi])
+    P = [P0] + Ps
+    field_off = [off0] + offs
+    seeds0 = pdg  # three seeds per cell, from the element-to-DoF map (Sec. 3.3.1)
+    patches = [make_patches(K[0], off0, d, seeds=seeds0, Bpattern=B_in)]
+    bpat = {1: B1pat}
+    patches += [make_patches(K[l], field_off[l], d, Bpattern=bpat.get(l)) for l in range(1, len(K) - 1)]
+    L = len(K)
+    cn = np.zeros(K[-1].shape[0])
+    offL = field_off[-1]
+    cn[offL[d]:offL[d + 1]] = Bp[L - 2] if L >= 2 else 1.0
+    prob = Problem(name=name, dim=d, disc=SV, nu=nu, K=K, P=P, field_off=field_off, patches=patches, b=b,
+                   coarse_null=cn, dirichlet=np.concatenate([bnd] * d + [np.zeros(ndg, bool)]),
+                   Mp=Mdg, R0p=R0p, Mcg=Mcg, mcg_bounds=(0.5, 2.0))
+    prob.lambda_A, prob.lambda_S = dlsc_bounds(K, field_off, d)
+    prob.info = dict(mesh=mesh, base=base, V=V, n2=n2, npres=ndg, Mu=Mu, Mdg=Mdg, Pi=Pi)
+    return prob
+
+
+def divergence_norm(prob, x):
+    """|| div u_h ||_L2 of the velocity part of x for a P2/P1disc problem:
+    B u = -M_dg div_h u, so ||div u_h||^2 = (B u)^T M_dg^-1 (B u)."""
+    off = prob.field_off[0]
+    d = prob.dim
+    K = prob.K[0]
+    Bu = K[off[d]:off[d + 1], : off[d]] @ x[: off[d]]
+    Mdg = prob.info["Mdg"].tocsc()
+    import scipy.sparse.linalg as spla
+    w = spla.spsolve(Mdg, Bu)
+    return float(np.sqrt(max(Bu @ w, 0.0)))

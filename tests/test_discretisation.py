@@ -106,3 +106,55 @@ def test_divergence_theorem_on_B():
     one = np.zeros(K.shape[0])
     one[off[2]:] = 1.0
     assert np.abs(K @ one).max() < 1e-13
+
+
+def test_scott_vogelius_is_pointwise_divergence_free():
+    """On the Alfeld split, div P2 lies in P1disc, so the discrete solution is
+    divergence-free to roundoff (Sec. 2.1); Taylor-Hood is not."""
+    from problems import stokes as S
+    pr = S.build_sv(8, max_levels=2)
+    off = pr.field_off[0]
+    x = direct.solve_stokes(pr.K[0], pr.b, off, 2, Mp=pr.Mp)
+    dn = S.divergence_norm(pr, x)
+    A = pr.K[0][: off[2], : off[2]]
+    energy = np.sqrt(x[: off[2]] @ (A @ x[: off[2]]))
+    assert dn < 1e-12 * energy, (dn, energy)
+    # the same measure is clearly nonzero for Taylor-Hood (div u_h in P1disc,
+    # measured with a discontinuous-pressure divergence on its own mesh)
+    import scipy.sparse.linalg as spla
+    th = stokes.build_th(M.unit_square(8), bc="noslip", rhs="manufactured", max_levels=2)
+    xo = direct.solve_stokes(th.K[0], th.b, th.field_off[0], 2, Mp=th.Mp)
+    mesh, V = th.info["mesh"], th.info["V"]
+    pdg = np.arange(3 * mesh.nc).reshape(-1, 3)
+    b1, b2 = fem.p1_basis(2), fem.p2_basis(2)
+    Bd = fem.assemble_div(mesh.x, mesh.cells, pdg, V.cell_nodes, fem.div_tensor(b1, b2, 2), pdg.size, V.n)
+    Md = fem.assemble_mass(mesh.x, mesh.cells, pdg, pdg, fem.mass_tensor(b1, b1, 2), pdg.size, pdg.size)
+    n2 = V.n
+    Bu = Bd[0] @ xo[:n2] + Bd[1] @ xo[n2:2 * n2]
+    dth = np.sqrt(Bu @ spla.spsolve(Md.tocsc(), Bu))
+    assert dth > 1e-6, dth
+
+
+def test_scott_vogelius_transfers():
+    """Pi^T M_dg Pi = Mcg (a continuous P1 function is its own projection),
+    the perturbed Alfeld mesh stays valid, and the 3-seed cell patches hold
+    the 6 P2 nodes of their cell (15 DoFs inside the domain)."""
+    from problems import stokes as S
+    pr = S.build_sv(8)
+    Pi = pr.info["Pi"]
+    assert abs(pr.R0p @ Pi - pr.Mcg).max() < 1e-15
+    base = pr.info["base"]
+    assert M.cell_measure(base.x, base.cells).min() > 0
+    pa = pr.patches[0]
+    assert np.all(pa.npres == 3) and np.diff(pa.ptr).max() == 15
+    # the projection solve: Chebyshev-Jacobi of degree 32 against a direct solve
+    from oracle.cycle import chebyshev_jacobi
+    import scipy.sparse.linalg as spla
+    rhs = np.random.default_rng(0).standard_normal(pr.Mcg.shape[0])
+    x = chebyshev_jacobi(pr.Mcg, rhs, 0.5, 2.0, 32)
+    xd = spla.spsolve(pr.Mcg.tocsc(), rhs)
+    assert np.linalg.norm(x - xd) < 1e-13 * np.linalg.norm(xd)
+    # the Wathen interval holds the spectrum of D^-1 Mcg
+    D = pr.Mcg.diagonal()
+    ev = np.linalg.eigvals(pr.Mcg.toarray() / D[:, None]).real
+    assert ev.min() >= 0.5 - 1e-12 and ev.max() <= 2.0 + 1e-12
