@@ -1140,6 +1140,36 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       if (nb < 1) return fail(STOKES_ERR_INVALID_ARG, "patch tiles do not fit on an SM");
       dp.tma_grid = std::min(dp.ntiles, nsm * nb);
     }
+    // factorisation order: blocks that fit in shared memory, then the rest
+    {
+      int optin = 0, dev = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      std::vector<int> fl, fg;
+      int msm = 0;
+      for (int si = 0; si < npatch; ++si) {
+        if (vanka_factor_smem(dim, pnv[si], max_np, T, false) <= (size_t)optin) {
+          fl.push_back(si);
+          msm = std::max(msm, pnv[si]);
+        } else {
+          fg.push_back(si);
+        }
+      }
+      dp.nfac_smem = (int)fl.size();
+      dp.max_m_fac_smem = msm;
+      fl.insert(fl.end(), fg.begin(), fg.end());
+      TRY(upload(h, &dp.fac_list, fl));
+      if (!fg.empty()) {
+        if (vanka_factor_smem(dim, max_m, max_np, T, true) > (size_t)optin)
+          return fail(STOKES_ERR_INVALID_ARG, "patch too large for the factorisation kernel");
+        char* scr = nullptr;
+        TRY(dalloc(h, &scr, (size_t)dp.fac_chunk * max_m * max_m * T));
+        dp.fac_scratch = scr;
+      }
+      const size_t apply_shm = T * (((size_t)max_m_large * (max_m_large + 1) / 2 + 3) / 4 * 4 +
+                                    (size_t)dim * max_m_large + 20) + 16;
+      dp.apply_global_a = apply_shm > (size_t)optin ? 1 : 0;
+    }
     char* facp = nullptr;
     TRY(dalloc(h, &facp, (size_t)fac * T));
     dp.fac = facp;
@@ -1604,7 +1634,7 @@ static int level_op_impl(stokes_handle* h, int32_t op, int32_t l, const double* 
     }
     case STOKES_OP_VANKA:
     case STOKES_OP_RELAX: {
-      if (!lv.has_patches) return fail(STOKES_ERR_INVALID_ARG, "level has no patches");
+      if (!lv.has_patches && !(op == STOKES_OP_RELAX && lv.dlsc)) return fail(STOKES_ERR_INVALID_ARG, "level has no patches");
       if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
       if (op == STOKES_OP_VANKA) {
         TRY(in_cast(lv.n, x, lv.ta));

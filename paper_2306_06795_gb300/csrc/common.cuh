@@ -54,7 +54,14 @@ struct DevPatches {
   int tp = 0, stages = 0, ntiles = 0, tma_grid = 0;
   int tile_fac_bytes = 0, tile_dof_bytes = 0, rhs_elems = 0, max_np_small = 0;
   int* err = nullptr;     // device error flags of the pipelines
+  // factorisation: patches whose block fits in shared memory first
+  int* fac_list = nullptr;
+  int nfac_smem = 0, max_m_fac_smem = 0, fac_chunk = 256;
+  void* fac_scratch = nullptr;  // fac_chunk * max_m^2 elements, when needed
+  int apply_global_a = 0;       // large-bin apply reads A from global memory
 };
+
+size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool global_a);
 
 size_t vanka_tma_smem(const DevPatches& p, size_t elem);
 cudaError_t vanka_prepare_kernels();

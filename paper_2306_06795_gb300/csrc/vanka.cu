@@ -11,6 +11,8 @@
 //   y_u = A^-1 b_u,  y_p = S^-1 (b_p - U^T b_u),  x_u = y_u - U y_p,
 // which is [I U^; 0 I][A^-1 0; B^ S^-1] b with U^ = -U and
 // B^ = -S^-1 B A^-1 = -S^-1 U^T (A is symmetric), so B^ needs no storage.
+#include <algorithm>
+
 #include "common.cuh"
 #include "tma.cuh"
 
@@ -44,20 +46,20 @@ __device__ __forceinline__ int bsearch_int(const int* v, int n, int key) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_vanka_factor(int npatch, int dim, int shared,
+__global__ void __launch_bounds__(128) k_vanka_factor(int nlist, const int* __restrict__ list, int dim, int shared,
     const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
     const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing,
-    int max_m, int max_np) {
+    int max_m, int max_np, T* __restrict__ gA) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int i = blockIdx.x;
-  if (i >= npatch) return;
+  if ((int)blockIdx.x >= nlist) return;
+  const int i = list[blockIdx.x];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int base = ptr[i], m = nvel[i], np = npres[i];
   const int mu = dim * m, mt = mu + np;
-  // shared layout
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* BT = A + (size_t)max_m * max_m;
+  // shared layout (the m x m block lives in global scratch when gA is given)
+  T* A = gA ? gA + (size_t)blockIdx.x * max_m * max_m : reinterpret_cast<T*>(smem_raw);
+  T* BT = reinterpret_cast<T*>(smem_raw) + (gA ? 0 : (size_t)max_m * max_m);
   T* U = BT + (size_t)dim * max_m * max_np;
   T* colk = U + (size_t)dim * max_m * max_np;
   T* rowk = colk + max_m;
@@ -178,17 +180,39 @@ __global__ void __launch_bounds__(128) k_vanka_factor(int npatch, int dim, int s
   }
 }
 
+size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool global_a) {
+  return elem * ((global_a ? 0 : (size_t)max_m * max_m) + 2 * (size_t)dim * max_m * max_np + 2 * max_m +
+                 kMaxNp * kMaxNp + 4) +
+         sizeof(int) * ((size_t)dim * max_m + max_np) + 16;
+}
+
+// Factorise the patches in `list`: patches whose m x m block fits in shared
+// memory in one launch; the others (coarse 3D levels) in chunks of at most
+// `chunk` patches with the block in the global scratch gA.
 template <typename T>
 cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st) {
   if (p.npatch == 0) return cudaSuccess;
   const int dm = p.dim;
-  size_t shm = sizeof(T) * ((size_t)p.max_m * p.max_m + 2 * (size_t)dm * p.max_m * p.max_np + 2 * p.max_m +
-                            kMaxNp * kMaxNp + 4) +
-               sizeof(int) * ((size_t)dm * p.max_m + p.max_np) + 16;
-  k_vanka_factor<T><<<p.npatch, 128, shm, st>>>(p.npatch, dm, p.shared, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac), nsingular,
-                                                p.max_m, p.max_np);
-  return cudaGetLastError();
+  if (p.nfac_smem > 0) {
+    const size_t shm = vanka_factor_smem(dm, p.max_m_fac_smem, p.max_np, sizeof(T), false);
+    k_vanka_factor<T><<<p.nfac_smem, 128, shm, st>>>(p.nfac_smem, p.fac_list, dm, p.shared, p.ptr, p.dof, p.nvel,
+                                                     p.npres, p.foff, K.rowptr, K.col, K.v64,
+                                                     reinterpret_cast<T*>(p.fac), nsingular, p.max_m_fac_smem,
+                                                     p.max_np, (T*)nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int nglob = p.npatch - p.nfac_smem;
+  for (int c0 = 0; c0 < nglob; c0 += p.fac_chunk) {
+    const int cnt = std::min(p.fac_chunk, nglob - c0);
+    const size_t shm = vanka_factor_smem(dm, p.max_m, p.max_np, sizeof(T), true);
+    k_vanka_factor<T><<<cnt, 128, shm, st>>>(cnt, p.fac_list + p.nfac_smem + c0, dm, p.shared, p.ptr, p.dof, p.nvel,
+                                             p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac),
+                                             nsingular, p.max_m, p.max_np, reinterpret_cast<T*>(p.fac_scratch));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 template cudaError_t vanka_factor<float>(const DevPatches&, const DevCSR&, int*, cudaStream_t);
 template cudaError_t vanka_factor<double>(const DevPatches&, const DevCSR&, int*, cudaStream_t);
@@ -289,7 +313,7 @@ template <typename T, typename TR, int DIM>
 __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* __restrict__ list,
     const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, int shared, const T* __restrict__ fac,
-    const TR* __restrict__ r, T* __restrict__ yp, int max_m) {
+    const TR* __restrict__ r, T* __restrict__ yp, int max_m, int global_a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NT = 128, RPT = 4;  // rows per thread: m <= 512
   const int bi = blockIdx.x;
@@ -300,15 +324,16 @@ __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* _
   const int mu = DIM * m, mt = mu + np;
   const int64_t fo = foff[i];
   const int pk = m * (m + 1) / 2;
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* b = A + ((max_m * (max_m + 1) / 2 + 3) & ~3);
+  T* As = reinterpret_cast<T*>(smem_raw);
+  T* b = As + (global_a ? 0 : ((max_m * (max_m + 1) / 2 + 3) & ~3));
   T* red = b + DIM * max_m + kMaxNp;  // [4 warps][kMaxNp]
   for (int k = tid; k < mt; k += NT) b[k] = T(r[dof[base + k]]);
   T yu[DIM][RPT];
   const int nblk = shared ? 1 : DIM;
   for (int cb = 0; cb < nblk; ++cb) {
+    const T* A = global_a ? fac + fo + (int64_t)cb * padded_pk<T>(m) : As;
     __syncthreads();
-    group_copy(A, fac + fo + (int64_t)cb * padded_pk<T>(m), pk, tid, NT);
+    if (!global_a) group_copy(As, fac + fo + (int64_t)cb * padded_pk<T>(m), pk, tid, NT);
     __syncthreads();
     const int c0 = shared ? 0 : cb, c1 = shared ? DIM : cb + 1;
 #pragma unroll
@@ -607,14 +632,15 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
   }
   if (p.nlarge > 0) {
     const int mm = p.max_m_large;
-    size_t shm = sizeof(T) * (((size_t)mm * (mm + 1) / 2 + 3) / 4 * 4 + (size_t)p.dim * mm + kMaxNp + 4 * kMaxNp) + 16;
+    const int ga = p.apply_global_a;
+    size_t shm = sizeof(T) * ((ga ? 0 : ((size_t)mm * (mm + 1) / 2 + 3) / 4 * 4) + (size_t)p.dim * mm + kMaxNp + 4 * kMaxNp) + 16;
     cudaError_t e;
     if (p.dim == 2) {
       k_vanka_apply_cta<T, TR, 2><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm);
+                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga);
     } else {
       k_vanka_apply_cta<T, TR, 3><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm);
+                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
