@@ -225,6 +225,25 @@ int stokes_time_kernel(stokes_handle* h, int32_t which, int32_t level, int32_t r
                        double* avg_ms, double* bytes);
 int64_t stokes_kernel_launches(const stokes_handle* h);
 
+/* y = M_l^-1 x on level l (the sum of weighted Vanka patch solves, the
+ * same result as stokes_level_op with STOKES_OP_VANKA) without allocating
+ * any device memory during the call.  It is meant for callers that cannot
+ * call cudaMalloc while they run (a fixed device-memory budget, or a
+ * context in which allocation is not permitted); they create and factorise
+ * the handle beforehand and pass the input and output vectors (device FP64,
+ * the level-l size).  The paper has no counterpart: this is an
+ * implementation service.  Its scratch (the cycle-precision copy of x, the
+ * patch-major solutions and the result before conversion) is one fixed
+ * 32 MiB device array inside the library, held by every GPU that loads the
+ * library until the process exits; a level needing more returns
+ * STOKES_ERR_INVALID_ARG with the sizes in stokes_last_error().  Every call
+ * shares that array and overwrites it completely before reading it, so no
+ * part must start at zero; calls that overlap on the GPU (from several
+ * threads or streams) race on it.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Queued on the handle's stream, asynchronous. */
+int stokes_vanka_noalloc(stokes_handle* h, int32_t level, const double* x_dev, double* y_dev);
+
 /* Release all device memory of the handle (NULL is allowed). */
 void stokes_destroy(stokes_handle* h);
 

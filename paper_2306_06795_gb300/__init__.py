@@ -34,7 +34,7 @@ STOKES_KERNEL_VANKA_APPLY, STOKES_KERNEL_SCATTER, STOKES_KERNEL_SPMV, STOKES_KER
 EXPORTS = ["stokes_setup", "stokes_factor_patches", "stokes_vcycle", "stokes_fgmres_solve",
            "stokes_fgmres_solve_host", "stokes_level_op", "stokes_num_levels", "stokes_level_size",
            "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_time_kernel",
-           "stokes_kernel_launches", "stokes_destroy",
+           "stokes_kernel_launches", "stokes_vanka_noalloc", "stokes_destroy",
            "stokes_status_string", "stokes_last_error"]
 
 
@@ -96,6 +96,7 @@ def _load():
                                        C.POINTER(C.c_double)]
     lib.stokes_kernel_launches.argtypes = [vp]
     lib.stokes_kernel_launches.restype = C.c_int64
+    lib.stokes_vanka_noalloc.argtypes = [vp, C.c_int32, vp, vp]
     lib.stokes_destroy.argtypes = [vp]
     lib.stokes_destroy.restype = None
     lib.stokes_status_string.argtypes = [C.c_int]
@@ -310,6 +311,12 @@ def stokes_time_kernel(h, which, level, reps=10):
 
 def stokes_kernel_launches(h):
     return lib.stokes_kernel_launches(h.ptr)
+
+
+def stokes_vanka_noalloc(h, level, x, y):
+    """y = M_level^-1 x with the library's fixed scratch (no device
+    allocation during the call); see include/stokes_dcamg.h."""
+    _check(lib.stokes_vanka_noalloc(h.ptr, level, _dptr(x), _dptr(y)), "stokes_vanka_noalloc")
 
 
 def stokes_destroy(h):

@@ -706,6 +706,24 @@ int join_out(stokes_handle* h) {
 }
 }  // namespace
 
+// Level data the no-allocation Vanka entry point needs (noalloc.cu).
+namespace sd {
+int vanka_level_view(stokes_handle* h, int l, VankaView* v) {
+  if (!h || l < 0 || l >= h->L) return fail(STOKES_ERR_INVALID_ARG, "level out of range");
+  Level& lv = h->lv[l];
+  if (!lv.has_patches) return fail(STOKES_ERR_INVALID_ARG, "level has no Vanka patches");
+  if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
+  v->pat = &lv.pat;
+  v->n = lv.n;
+  v->fp32 = h->prec == STOKES_FP32;
+  v->st = h->st;
+  return STOKES_OK;
+}
+int stream_join_in(stokes_handle* h) { return join_in(h); }
+int stream_join_out(stokes_handle* h) { return join_out(h); }
+int set_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace sd
+
 // ------------------------------------------------------------- C ABI
 extern "C" {
 

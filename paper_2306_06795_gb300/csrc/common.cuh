@@ -63,6 +63,20 @@ struct DevPatches {
 
 size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool global_a);
 
+}  // namespace sd
+struct stokes_handle;
+namespace sd {
+struct VankaView {
+  const DevPatches* pat;
+  int64_t n;
+  bool fp32;
+  cudaStream_t st;
+};
+int vanka_level_view(stokes_handle* h, int l, VankaView* v);
+int stream_join_in(stokes_handle* h);
+int stream_join_out(stokes_handle* h);
+int set_error(int code, const char* msg);
+
 size_t vanka_tma_smem(const DevPatches& p, size_t elem);
 cudaError_t vanka_prepare_kernels();
 int vanka_tma_blocks_per_sm(const DevPatches& p, size_t elem);
