@@ -91,3 +91,22 @@ class VankaLevel:
     def sweep(self, K, x, b, omega):
         """One stationary damped sweep x <- x + omega M^-1 (b - K x)."""
         return x + omega * self.apply(b - K @ x)
+
+
+def sampled_apply(K, patches, r, dofs):
+    """(M^-1 r)[dofs] of Eq. vanka computed from only the patches that hold
+    the sampled DoFs, each by a dense LU solve: a check of a full-size Vanka
+    application at a handful of entries."""
+    K = K.tocsr()
+    lists = patch_lists(patches)
+    W = partition_of_unity(patches, K.shape[0])
+    want = {int(d): 0.0 for d in dofs}
+    for ix in lists:
+        hit = [int(g) for g in ix if int(g) in want]
+        if not hit:
+            continue
+        y = np.linalg.solve(K[ix][:, ix].toarray(), r[ix])
+        pos = {int(g): k for k, g in enumerate(ix)}
+        for g in hit:
+            want[g] += y[pos[g]]
+    return np.array([W[int(d)] * want[int(d)] for d in dofs])

@@ -141,6 +141,7 @@ struct stokes_handle {
   int64_t launches = 0;       // kernels launched so far
   int cycle_launches = -1;    // kernels in one DC cycle (from the ledger)
   std::vector<void*> allocs;
+  std::vector<int*> err_flags;  // device error flags of every bulk-copy pipeline
 };
 
 // ------------------------------------------------------------- utilities
@@ -176,18 +177,64 @@ int choose_tpr(int64_t nnz, int nrows) {
   return 32;
 }
 
+// Operators with at least this many rows use the bulk-copy SpMV.
+constexpr int kTmaRows = 32768;
+constexpr int kTileNnz = 2048, kTileRows = 512;
+
 int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
   d.nrows = c.nrows;
   d.ncols = c.ncols;
   d.nnz = (int64_t)c.col.size();
-  TRY(upload(h, &d.rowptr, c.rowptr));
-  TRY(upload(h, &d.col, c.col));
-  TRY(upload(h, &d.v64, c.val));
+  // arrays padded so that 16-byte-widened tile copies stay inside them
+  std::vector<int> rp(c.rowptr);
+  rp.resize(rp.size() + 8, rp.back());
+  std::vector<int> cl(c.col);
+  cl.resize(cl.size() + 8, 0);
+  std::vector<double> v(c.val);
+  v.resize(v.size() + 8, 0.0);
+  TRY(upload(h, &d.rowptr, rp));
+  TRY(upload(h, &d.col, cl));
+  TRY(upload(h, &d.v64, v));
   if (h->prec == STOKES_FP32) {
-    std::vector<float> v32(c.val.begin(), c.val.end());
+    std::vector<float> v32(v.begin(), v.end());
     TRY(upload(h, &d.v32, v32));
   }
   d.tpr = choose_tpr(d.nnz, d.nrows);
+  // tiles for the bulk-copy SpMV
+  int maxrow = 0;
+  for (int i = 0; i < c.nrows; ++i) maxrow = std::max(maxrow, c.rowptr[i + 1] - c.rowptr[i]);
+  if (c.nrows >= kTmaRows && maxrow <= kTileNnz - 8) {
+    std::vector<int> trow{0};
+    int vb = 0, vb32 = 0, cb = 0, pb = 0;
+    int r = 0;
+    while (r < c.nrows) {
+      int r1 = r;
+      while (r1 < c.nrows && r1 - r < kTileRows && c.rowptr[r1 + 1] - c.rowptr[r] <= kTileNnz - 8) ++r1;
+      trow.push_back(r1);
+      const int n0 = c.rowptr[r], n1 = c.rowptr[r1];
+      vb = std::max(vb, ((n1 + 1) / 2 * 2 - n0 / 2 * 2) * 8);
+      vb32 = std::max(vb32, ((n1 + 3) / 4 * 4 - n0 / 4 * 4) * 4);
+      cb = std::max(cb, ((n1 + 3) / 4 * 4 - n0 / 4 * 4) * 4);
+      pb = std::max(pb, ((r1 + 1 + 3) / 4 * 4 - r / 4 * 4) * 4);
+      r = r1;
+    }
+    d.ntiles = (int)trow.size() - 1;
+    d.tile_val_bytes = vb;
+    d.tile_val_bytes32 = vb32;
+    d.tile_col_bytes = cb;
+    d.tile_rp_bytes = pb;
+    TRY(upload(h, &d.trow, trow));
+    TRY(dalloc(h, &d.err, 1));
+    CK(cudaMemset(d.err, 0, sizeof(int)));
+    h->err_flags.push_back(d.err);
+    int nsm = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int b32 = spmv_tma_blocks_per_sm(d, false), b64 = spmv_tma_blocks_per_sm(d, true);
+    if (b32 < 1 || b64 < 1) return fail(STOKES_ERR_INVALID_ARG, "SpMV tiles do not fit on an SM");
+    d.tma_grid32 = std::min(d.ntiles, nsm * b32);
+    d.tma_grid64 = std::min(d.ntiles, nsm * b64);
+  }
   return STOKES_OK;
 }
 
@@ -506,6 +553,10 @@ int cheb_run(stokes_handle* h, const DevCSR& M, const T* mval, const DevCSR* BT,
 }
 
 }  // namespace
+
+namespace {
+int check_pipeline_errors(stokes_handle* h);
+}
 
 // ------------------------------------------------------------- the cycle
 namespace {
@@ -1148,6 +1199,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     TRY(upload(h, &dp.meta, meta));
     TRY(dalloc(h, &dp.err, 1));
     CK(cudaMemset(dp.err, 0, sizeof(int)));
+    h->err_flags.push_back(dp.err);
     if (nsmall > 0) {
       const size_t shm = vanka_tma_smem(dp, T);
       if (shm > 220 * 1024) return fail(STOKES_ERR_INVALID_ARG, "patch tiles exceed shared memory");
@@ -1276,6 +1328,7 @@ int stokes_setup(const stokes_problem* const* probs, int32_t ninstances, const s
     }
   }
   e = vanka_prepare_kernels();
+  if (e == cudaSuccess) e = spmv_prepare_kernels();
   if (e != cudaSuccess) {
     stokes_destroy(h);
     return fail(STOKES_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
@@ -1346,12 +1399,11 @@ namespace {
 // The bulk-copy pipelines record a flag instead of waiting forever; a set
 // flag means a result is unusable.
 int check_pipeline_errors(stokes_handle* h) {
-  for (int l = 0; l < h->L; ++l) {
-    if (!h->lv[l].has_patches) continue;
+  for (int* f : h->err_flags) {
     int e = 0;
-    CK(cudaMemcpyAsync(&e, h->lv[l].pat.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&e, f, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    if (e) return fail(STOKES_ERR_CUDA, "a patch pipeline wait timed out on level " + std::to_string(l));
+    if (e) return fail(STOKES_ERR_CUDA, "a bulk-copy pipeline wait timed out (flag " + std::to_string(e) + ")");
   }
   return STOKES_OK;
 }
@@ -1608,6 +1660,7 @@ extern "C" int stokes_level_op(stokes_handle* h, int32_t op, int32_t l, const do
   if (!h || l < 0 || l >= h->L || !y) return fail(STOKES_ERR_INVALID_ARG, "level_op arguments");
   TRY(join_in(h));
   TRY(level_op_impl(h, op, l, x, b, y));
+  TRY(check_pipeline_errors(h));
   return join_out(h);
 }
 

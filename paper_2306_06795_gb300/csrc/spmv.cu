@@ -63,6 +63,7 @@ static cudaError_t launch_mode(const DevCSR& A, const TA* val, const TX* x, cons
 template <typename TA, typename TX, typename TB, typename TY, typename TACC>
 cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y, int mode, double s0,
                  double s1, const uint8_t* kind, cudaStream_t st) {
+  if (A.ntiles > 0) return spmv_tma<TA, TX, TB, TY, TACC>(A, val, x, b, y, mode, s0, s1, kind, st);
   switch (A.tpr) {
     case 2: return launch_mode<TA, TX, TB, TY, TACC, 2>(A, val, x, b, y, mode, s0, s1, kind, st);
     case 4: return launch_mode<TA, TX, TB, TY, TACC, 4>(A, val, x, b, y, mode, s0, s1, kind, st);

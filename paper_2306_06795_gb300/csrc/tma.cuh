@@ -7,7 +7,7 @@ namespace sd {
 
 // Upper bound on mbarrier polls before a wait gives up (each poll may
 // suspend the thread for a short, hardware-chosen time).
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

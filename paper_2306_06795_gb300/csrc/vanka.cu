@@ -686,7 +686,15 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int64_t n, const int* __r
   if (j >= n) return;
   const int b = tptr[j], e = tptr[j + 1];
   T s = T(0);
-  for (int k = b; k < e; ++k) s += yp[tslot[k]];
+  // slots of the DoF in ascending patch order; four independent loads in
+  // flight, summed in that order
+  for (int k = b; k < e; k += 4) {
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = k + u < e ? yp[tslot[k + u]] : T(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += v[u];
+  }
   const T upd = e > b ? omega * s / T(e - b) : T(0);
   if (MODE == 0) x[j] = upd;
   else if (MODE == 1) x[j] += upd;

@@ -13,7 +13,6 @@ from . import mesh as M, stokes
 
 # cycle parameters ------------------------------------------------------------
 TH2D_VANKA = dict(schedule=0, nu1=1, nu2=1, eta_u=0.75, eta_p=0.75, omega=0.55)
-TH3D_VANKA = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=1.0, omega=0.55)
 SV2D_VANKA = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=2.68, omega0=0.78, omega=0.55)
 SV2D_VANKA_DLSC = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=2.96, omega0=0.87, omega=1.0)
 
@@ -40,3 +39,30 @@ def c3(n=128):
 def sv_vanka_dlsc(nlevels):
     """Vanka on level 0, DLSC on levels >= 1 (Table p2p1disc_params)."""
     return dict(SV2D_VANKA_DLSC, relax=[0] + [1] * (nlevels - 2))
+
+
+# 3D: eta = 1.00 (Sec. 4.1 table, 3D structured Vanka); omega from the
+# brute-force search on the 6^3 cavity (0.70: 10 iterations; 0.55: 11)
+TH3D_VANKA = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=1.0, omega=0.70)
+
+
+def c4(n=32):
+    """3D Taylor-Hood P2/P1, unit cube n^3 hexes split into 6 Kuhn tetrahedra,
+    lid-driven cavity (u = (1,0,0) strictly inside the top face), f = 0."""
+    return stokes.build_th(M.unit_cube(n), nu=1.0, bc="lid", rhs="zero", name=f"C4 TH3D {n}^3 lid")
+
+
+def c5_instances(count=64, lo=32, hi=192, seed=5000):
+    """Batched workload: `count` independent 2D Taylor-Hood problems on n x n
+    unit squares, n ~ U{lo..hi}, nu = 10^U(-2, 2), b_u ~ N(0,1) on free rows,
+    b_p = 0, no-slip walls; instance k draws from seed + k."""
+    from . import rng
+    ns = rng.integers(seed, count, lo, hi)
+    lognu = rng.uniform(seed + 10**6, count, -2.0, 2.0)
+    return [(int(ns[k]), float(10.0 ** lognu[k]), seed + k) for k in range(count)]
+
+
+def c5(count=64, lo=32, hi=192, seed=5000):
+    return [stokes.build_th(M.unit_square(n), nu=nu, bc="noslip", rhs="random_b", seed=s,
+                            name=f"C5[{k}] TH2D {n}^2 nu={nu:.3g}")
+            for k, (n, nu, s) in enumerate(c5_instances(count, lo, hi, seed))]

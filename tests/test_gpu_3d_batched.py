@@ -1,0 +1,128 @@
+"""GPU parity in 3D (Taylor-Hood on Kuhn tetrahedra, 196-DoF patches,
+coarse patches through the global-memory factor and apply paths) and for
+batched instances, against the FP64 oracle through the C ABI; the full
+32^3 cavity is checked on sampled Vanka entries and by solve properties."""
+import numpy as np
+import pytest
+
+from oracle import krylov, vanka
+from problems import configs, mesh as M, stokes
+from tests.helpers import make_oracle, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sd():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2306_06795_gb300 as sd
+    return sd
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def cube():
+    return stokes.build_th(M.unit_cube(4), bc="lid")
+
+
+@pytest.mark.parametrize("relax", ["vanka", "dlsc"])
+def test_3d_cycle_fp64_matches_oracle(sd, cube, relax):
+    prm = dict(configs.TH3D_VANKA, cheb_deg=(4, 4, 16))
+    if relax == "dlsc":
+        prm["relax"] = [0] + [1] * (cube.nlevels - 2)
+    h = sd.stokes_setup(cube, dict(prm, precision=sd.STOKES_FP64))
+    sd.stokes_factor_patches(h)
+    o = make_oracle(cube, prm)
+    r = np.random.default_rng(31).standard_normal(cube.b.size)
+    z = torch.empty(r.size, dtype=torch.float64, device="cuda")
+    sd.stokes_vcycle(h, dev(r), z)
+    assert rel(host(z), o.apply(r)) < 1e-12
+
+
+def test_3d_large_coarse_patches_fp64(sd):
+    """A 8^3 cavity has coarse patches of several hundred DoFs (global-memory
+    factorisation and apply)."""
+    pr = stokes.build_th(M.unit_cube(8), bc="lid")
+    assert max(np.diff(p.ptr).max() for p in pr.patches) > 300
+    prm = dict(configs.TH3D_VANKA)
+    h = sd.stokes_setup(pr, dict(prm, precision=sd.STOKES_FP64))
+    sd.stokes_factor_patches(h)
+    o = make_oracle(pr, prm)
+    r = np.random.default_rng(32).standard_normal(pr.b.size)
+    z = torch.empty(r.size, dtype=torch.float64, device="cuda")
+    sd.stokes_vcycle(h, dev(r), z)
+    assert rel(host(z), o.apply(r)) < 1e-12
+
+
+def test_3d_fgmres_fp32_within_two_iterations(sd, cube):
+    prm = dict(configs.TH3D_VANKA)
+    o = make_oracle(cube, prm)
+    _, its_o, _ = krylov.fgmres(cube.K[0], cube.b, o.apply, rtol=1e-8, restart=30, maxit=200)
+    h = sd.stokes_setup(cube, dict(prm, precision=sd.STOKES_FP32))
+    sd.stokes_factor_patches(h)
+    x = torch.zeros(cube.b.size, dtype=torch.float64, device="cuda")
+    rc, info = sd.stokes_fgmres_solve(h, dev(cube.b), x, rtol=1e-8, restart=30, maxit=200)
+    assert rc == sd.STOKES_OK and info[0][2] <= 1e-8
+    assert abs(info[0][0] - its_o) <= 2
+
+
+@pytest.fixture(scope="module")
+def c4():
+    return configs.c4()
+
+
+def test_c4_full_size_sampled_vanka_and_solve(sd, c4):
+    prm = dict(configs.TH3D_VANKA)
+    h64 = sd.stokes_setup(c4, dict(prm, precision=sd.STOKES_FP64))
+    assert sd.stokes_factor_patches(h64) == 0
+    rng = np.random.default_rng(33)
+    for l in (0, 1, 2):
+        n = c4.K[l].shape[0]
+        r = rng.standard_normal(n)
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        sd.stokes_level_op(h64, sd.STOKES_OP_VANKA, l, dev(r), None, y)
+        covered = np.nonzero(np.bincount(c4.patches[l].dof, minlength=n))[0]
+        dofs = rng.choice(covered, size=40, replace=False)
+        ref = vanka.sampled_apply(c4.K[l], c4.patches[l], r, dofs)
+        assert rel(host(y)[dofs], ref) < 1e-11, l
+    # FP32 and FP64 preconditioned solves reach 1e-8 within +-2 iterations
+    b = dev(c4.b)
+    its = {}
+    xs = {}
+    for prec in (sd.STOKES_FP64, sd.STOKES_FP32):
+        h = h64 if prec == sd.STOKES_FP64 else sd.stokes_setup(c4, dict(prm, precision=prec))
+        if prec == sd.STOKES_FP32:
+            sd.stokes_factor_patches(h)
+        x = torch.zeros_like(b)
+        rc, info = sd.stokes_fgmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=400)
+        assert rc == sd.STOKES_OK and info[0][2] <= 1e-8
+        its[prec] = info[0][0]
+        xs[prec] = host(x)
+    assert abs(its[sd.STOKES_FP32] - its[sd.STOKES_FP64]) <= 2
+    assert rel(xs[sd.STOKES_FP32], xs[sd.STOKES_FP64]) < 1e-5
+
+
+def test_batched_small_c5_like_matches_oracle(sd):
+    inst = configs.c5_instances(count=6, lo=6, hi=20, seed=777)
+    probs = [stokes.build_th(M.unit_square(n), nu=nu, bc="noslip", rhs="random_b", seed=s) for n, nu, s in inst]
+    prm = dict(configs.TH2D_VANKA)
+    h = sd.stokes_setup(probs, dict(prm, precision=sd.STOKES_FP64))
+    sd.stokes_factor_patches(h)
+    r = np.concatenate([np.random.default_rng(k).standard_normal(p.b.size) for k, p in enumerate(probs)])
+    z = torch.empty(r.size, dtype=torch.float64, device="cuda")
+    sd.stokes_vcycle(h, dev(r), z)
+    zh = host(z)
+    o = 0
+    for p in probs:
+        n = p.b.size
+        assert rel(zh[o:o + n], make_oracle(p, prm).apply(r[o:o + n])) < 1e-12
+        o += n
