@@ -332,6 +332,9 @@ def run_profile(args):
     z = torch.empty_like(r)
     for _ in range(args.profile_cycles):
         sd.stokes_vcycle(h, r, z)
+    if args.profile_solve:
+        with torch.cuda.stream(stream):
+            sd.stokes_fgmres_solve(h, r, z.zero_(), rtol=1e-8, restart=30, maxit=600)
     torch.cuda.synchronize()
 
 
@@ -344,12 +347,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-cycles", type=int, default=0,
                     help="profiling driver: set up, factorise and run this many DC cycles, print nothing")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="profiling driver: set up, factorise and run one FP32-preconditioned solve")
     ap.add_argument("--ref-iters", type=int, default=34,
                     help="iterations a full oracle solve takes (scales the reference sample)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.profile_cycles:
+    elif args.profile_cycles or args.profile_solve:
         run_profile(args)
     else:
         run_gpu(args)

@@ -1104,14 +1104,19 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       shared = shared && sh;
     }
     if (onv.empty()) continue;
-    // storage order: patches with m <= 32 first (TMA tiles), then the rest
+    // storage order: the bulk-copy bins by m (<= 8, 32, 64, 96), then the rest
     const int npatch = (int)onv.size();
     std::vector<int> order;
-    for (int i = 0; i < npatch; ++i)
-      if (onv[i] <= 32) order.push_back(i);
+    int bin_start[kTmaBins + 1];
+    for (int b = 0; b < kTmaBins; ++b) {
+      bin_start[b] = (int)order.size();
+      for (int i = 0; i < npatch; ++i)
+        if (vanka_tma_bin_of(onv[i]) == b) order.push_back(i);
+    }
+    bin_start[kTmaBins] = (int)order.size();
     const int nsmall = (int)order.size();
     for (int i = 0; i < npatch; ++i)
-      if (onv[i] > 32) order.push_back(i);
+      if (vanka_tma_bin_of(onv[i]) < 0) order.push_back(i);
     std::vector<int> pptr{0}, pdof, pnv, pnp, small, large, stor(npatch);
     std::vector<int64_t> foff;
     int64_t fac = 0;
@@ -1132,7 +1137,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       (si < nsmall ? small : large).push_back(si);
       max_m = std::max(max_m, (int)m);
       max_np = std::max(max_np, (int)np);
-      if (m > 32) max_m_large = std::max(max_m_large, (int)m);
+      if (si >= nsmall) max_m_large = std::max(max_m_large, (int)m);
       else max_np_small = std::max(max_np_small, (int)np);
     }
     foff.push_back(fac);  // sentinel
@@ -1159,20 +1164,28 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     dp.max_m = max_m;
     dp.max_np = max_np;
     dp.max_m_large = max_m_large;
-    dp.max_np_small = max_np_small;
     dp.fac_elems = fac;
     dp.nslots = (int64_t)pdof.size();
-    // tiles: about 8 KB of factors per stage, 3 stages
-    if (nsmall > 0) {
+    // bulk-copy tiles per bin: about 8 KB of factors per stage (at least one
+    // patch per consumer lane group), 3 stages
+    dp.stages = 3;
+    for (int b = 0; b < kTmaBins; ++b) {
+      TmaBin& bn = dp.bins[b];
+      bn.start = bin_start[b];
+      bn.count = bin_start[b + 1] - bin_start[b];
+      if (bn.count == 0) continue;
       int64_t maxblk = 0;
-      for (int si = 0; si < nsmall; ++si) maxblk = std::max(maxblk, (foff[si + 1] - foff[si]) * (int64_t)T);
-      int tp = (int)std::max<int64_t>(4, std::min<int64_t>(64, 8192 / std::max<int64_t>(maxblk, 1)));
-      dp.tp = tp;
-      dp.stages = 3;
-      dp.ntiles = (nsmall + tp - 1) / tp;
+      for (int si = bn.start; si < bn.start + bn.count; ++si) {
+        maxblk = std::max(maxblk, (foff[si + 1] - foff[si]) * (int64_t)T);
+        bn.max_np = std::max(bn.max_np, pnp[si]);
+      }
+      const int ppw = b == 0 ? 4 : (b == 1 ? 2 : 1);  // patches per warp at a time
+      const int tp = (int)std::max<int64_t>(4 * ppw, std::min<int64_t>(64, 8192 / std::max<int64_t>(maxblk, 1)));
+      bn.tp = tp;
+      bn.ntiles = (bn.count + tp - 1) / tp;
       int64_t fb = 0, db = 0, rh = 0;
-      for (int t = 0; t < dp.ntiles; ++t) {
-        const int i0 = t * tp, i1 = std::min(i0 + tp, nsmall);
+      for (int t = 0; t < bn.ntiles; ++t) {
+        const int i0 = bn.start + t * tp, i1 = std::min(i0 + tp, bn.start + bn.count);
         fb = std::max(fb, (foff[i1] - foff[i0]) * (int64_t)T);
         db = std::max<int64_t>(db, (int64_t)(((pptr[i1] + 3) & ~3) - (pptr[i0] & ~3)) * 4);
         const int cnt = i1 - i0, per = (cnt + 3) / 4;
@@ -1181,9 +1194,9 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
           rh = std::max<int64_t>(rh, pptr[j1] - pptr[j0]);
         }
       }
-      dp.tile_fac_bytes = (int)fb;
-      dp.tile_dof_bytes = (int)db;
-      dp.rhs_elems = (int)((rh + 3) / 4 * 4);
+      bn.fac_bytes = (int)fb;
+      bn.dof_bytes = (int)db;
+      bn.rhs_elems = (int)((rh + 3) / 4 * 4);
     }
     std::vector<int> pdof_pad(pdof);
     pdof_pad.resize(pdof.size() + 8, 0);  // bulk copies may read up to 16 bytes past the last list
@@ -1200,15 +1213,20 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     TRY(dalloc(h, &dp.err, 1));
     CK(cudaMemset(dp.err, 0, sizeof(int)));
     h->err_flags.push_back(dp.err);
-    if (nsmall > 0) {
-      const size_t shm = vanka_tma_smem(dp, T);
-      if (shm > 220 * 1024) return fail(STOKES_ERR_INVALID_ARG, "patch tiles exceed shared memory");
-      const int nb = vanka_tma_blocks_per_sm(dp, T);
+    {
       int nsm = 0, dev = 0;
       CK(cudaGetDevice(&dev));
       CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-      if (nb < 1) return fail(STOKES_ERR_INVALID_ARG, "patch tiles do not fit on an SM");
-      dp.tma_grid = std::min(dp.ntiles, nsm * nb);
+      for (int b = 0; b < kTmaBins; ++b) {
+        TmaBin& bn = dp.bins[b];
+        if (bn.count == 0) continue;
+        if (vanka_tma_smem(dp, bn, T) > 220 * 1024)
+          return fail(STOKES_ERR_INVALID_ARG, "patch tiles exceed shared memory");
+        const int nb = vanka_tma_blocks_per_sm(dp, bn, b, T);
+        if (nb < 1) return fail(STOKES_ERR_INVALID_ARG, "patch tiles do not fit on an SM");
+        bn.grid = std::min(bn.ntiles, nsm * nb);
+      }
+      dp.use_tma = nsmall > 0;
     }
     // factorisation order: blocks that fit in shared memory, then the rest
     {

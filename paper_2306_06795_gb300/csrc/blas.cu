@@ -219,22 +219,30 @@ cudaError_t multidot_partial(int nchunks, const int64_t* cbeg, const int64_t* ce
   return cudaGetLastError();
 }
 
-__global__ void k_multidot_finish(int nseg, const int* __restrict__ sc_beg, const int* __restrict__ sc_end,
-                                  int ncols, const double* __restrict__ partial, int ldp, double* __restrict__ h,
-                                  int ldh, int accumulate) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per (segment, column): lane l sums chunks l, l+32, ... of the
+// segment in order, then a fixed shuffle tree combines the lanes.
+__global__ void __launch_bounds__(128) k_multidot_finish(int nseg, const int* __restrict__ sc_beg,
+                                                         const int* __restrict__ sc_end, int ncols,
+                                                         const double* __restrict__ partial, int ldp,
+                                                         double* __restrict__ h, int ldh, int accumulate) {
+  const int idx = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (idx >= nseg * ncols) return;
   const int s = idx / ncols, k = idx - s * ncols;
   double v = 0.0;
-  for (int c = sc_beg[s]; c < sc_end[s]; ++c) v += partial[(int64_t)c * ldp + k];
-  if (accumulate) h[s * ldh + k] += v;
-  else h[s * ldh + k] = v;
+  for (int c = sc_beg[s] + lane; c < sc_end[s]; c += 32) v += partial[(int64_t)c * ldp + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    if (accumulate) h[s * ldh + k] += v;
+    else h[s * ldh + k] = v;
+  }
 }
 cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int ncols, const double* partial,
                             int ldp, double* h, int ldh, int accumulate, cudaStream_t st) {
   const int tot = nseg * ncols;
   if (tot == 0) return cudaSuccess;
-  k_multidot_finish<<<(tot + 127) / 128, 128, 0, st>>>(nseg, sc_beg, sc_end, ncols, partial, ldp, h, ldh, accumulate);
+  k_multidot_finish<<<(tot + 3) / 4, 128, 0, st>>>(nseg, sc_beg, sc_end, ncols, partial, ldp, h, ldh, accumulate);
   return cudaGetLastError();
 }
 

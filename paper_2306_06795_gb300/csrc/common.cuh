@@ -43,6 +43,14 @@ template <typename TA, typename TX, typename TB, typename TY, typename TACC>
 cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y, int mode,
                  double s0, double s1, const uint8_t* kind, cudaStream_t st);
 
+// A bin of patches solved by the bulk-copy kernel: storage patches
+// [start, start + count), all with m in the bin's range.
+constexpr int kTmaBins = 4;
+struct TmaBin {
+  int start = 0, count = 0, tp = 0, ntiles = 0, grid = 0;
+  int fac_bytes = 0, dof_bytes = 0, rhs_elems = 0, max_np = 0;
+};
+
 // Vanka patch data of one level on the device.
 struct DevPatches {
   int npatch = 0;
@@ -63,10 +71,11 @@ struct DevPatches {
   int* tptr = nullptr;    // [n+1] transpose map: DoF -> patch-major slots
   int* tslot = nullptr;
   int64_t nslots = 0;
-  // TMA tiles of the small bin (storage order: small patches first)
+  // bulk-copy bins (storage order: bins by m, then the CTA-per-patch rest)
   int4* meta = nullptr;   // [npatch] {ptr, m | np << 16, foff lo, foff hi}
-  int tp = 0, stages = 0, ntiles = 0, tma_grid = 0;
-  int tile_fac_bytes = 0, tile_dof_bytes = 0, rhs_elems = 0, max_np_small = 0;
+  int stages = 3;
+  bool use_tma = false;
+  TmaBin bins[kTmaBins];
   int* err = nullptr;     // device error flags of the pipelines
   // factorisation: patches whose block fits in shared memory first
   int* fac_list = nullptr;
@@ -91,9 +100,10 @@ int stream_join_in(stokes_handle* h);
 int stream_join_out(stokes_handle* h);
 int set_error(int code, const char* msg);
 
-size_t vanka_tma_smem(const DevPatches& p, size_t elem);
+size_t vanka_tma_smem(const DevPatches& p, const TmaBin& bn, size_t elem);
 cudaError_t vanka_prepare_kernels();
-int vanka_tma_blocks_per_sm(const DevPatches& p, size_t elem);
+int vanka_tma_blocks_per_sm(const DevPatches& p, const TmaBin& bn, int b, size_t elem);
+int vanka_tma_bin_of(int m);
 
 template <typename T>
 cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st);

@@ -12,6 +12,7 @@
 // which is [I U^; 0 I][A^-1 0; B^ S^-1] b with U^ = -U and
 // B^ = -S^-1 B A^-1 = -S^-1 U^T (A is symmetric), so B^ needs no storage.
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "tma.cuh"
@@ -231,82 +232,6 @@ __device__ __forceinline__ void group_copy(T* __restrict__ dst, const T* __restr
   for (int k = nv * V + lane; k < n; k += nl) dst[k] = __ldcs(src + k);
 }
 
-template <typename T, typename TR, int DIM>
-__global__ void __launch_bounds__(128) k_vanka_apply_warp(int nlist, const int* __restrict__ list,
-    const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
-    const int* __restrict__ npres, const int64_t* __restrict__ foff, int shared, const T* __restrict__ fac,
-    const TR* __restrict__ r, T* __restrict__ yp) {
-  __shared__ __align__(16) T sA[4][kWarpPk + 4];
-  __shared__ T sb[4][DIM * kWarpM + kMaxNp];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * 4 + warp;
-  if (gw >= nlist) return;
-  const int i = list ? list[gw] : gw;
-  const int base = ptr[i], m = nvel[i], np = npres[i];
-  const int mu = DIM * m, mt = mu + np;
-  const int64_t fo = foff[i];
-  const int pk = m * (m + 1) / 2;
-  T* A = sA[warp];
-  T* b = sb[warp];
-  for (int k = lane; k < mt; k += 32) b[k] = T(r[dof[base + k]]);
-  T yu[DIM];
-  const int nblk = shared ? 1 : DIM;
-  for (int cb = 0; cb < nblk; ++cb) {
-    __syncwarp();
-    group_copy(A, fac + fo + (int64_t)cb * padded_pk<T>(m), pk, lane, 32);
-    __syncwarp();
-    if (lane < m) {
-      const int c0 = shared ? 0 : cb, c1 = shared ? DIM : cb + 1;
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        if (c < c0 || c >= c1) continue;
-        T acc = T(0);
-        for (int bb = 0; bb < m; ++bb) acc += A[packed_index(lane, bb)] * b[c * m + bb];
-        yu[c] = acc;
-      }
-    }
-  }
-  const T* U = fac + fo + (int64_t)nblk * padded_pk<T>(m);
-  const T* Sinv = U + (int64_t)mu * np;
-  T u[DIM][kMaxNp];
-  T ypk[kMaxNp];
-  T t[kMaxNp];
-#pragma unroll
-  for (int k = 0; k < kMaxNp; ++k) {
-    if (k >= np) break;
-    T part = T(0);
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      u[c][k] = lane < m ? __ldcs(U + (int64_t)k * mu + c * m + lane) : T(0);
-      if (lane < m) part += u[c][k] * b[c * m + lane];
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    t[k] = b[mu + k] - part;
-  }
-#pragma unroll
-  for (int k = 0; k < kMaxNp; ++k) {
-    if (k >= np) break;
-    T s = T(0);
-    for (int k2 = 0; k2 < np; ++k2) s += Sinv[k * np + k2] * t[k2];
-    ypk[k] = s;
-  }
-  if (lane < m) {
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      T x = yu[c];
-      for (int k = 0; k < np; ++k) x -= u[c][k] * ypk[k];
-      yp[base + c * m + lane] = x;
-    }
-  }
-  if (lane < np) {
-    T v = ypk[0];
-    for (int k = 1; k < np; ++k)
-      if (lane == k) v = ypk[k];
-    yp[base + mu + lane] = v;
-  }
-}
-
 // One CTA of 128 threads per patch for patches with more than 32 velocity
 // DoFs per component (coarse levels, 3D).
 template <typename T, typename TR, int DIM>
@@ -384,21 +309,21 @@ __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* _
   if (tid < np) yp[base + mu + tid] = ypk[tid];
 }
 
-// Persistent, warp-specialised patch solves for patches with at most 32
-// velocity DoFs per component.  Patches are stored small-bin first, so the
-// factor blocks, index lists and metadata of `tp` consecutive patches (a
-// tile) are three contiguous ranges: one producer thread moves each tile
-// into a shared-memory ring of `stages` buffers with 1D bulk copies
-// (cp.async.bulk, evict-first in L2) completing on an mbarrier, while
-// kNCW consumer warps solve the previous tiles.  A consumer warp gathers
-// the right-hand side of its contiguous share of the tile into registers
-// (all loads in flight at once), then each half-warp solves one patch with
-// two matrix rows per lane.
+// Persistent, warp-specialised patch solves.  Patches are stored bin by bin
+// (by velocity DoFs per component), so the factor blocks, index lists and
+// metadata of `tp` consecutive patches of a bin (a tile) are three
+// contiguous ranges: one producer thread moves each tile into a
+// shared-memory ring of `stages` buffers with 1D bulk copies
+// (cp.async.bulk, evict-first in L2) completing on an mbarrier, while kNCW
+// consumer warps solve the previous tiles.  A consumer warp gathers the
+// right-hand side of its contiguous share of the tile into registers (all
+// loads in flight), then LP lanes solve one patch, R matrix rows per lane
+// (row a = l + i LP), so a warp holds 32 / LP patches at a time.
 constexpr int kNCW = 4;
 
-template <typename T, typename TR, int DIM, int NPM>
+template <typename T, typename TR, int DIM, int NPM, int LP, int R>
 __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
-    int nsmall, int ntiles, int tp, int stages, int fac_bytes, int dof_bytes, int rhs_elems, int shared,
+    int pstart, int pcount, int ntiles, int tp, int stages, int fac_bytes, int dof_bytes, int rhs_elems, int shared,
     const int4* __restrict__ meta, const int* __restrict__ pptr, const int64_t* __restrict__ foff,
     const int* __restrict__ dof, const T* __restrict__ fac, const TR* __restrict__ r, T* __restrict__ yp,
     int* __restrict__ err) {
@@ -417,6 +342,7 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     mbar_fence_init();
   }
   __syncthreads();
+  const int pend = pstart + pcount;
   if (warp == kNCW) {
     if (lane == 0) {
       const uint64_t pol = policy_evict_first();
@@ -427,7 +353,7 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
           atomicOr(err, 1);
           break;
         }
-        const int i0 = t * tp, i1 = min(i0 + tp, nsmall);
+        const int i0 = pstart + t * tp, i1 = min(i0 + tp, pend);
         const int64_t f0 = foff[i0], f1 = foff[i1];
         const int d0 = pptr[i0] & ~3, d1 = (pptr[i1] + 3) & ~3;
         const uint32_t fb = (uint32_t)((f1 - f0) * (int64_t)sizeof(T));
@@ -444,8 +370,9 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     }
     return;
   }
+  constexpr int PPW = 32 / LP;  // patches a warp holds at a time
   T* myrhs = rhsb + (size_t)warp * rhs_elems;
-  const int half = lane >> 4, l16 = lane & 15;
+  const int slot = lane / LP, l = lane % LP;
   const int nblk = shared ? 1 : DIM;
   int k = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
@@ -458,7 +385,7 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     const T* sfac = reinterpret_cast<const T*>(st);
     const int* sdof = reinterpret_cast<const int*>(st + fac_bytes);
     const int4* smeta = reinterpret_cast<const int4*>(st + fac_bytes + dof_bytes);
-    const int cnt = min(tp, nsmall - t * tp);
+    const int cnt = min(tp, pend - (pstart + t * tp));
     const int per = (cnt + kNCW - 1) / kNCW;
     const int j0 = min(warp * per, cnt), j1 = min(j0 + per, cnt);
     const int4 mf = smeta[0];
@@ -483,10 +410,10 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
         }
       }
       __syncwarp();
-      for (int pp = 0; j0 + 2 * pp < j1; ++pp) {
-        const int j = j0 + 2 * pp + half;
+      for (int jb = j0; jb < j1; jb += PPW) {
+        const int j = jb + slot;
         const bool valid = j < j1;
-        const int4 mt = smeta[valid ? j : j0];
+        const int4 mt = smeta[valid ? j : jb];
         const int m = mt.y & 0xffff, np = mt.y >> 16, base = mt.x;
         const int mu = DIM * m;
         const int64_t fo = ((int64_t)(uint32_t)mt.z | ((int64_t)mt.w << 32)) - ftile;
@@ -495,33 +422,38 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
         const T* U = A + nblk * pkp;
         const T* Sv = U + mu * np;
         const T* bb = myrhs + (base - sb);
-        const int ra = l16, rb = l16 + 16;
-        const int ca = min(ra, m - 1), cb = min(rb, m - 1);
-        const int ta = ca * (ca + 1) / 2, tb2 = cb * (cb + 1) / 2;
-        T acc[DIM][2];
+        int ca[R], ta[R];
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) acc[c][0] = acc[c][1] = T(0);
+        for (int i = 0; i < R; ++i) {
+          ca[i] = min(l + i * LP, m - 1);
+          ta[i] = ca[i] * (ca[i] + 1) / 2;
+        }
+        T acc[DIM][R];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int i = 0; i < R; ++i) acc[c][i] = T(0);
         for (int blk = 0; blk < nblk; ++blk) {
           const T* Ab = A + blk * pkp;
           int tb = 0;
           for (int b = 0; b < m; ++b) {
-            const T va = Ab[ca >= b ? ta + b : tb + ca];
-            const T vb = Ab[cb >= b ? tb2 + b : tb + cb];
+            T va[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) va[i] = Ab[ca[i] >= b ? ta[i] + b : tb + ca[i]];
             if (shared) {
 #pragma unroll
               for (int c = 0; c < DIM; ++c) {
-                const T x = bb[c * m + b];
-                acc[c][0] += va * x;
-                acc[c][1] += vb * x;
+                const T xv = bb[c * m + b];
+#pragma unroll
+                for (int i = 0; i < R; ++i) acc[c][i] += va[i] * xv;
               }
             } else {
-              const T x = bb[blk * m + b];
+              const T xv = bb[blk * m + b];
 #pragma unroll
               for (int c = 0; c < DIM; ++c)
-                if (c == blk) {
-                  acc[c][0] += va * x;
-                  acc[c][1] += vb * x;
-                }
+                if (c == blk)
+#pragma unroll
+                  for (int i = 0; i < R; ++i) acc[c][i] += va[i] * xv;
             }
             tb += b + 1;
           }
@@ -531,11 +463,9 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
         for (int kk = 0; kk < NPM; ++kk) {
           T part = T(0);
           if (kk < np)
-            for (int row = l16; row < mu; row += 16) part += U[kk * mu + row] * bb[row];
-          part += __shfl_xor_sync(0xffffffffu, part, 8);
-          part += __shfl_xor_sync(0xffffffffu, part, 4);
-          part += __shfl_xor_sync(0xffffffffu, part, 2);
-          part += __shfl_xor_sync(0xffffffffu, part, 1);
+            for (int row = l; row < mu; row += LP) part += U[kk * mu + row] * bb[row];
+#pragma unroll
+          for (int o = LP / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
           tk[kk] = kk < np ? bb[mu + kk] - part : T(0);
         }
 #pragma unroll
@@ -548,25 +478,21 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
         }
         if (valid) {
 #pragma unroll
-          for (int c = 0; c < DIM; ++c) {
-            if (ra < m) {
-              T x = acc[c][0];
+          for (int c = 0; c < DIM; ++c)
 #pragma unroll
-              for (int kk = 0; kk < NPM; ++kk)
-                if (kk < np) x -= U[kk * mu + c * m + ra] * yk[kk];
-              yp[base + c * m + ra] = x;
-            }
-            if (rb < m) {
-              T x = acc[c][1];
+            for (int i = 0; i < R; ++i) {
+              const int a = l + i * LP;
+              if (a < m) {
+                T x = acc[c][i];
 #pragma unroll
-              for (int kk = 0; kk < NPM; ++kk)
-                if (kk < np) x -= U[kk * mu + c * m + rb] * yk[kk];
-              yp[base + c * m + rb] = x;
+                for (int kk = 0; kk < NPM; ++kk)
+                  if (kk < np) x -= U[kk * mu + c * m + a] * yk[kk];
+                yp[base + c * m + a] = x;
+              }
             }
-          }
 #pragma unroll
           for (int kk = 0; kk < NPM; ++kk)
-            if (kk < np && l16 == kk) yp[base + mu + kk] = yk[kk];
+            if (kk < np && l == kk) yp[base + mu + kk] = yk[kk];
         }
       }
     }
@@ -575,59 +501,82 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
   }
 }
 
-template <typename T, typename TR, int DIM, int NPM>
-static cudaError_t launch_tma(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
-  auto kern = k_vanka_apply_tma<T, TR, DIM, NPM>;
-  const size_t shm = 128 + (size_t)p.stages * (p.tile_fac_bytes + p.tile_dof_bytes + p.tp * 16) +
-                     (size_t)kNCW * p.rhs_elems * sizeof(T);
-  kern<<<p.tma_grid, 32 * (kNCW + 1), shm, st>>>(p.nsmall, p.ntiles, p.tp, p.stages, p.tile_fac_bytes,
-                                                 p.tile_dof_bytes, p.rhs_elems, p.shared, p.meta, p.ptr, p.foff,
-                                                 p.dof, reinterpret_cast<const T*>(p.fac), r, yp, p.err);
+// (lanes per patch, rows per lane) of TMA bin b; bins hold m <= 8, 32, 64, 96.
+__host__ __device__ constexpr int bin_lp(int b) { return b == 0 ? 8 : (b == 1 ? 16 : 32); }
+__host__ __device__ constexpr int bin_r(int b) { return b == 0 ? 1 : (b == 1 ? 2 : (b == 2 ? 2 : 3)); }
+
+template <typename T, typename TR, int DIM, int NPM, int LP, int R>
+static cudaError_t launch_tma_bin(const DevPatches& p, const TmaBin& bn, const TR* r, T* yp, cudaStream_t st) {
+  const size_t shm = 128 + (size_t)p.stages * (bn.fac_bytes + bn.dof_bytes + bn.tp * 16) +
+                     (size_t)kNCW * bn.rhs_elems * sizeof(T);
+  k_vanka_apply_tma<T, TR, DIM, NPM, LP, R><<<bn.grid, 32 * (kNCW + 1), shm, st>>>(
+      bn.start, bn.count, bn.ntiles, bn.tp, p.stages, bn.fac_bytes, bn.dof_bytes, bn.rhs_elems, p.shared, p.meta,
+      p.ptr, p.foff, p.dof, reinterpret_cast<const T*>(p.fac), r, yp, p.err);
   return cudaGetLastError();
 }
 
-template <typename T, typename TR>
-static cudaError_t apply_small_tma(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
-  const bool one = p.max_np_small <= 1;
-  if (p.dim == 2) return one ? launch_tma<T, TR, 2, 1>(p, r, yp, st) : launch_tma<T, TR, 2, 4>(p, r, yp, st);
-  return one ? launch_tma<T, TR, 3, 1>(p, r, yp, st) : launch_tma<T, TR, 3, 4>(p, r, yp, st);
-}
-
-// Shared-memory bytes of the TMA kernel for a tile configuration.
-size_t vanka_tma_smem(const DevPatches& p, size_t elem) {
-  return 128 + (size_t)p.stages * (p.tile_fac_bytes + p.tile_dof_bytes + p.tp * 16) + (size_t)kNCW * p.rhs_elems * elem;
-}
-
-int vanka_tma_blocks_per_sm(const DevPatches& p, size_t elem) {
-  int nb = 0;
-  const size_t shm = vanka_tma_smem(p, elem);
-  cudaError_t e;
-  if (elem == 4) {
-    auto kern = p.max_np_small <= 1 ? (p.dim == 2 ? k_vanka_apply_tma<float, float, 2, 1> : k_vanka_apply_tma<float, float, 3, 1>)
-                                    : (p.dim == 2 ? k_vanka_apply_tma<float, float, 2, 4> : k_vanka_apply_tma<float, float, 3, 4>);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * (kNCW + 1), shm);
-  } else {
-    auto kern = p.max_np_small <= 1 ? (p.dim == 2 ? k_vanka_apply_tma<double, double, 2, 1> : k_vanka_apply_tma<double, double, 3, 1>)
-                                    : (p.dim == 2 ? k_vanka_apply_tma<double, double, 2, 4> : k_vanka_apply_tma<double, double, 3, 4>);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * (kNCW + 1), shm);
+template <typename T, typename TR, int DIM, int NPM>
+static cudaError_t launch_bin_np(const DevPatches& p, int b, const TR* r, T* yp, cudaStream_t st) {
+  const TmaBin& bn = p.bins[b];
+  switch (b) {
+    case 0: return launch_tma_bin<T, TR, DIM, NPM, 8, 1>(p, bn, r, yp, st);
+    case 1: return launch_tma_bin<T, TR, DIM, NPM, 16, 2>(p, bn, r, yp, st);
+    case 2: return launch_tma_bin<T, TR, DIM, NPM, 32, 2>(p, bn, r, yp, st);
+    default: return launch_tma_bin<T, TR, DIM, NPM, 32, 3>(p, bn, r, yp, st);
   }
+}
+
+template <typename T, typename TR>
+static cudaError_t apply_tma_bins(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
+  for (int b = 0; b < kTmaBins; ++b) {
+    const TmaBin& bn = p.bins[b];
+    if (bn.count == 0) continue;
+    const bool one = bn.max_np <= 1;
+    cudaError_t e;
+    if (p.dim == 2) e = one ? launch_bin_np<T, TR, 2, 1>(p, b, r, yp, st) : launch_bin_np<T, TR, 2, 4>(p, b, r, yp, st);
+    else e = one ? launch_bin_np<T, TR, 3, 1>(p, b, r, yp, st) : launch_bin_np<T, TR, 3, 4>(p, b, r, yp, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Shared-memory bytes of a TMA bin's tile configuration.
+size_t vanka_tma_smem(const DevPatches& p, const TmaBin& bn, size_t elem) {
+  return 128 + (size_t)p.stages * (bn.fac_bytes + bn.dof_bytes + bn.tp * 16) + (size_t)kNCW * bn.rhs_elems * elem;
+}
+
+template <typename T, int DIM, int NPM>
+static const void* tma_kernel_ptr(int b) {
+  switch (b) {
+    case 0: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 8, 1>;
+    case 1: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 16, 2>;
+    case 2: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 32, 2>;
+    default: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 32, 3>;
+  }
+}
+
+static const void* tma_kernel(size_t elem, int dim, bool one, int b) {
+  if (elem == 4) {
+    if (dim == 2) return one ? tma_kernel_ptr<float, 2, 1>(b) : tma_kernel_ptr<float, 2, 4>(b);
+    return one ? tma_kernel_ptr<float, 3, 1>(b) : tma_kernel_ptr<float, 3, 4>(b);
+  }
+  if (dim == 2) return one ? tma_kernel_ptr<double, 2, 1>(b) : tma_kernel_ptr<double, 2, 4>(b);
+  return one ? tma_kernel_ptr<double, 3, 1>(b) : tma_kernel_ptr<double, 3, 4>(b);
+}
+
+int vanka_tma_blocks_per_sm(const DevPatches& p, const TmaBin& bn, int b, size_t elem) {
+  int nb = 0;
+  const void* k = tma_kernel(elem, p.dim, bn.max_np <= 1, b);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * (kNCW + 1), vanka_tma_smem(p, bn, elem));
   return e == cudaSuccess ? nb : 0;
 }
 
+int vanka_tma_bin_of(int m) { return m <= 8 ? 0 : (m <= 32 ? 1 : (m <= 64 ? 2 : (m <= 96 ? 3 : -1))); }
+
 template <typename T, typename TR>
 cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
-  if (p.nsmall > 0 && p.ntiles > 0) {
-    cudaError_t e = apply_small_tma<T, TR>(p, r, yp, st);
-    if (e != cudaSuccess) return e;
-  } else if (p.nsmall > 0) {
-    const unsigned blocks = (unsigned)((p.nsmall + 3) / 4);
-    if (p.dim == 2)
-      k_vanka_apply_warp<T, TR, 2><<<blocks, 128, 0, st>>>(p.nsmall, p.small, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                           p.shared, reinterpret_cast<const T*>(p.fac), r, yp);
-    else
-      k_vanka_apply_warp<T, TR, 3><<<blocks, 128, 0, st>>>(p.nsmall, p.small, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                           p.shared, reinterpret_cast<const T*>(p.fac), r, yp);
-    cudaError_t e = cudaGetLastError();
+  if (p.nsmall > 0) {
+    cudaError_t e = apply_tma_bins<T, TR>(p, r, yp, st);
     if (e != cudaSuccess) return e;
   }
   if (p.nlarge > 0) {
@@ -649,7 +598,6 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
 }
 template cudaError_t vanka_apply<float, float>(const DevPatches&, const float*, float*, cudaStream_t);
 template cudaError_t vanka_apply<double, double>(const DevPatches&, const double*, double*, cudaStream_t);
-template cudaError_t vanka_apply<float, double>(const DevPatches&, const double*, float*, cudaStream_t);
 
 // Allow every kernel with large dynamic shared memory the device's opt-in
 // maximum once, so launches inside graph capture never need the attribute.
@@ -659,17 +607,14 @@ cudaError_t vanka_prepare_kernels() {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  const void* ks[] = {
+  std::vector<const void*> ks = {
       (const void*)k_vanka_factor<float>, (const void*)k_vanka_factor<double>,
-      (const void*)k_vanka_apply_tma<float, float, 2, 1>, (const void*)k_vanka_apply_tma<float, float, 2, 4>,
-      (const void*)k_vanka_apply_tma<float, float, 3, 1>, (const void*)k_vanka_apply_tma<float, float, 3, 4>,
-      (const void*)k_vanka_apply_tma<double, double, 2, 1>, (const void*)k_vanka_apply_tma<double, double, 2, 4>,
-      (const void*)k_vanka_apply_tma<double, double, 3, 1>, (const void*)k_vanka_apply_tma<double, double, 3, 4>,
-      (const void*)k_vanka_apply_tma<float, double, 2, 1>, (const void*)k_vanka_apply_tma<float, double, 2, 4>,
-      (const void*)k_vanka_apply_tma<float, double, 3, 1>, (const void*)k_vanka_apply_tma<float, double, 3, 4>,
       (const void*)k_vanka_apply_cta<float, float, 2>, (const void*)k_vanka_apply_cta<float, float, 3>,
-      (const void*)k_vanka_apply_cta<double, double, 2>, (const void*)k_vanka_apply_cta<double, double, 3>,
-      (const void*)k_vanka_apply_cta<float, double, 2>, (const void*)k_vanka_apply_cta<float, double, 3>};
+      (const void*)k_vanka_apply_cta<double, double, 2>, (const void*)k_vanka_apply_cta<double, double, 3>};
+  for (size_t elem : {size_t(4), size_t(8)})
+    for (int dim : {2, 3})
+      for (bool one : {true, false})
+        for (int b = 0; b < kTmaBins; ++b) ks.push_back(tma_kernel(elem, dim, one, b));
   for (const void* k : ks) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;

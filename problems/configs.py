@@ -62,7 +62,27 @@ def c5_instances(count=64, lo=32, hi=192, seed=5000):
     return [(int(ns[k]), float(10.0 ** lognu[k]), seed + k) for k in range(count)]
 
 
-def c5(count=64, lo=32, hi=192, seed=5000):
-    return [stokes.build_th(M.unit_square(n), nu=nu, bc="noslip", rhs="random_b", seed=s,
-                            name=f"C5[{k}] TH2D {n}^2 nu={nu:.3g}")
-            for k, (n, nu, s) in enumerate(c5_instances(count, lo, hi, seed))]
+def _c5_one(args):
+    k, n, nu, s = args
+    return stokes.build_th(M.unit_square(n), nu=nu, bc="noslip", rhs="random_b", seed=s,
+                           name=f"C5[{k}] TH2D {n}^2 nu={nu:.3g}")
+
+
+def c5(count=64, lo=32, hi=192, seed=5000, workers=None):
+    """The batched workload; instances are built in a spawn-context process
+    pool when workers > 1 (default: the host's cores)."""
+    import os
+    jobs = [(k, n, nu, s) for k, (n, nu, s) in enumerate(c5_instances(count, lo, hi, seed))]
+    workers = workers if workers is not None else min(len(jobs), os.cpu_count() or 1)
+    if workers <= 1:
+        return [_c5_one(j) for j in jobs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    # largest first for load balance, results back in instance order
+    order = sorted(range(len(jobs)), key=lambda i: -jobs[i][1])
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        built = list(ex.map(_c5_one, [jobs[i] for i in order]))
+    out = [None] * len(jobs)
+    for i, p in zip(order, built):
+        out[i] = p
+    return out
