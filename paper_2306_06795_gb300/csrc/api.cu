@@ -179,7 +179,7 @@ int choose_tpr(int64_t nnz, int nrows) {
 
 // Operators with at least this many rows use the bulk-copy SpMV.
 constexpr int kTmaRows = 32768;
-constexpr int kTileNnz = 2048, kTileRows = 512;
+constexpr int kTileNnz = 1024, kTileRows = 256;
 
 int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
   d.nrows = c.nrows;
@@ -1104,19 +1104,38 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       shared = shared && sh;
     }
     if (onv.empty()) continue;
-    // storage order: the bulk-copy bins by m (<= 8, 32, 64, 96), then the rest
+    // storage order: the bulk-copy bins by m (<= 8, 32, 64, 96), then the rest;
+    // a bin whose smallest tile (4 patches per warp group, 3 stages) would not
+    // fit in shared memory hands its patches to the CTA-per-patch kernel
     const int npatch = (int)onv.size();
+    const int nblk0 = shared ? 1 : dim;
+    bool bin_ok[kTmaBins];
+    for (int b = 0; b < kTmaBins; ++b) {
+      int64_t maxblk = 0;
+      for (int i = 0; i < npatch; ++i)
+        if (vanka_tma_bin_of(onv[i]) == b) {
+          const int64_t m = onv[i], np = onp[i];
+          const int64_t pkp = (m * (m + 1) / 2 + align - 1) / align * align;
+          maxblk = std::max(maxblk, (nblk0 * pkp + dim * m * np + np * np + align) * (int64_t)T);
+        }
+      const int ppw = b == 0 ? 4 : (b == 1 ? 2 : 1);
+      bin_ok[b] = 3 * 4 * ppw * maxblk <= 160 * 1024;
+    }
+    auto bin_of = [&](int m) {
+      const int b = vanka_tma_bin_of(m);
+      return (b >= 0 && bin_ok[b]) ? b : -1;
+    };
     std::vector<int> order;
     int bin_start[kTmaBins + 1];
     for (int b = 0; b < kTmaBins; ++b) {
       bin_start[b] = (int)order.size();
       for (int i = 0; i < npatch; ++i)
-        if (vanka_tma_bin_of(onv[i]) == b) order.push_back(i);
+        if (bin_of(onv[i]) == b) order.push_back(i);
     }
     bin_start[kTmaBins] = (int)order.size();
     const int nsmall = (int)order.size();
     for (int i = 0; i < npatch; ++i)
-      if (vanka_tma_bin_of(onv[i]) < 0) order.push_back(i);
+      if (bin_of(onv[i]) < 0) order.push_back(i);
     std::vector<int> pptr{0}, pdof, pnv, pnp, small, large, stor(npatch);
     std::vector<int64_t> foff;
     int64_t fac = 0;
