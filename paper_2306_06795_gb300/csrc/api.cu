@@ -113,6 +113,7 @@ struct stokes_handle {
   double* mdinv = nullptr;   // 1 / diag(Mcg)
   double* cv[5] = {nullptr}; // Chebyshev-Jacobi: rhs, x, r, d0, d1
   double* d0buf = nullptr;   // FP64 DC residual of level 0
+  double* x0_64 = nullptr;   // FP64 copy of the level-0 iterate (FP32 cycle)
   double mcg_lo = 0.5, mcg_hi = 2.0;
   int mcg_deg = 32;
   uint8_t* dir0 = nullptr;   // level 0: 1 on Dirichlet rows
@@ -417,18 +418,19 @@ int L_apply(stokes_handle* h, const Level& lv, const TR* r, T* yp) {
 
 template <typename T>
 int L_scatter(stokes_handle* h, const Level& lv, const T* yp, T* x, double omega, int mode,
-              const double* r64 = nullptr, double* out64 = nullptr) {
+              const double* r64 = nullptr, double* out64 = nullptr, double* x64 = nullptr) {
   const DevPatches& p = lv.pat;
   if (h->led.count) {
     double b = 4.0 * (lv.n + 1) + double(p.nslots) * (4 + sizeof(T));
     if (mode == 0) b += double(lv.n) * sizeof(T);
     else if (mode == 1) b += 2.0 * lv.n * sizeof(T);
     else b += double(lv.n) * (sizeof(T) + 1 + 8);
+    if (x64 && mode != 2) b += 8.0 * lv.n;
     h->led.bytes += b;
     h->led.launches += 1;
     return STOKES_OK;
   }
-  CK(vanka_scatter<T>(p, lv.n, yp, x, omega, mode, h->dir0, r64, out64, h->st));
+  CK(vanka_scatter<T>(p, lv.n, yp, x, omega, mode, h->dir0, r64, out64, h->st, x64));
   return STOKES_OK;
 }
 
@@ -599,7 +601,7 @@ int dlsc_sweep(stokes_handle* h, int l, T* x, const T* b) {
 // A DLSC level runs nsweeps calls of dlsc_sweeps DLSC sweeps instead.
 template <typename T>
 int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_guess, const double* r64 = nullptr,
-          double* out64 = nullptr) {
+          double* out64 = nullptr, double* x64 = nullptr) {
   Level& L = h->lv[l];
   if (L.dlsc) {
     if (zero_guess) TRY(L_zero<T>(h, L.n, x));
@@ -611,13 +613,14 @@ int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_gues
   if (nsweeps == 0 && zero_guess) TRY(L_zero<T>(h, L.n, x));
   for (int s = 0; s < nsweeps; ++s) {
     const bool last_out = out64 && s == nsweeps - 1;
+    double* xd = s == nsweeps - 1 ? x64 : nullptr;
     if (s == 0 && zero_guess) {
       TRY((L_apply<T, T>(h, L, b, yp)));
-      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 0, r64, out64));
+      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 0, r64, out64, xd));
     } else {
       TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
       TRY((L_apply<T, T>(h, L, r, yp)));
-      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 1, r64, out64));
+      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 1, r64, out64, xd));
     }
   }
   return STOKES_OK;
@@ -650,12 +653,12 @@ int vcycle(stokes_handle* h, int l) {
 // velocity injection of d, pressure = Mcg^-1 Pi^T M_dg d_p by mcg_deg
 // Chebyshev-Jacobi steps on the interval [mcg_lo, mcg_hi] (FP64).
 template <typename T>
-int restrict0_sv(stokes_handle* h, const T* x0, const double* r64) {
+int restrict0_sv_t(stokes_handle* h, const double* x0, const double* r64) {
   Level& L0 = h->lv[0];
   Level& L1 = h->lv[1];
   T* b1 = reinterpret_cast<T*>(L1.b);
-  TRY((L_spmv<double, T, double, double, double>(h, L0.K, L0.K.v64, x0, r64, h->d0buf, SPMV_SCALED_RES, h->eta_u,
-                                                 h->eta_p, h->kind0)));
+  TRY((L_spmv<double, double, double, double, double>(h, L0.K, L0.K.v64, x0, r64, h->d0buf, SPMV_SCALED_RES,
+                                                      h->eta_u, h->eta_p, h->kind0)));
   TRY((L_spmv<double, double, double, T, double>(h, h->R0v, h->R0v.v64, h->d0buf, (const double*)nullptr, b1,
                                                  SPMV_SET)));
   TRY((L_spmv<double, double, double, double, double>(h, h->R0q, h->R0q.v64, h->d0buf, (const double*)nullptr,
@@ -664,6 +667,10 @@ int restrict0_sv(stokes_handle* h, const T* x0, const double* r64) {
                        h->mcg_lo, h->mcg_hi, h->mcg_deg, h->cv[1], h->cv[2], h->cv[3], h->cv[4], h->ncg));
   TRY((L_scatter_rows<double, T>(h, h->ncg, h->cv[1], h->prow1, b1)));
   return STOKES_OK;
+}
+
+int restrict0_sv(stokes_handle* h, const double* x0, const double* r64) {
+  return h->prec == STOKES_FP32 ? restrict0_sv_t<float>(h, x0, r64) : restrict0_sv_t<double>(h, x0, r64);
 }
 
 // z = M_dc^-1 r (Eq. TG-operator-full, gamma = 1), zero initial guess.
@@ -680,14 +687,21 @@ int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
     r0 = reinterpret_cast<const T*>(L0.b);
   }
   const bool skip0 = h->schedule == STOKES_DC_SKIP0 || !L0.has_patches;
-  if (!skip0) TRY(relax<T>(h, 0, x0, r0, h->nu1, true));
-  else TRY(L_zero<T>(h, L0.n, x0));
+  // an FP32 cycle also keeps x in FP64 for the FP64 residual of the DC step,
+  // so that residual converts each entry once instead of once per nonzero
+  double* x0d = sizeof(T) == 8 ? reinterpret_cast<double*>(x0) : h->x0_64;
+  const bool pre = !skip0 && h->nu1 > 0;
+  if (pre) TRY(relax<T>(h, 0, x0, r0, h->nu1, true, nullptr, nullptr, sizeof(T) == 8 ? nullptr : x0d));
+  else {
+    TRY(L_zero<T>(h, L0.n, x0));
+    if (sizeof(T) != 8) TRY(L_zero<double>(h, L0.n, x0d));
+  }
   // DC residual in FP64: d = eta (r - K0 x), then R0 (Eq. interp)
   if (h->disc == STOKES_TH) {  // R0 = injection, fused into the residual
-    TRY((L_spmv<double, T, double, T, double>(h, L0.K, L0.K.v64, x0, r64, reinterpret_cast<T*>(L1.b),
-                                              SPMV_SCALED_RES, h->eta_u, h->eta_p, h->kind0)));
+    TRY((L_spmv<double, double, double, T, double>(h, L0.K, L0.K.v64, x0d, r64, reinterpret_cast<T*>(L1.b),
+                                                   SPMV_SCALED_RES, h->eta_u, h->eta_p, h->kind0)));
   } else {
-    TRY(restrict0_sv<T>(h, x0, r64));
+    TRY(restrict0_sv(h, x0d, r64));
   }
   TRY(vcycle<T>(h, 1));
   if (L0.Pident) TRY((L_axpy<T, T>(h, L0.n, 1.0, reinterpret_cast<const T*>(L1.x), x0)));  // P0 = I
@@ -1121,9 +1135,27 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       const int ppw = b == 0 ? 4 : (b == 1 ? 2 : 1);
       bin_ok[b] = 3 * 4 * ppw * maxblk <= 160 * 1024;
     }
+    // a nearly empty bin (e.g. the few corner patches below m = 8) joins the
+    // next larger usable bin, whose kernel handles any smaller m: one launch less
+    int bin_cnt[kTmaBins] = {0};
+    for (int i = 0; i < npatch; ++i) {
+      const int b = vanka_tma_bin_of(onv[i]);
+      if (b >= 0) bin_cnt[b]++;
+    }
+    int bin_map[kTmaBins];
+    for (int b = kTmaBins - 1; b >= 0; --b) {
+      bin_map[b] = bin_ok[b] ? b : -1;
+      if (bin_ok[b] && b + 1 < kTmaBins && bin_map[b + 1] >= 0) {
+        const int up = bin_map[b + 1];
+        if (bin_cnt[b] < std::max(64, bin_cnt[up] / 4)) {
+          bin_map[b] = up;
+          bin_cnt[up] += bin_cnt[b];
+        }
+      }
+    }
     auto bin_of = [&](int m) {
       const int b = vanka_tma_bin_of(m);
-      return (b >= 0 && bin_ok[b]) ? b : -1;
+      return b >= 0 ? bin_map[b] : -1;
     };
     std::vector<int> order;
     int bin_start[kTmaBins + 1];
@@ -1297,6 +1329,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     lv.x = x; lv.b = b; lv.r = r; lv.ta = ta; lv.tb = tb;
   }
   if (h->disc == STOKES_SV) TRY(setup_sv(h, probs, ninst, dim));
+  if (h->prec == STOKES_FP32) TRY(dalloc(h, &h->x0_64, (size_t)h->lv[0].n));
   // level-0 row kinds and Dirichlet mask
   {
     std::vector<uint8_t> kind(h->lv[0].n), dir(h->lv[0].n);

@@ -246,15 +246,27 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
   return cudaGetLastError();
 }
 
-// grid: nchunks; w[row] += sign * sum_k coef[seg*ldh + k] * V_k[row]
+// grid: (nchunks, kAxpySplit); w[row] += sign * sum_k coef[seg*ldh + k] * V_k[row],
+// one row per thread, the columns' loads issued eight at a time
+constexpr int kAxpySplit = 8;
 __global__ void __launch_bounds__(kRedThreads) k_multiaxpy(const int64_t* __restrict__ cbeg,
     const int64_t* __restrict__ cend, const int* __restrict__ cseg, int ncols, const double* __restrict__ V,
     int64_t ldv, const double* __restrict__ coef, int ldh, double sign, double* __restrict__ w) {
   const int c = blockIdx.x;
   const double* cf = coef + cseg[c] * ldh;
-  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kRedThreads) {
+  const int64_t len = cend[c] - cbeg[c];
+  const int64_t step = (int64_t)kRedThreads * kAxpySplit;
+  for (int64_t o = (int64_t)blockIdx.y * kRedThreads + threadIdx.x; o < len; o += step) {
+    const int64_t r = cbeg[c] + o;
     double s = 0.0;
-    for (int k = 0; k < ncols; ++k) s += cf[k] * V[(int64_t)k * ldv + r];
+    for (int k0 = 0; k0 < ncols; k0 += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = k0 + u < ncols ? V[(int64_t)(k0 + u) * ldv + r] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < ncols) s += cf[k0 + u] * v[u];
+    }
     w[r] += sign * s;
   }
 }
@@ -262,7 +274,8 @@ cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, con
                       const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
                       cudaStream_t st) {
   if (nchunks == 0 || ncols == 0) return cudaSuccess;
-  k_multiaxpy<<<nchunks, kRedThreads, 0, st>>>(cbeg, cend, cseg, ncols, V, ldv, coef, ldh, sign, w);
+  k_multiaxpy<<<dim3((unsigned)nchunks, kAxpySplit), kRedThreads, 0, st>>>(cbeg, cend, cseg, ncols, V, ldv, coef, ldh,
+                                                                         sign, w);
   return cudaGetLastError();
 }
 

@@ -116,10 +116,12 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
 // Weighted scatter of Eq. vanka: s_j = sum over the patch slots of DoF j in
 // ascending patch order; mode 0: x_j = omega s_j / cnt_j; mode 1: x_j +=
 // omega s_j / cnt_j; mode 2 (final level-0 output): out_j = dir_j ? r64_j :
-// double(x_j + omega s_j / cnt_j).
+// double(x_j + omega s_j / cnt_j).  With x64 (modes 0, 1) the new x is also
+// written in FP64.
 template <typename T>
 cudaError_t vanka_scatter(const DevPatches& p, int64_t n, const T* yp, T* x, double omega, int mode,
-                          const uint8_t* dir, const double* r64, double* out64, cudaStream_t st);
+                          const uint8_t* dir, const double* r64, double* out64, cudaStream_t st,
+                          double* x64 = nullptr);
 
 // Elementwise helpers
 template <typename TI, typename TO>

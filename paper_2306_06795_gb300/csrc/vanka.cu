@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
       const int sb = smeta[j0].x;
       const int4 ml = smeta[j1 - 1];
       const int ns = ml.x + DIM * (ml.y & 0xffff) + (ml.y >> 16) - sb;
-      constexpr int G = 8;
+      constexpr int G = 4;
       for (int q0 = 0; q0 < ns; q0 += 32 * G) {
         TR v[G];
 #pragma unroll
@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
         for (int blk = 0; blk < nblk; ++blk) {
           const T* Ab = A + blk * pkp;
           int tb = 0;
+#pragma unroll 2
           for (int b = 0; b < m; ++b) {
             T va[R];
 #pragma unroll
@@ -626,7 +627,8 @@ cudaError_t vanka_prepare_kernels() {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_vanka_scatter(int64_t n, const int* __restrict__ tptr,
     const int* __restrict__ tslot, const T* __restrict__ yp, T* __restrict__ x, T omega,
-    const uint8_t* __restrict__ dir, const double* __restrict__ r64, double* __restrict__ out64) {
+    const uint8_t* __restrict__ dir, const double* __restrict__ r64, double* __restrict__ out64,
+    double* __restrict__ x64) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int b = tptr[j], e = tptr[j + 1];
@@ -641,27 +643,31 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int64_t n, const int* __r
     for (int u = 0; u < 4; ++u) s += v[u];
   }
   const T upd = e > b ? omega * s / T(e - b) : T(0);
-  if (MODE == 0) x[j] = upd;
-  else if (MODE == 1) x[j] += upd;
-  else out64[j] = dir[j] ? r64[j] : double(x[j] + upd);
+  if (MODE == 2) {
+    out64[j] = dir[j] ? r64[j] : double(x[j] + upd);
+    return;
+  }
+  const T xn = MODE == 0 ? upd : x[j] + upd;
+  x[j] = xn;
+  if (x64) x64[j] = double(xn);  // FP64 copy for the FP64 defect-correction residual
 }
 
 template <typename T>
 cudaError_t vanka_scatter(const DevPatches& p, int64_t n, const T* yp, T* x, double omega, int mode,
-                          const uint8_t* dir, const double* r64, double* out64, cudaStream_t st) {
+                          const uint8_t* dir, const double* r64, double* out64, cudaStream_t st, double* x64) {
   if (n == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (mode == 0)
-    k_vanka_scatter<T, 0><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64);
+    k_vanka_scatter<T, 0><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64, x64);
   else if (mode == 1)
-    k_vanka_scatter<T, 1><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64);
+    k_vanka_scatter<T, 1><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64, x64);
   else
-    k_vanka_scatter<T, 2><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64);
+    k_vanka_scatter<T, 2><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64, x64);
   return cudaGetLastError();
 }
 template cudaError_t vanka_scatter<float>(const DevPatches&, int64_t, const float*, float*, double, int,
-                                          const uint8_t*, const double*, double*, cudaStream_t);
+                                          const uint8_t*, const double*, double*, cudaStream_t, double*);
 template cudaError_t vanka_scatter<double>(const DevPatches&, int64_t, const double*, double*, double, int,
-                                           const uint8_t*, const double*, double*, cudaStream_t);
+                                           const uint8_t*, const double*, double*, cudaStream_t, double*);
 
 }  // namespace sd

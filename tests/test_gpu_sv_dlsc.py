@@ -100,3 +100,38 @@ def test_th_dlsc_on_coarse_levels_fp64(sd):
     z = torch.empty(r.size, dtype=torch.float64, device="cuda")
     sd.stokes_vcycle(h, dev(r), z)
     assert rel(host(z), o.apply(r)) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def c3():
+    return configs.c3()
+
+
+@pytest.mark.parametrize("name", ["vanka", "vanka-dlsc"])
+def test_c3_full_size(sd, c3, name):
+    """The 128^2 Alfeld problem: the FP64 cycle equals the oracle's on one
+    application; the FP32-preconditioned solve reaches 1e-8 within +-2
+    iterations of the FP64 form and a divergence-free velocity."""
+    prm = variants(c3)[name]
+    h64 = sd.stokes_setup(c3, dict(prm, precision=sd.STOKES_FP64))
+    sd.stokes_factor_patches(h64)
+    o = make_oracle(c3, prm)
+    r = np.random.default_rng(24).standard_normal(c3.b.size)
+    z = torch.empty(r.size, dtype=torch.float64, device="cuda")
+    sd.stokes_vcycle(h64, dev(r), z)
+    assert rel(host(z), o.apply(r)) < 1e-12
+    its = {}
+    for prec, h in ((sd.STOKES_FP64, h64), (sd.STOKES_FP32, None)):
+        if h is None:
+            h = sd.stokes_setup(c3, dict(prm, precision=prec))
+            sd.stokes_factor_patches(h)
+        x = torch.zeros(c3.b.size, dtype=torch.float64, device="cuda")
+        rc, info = sd.stokes_fgmres_solve(h, dev(c3.b), x, rtol=1e-8, restart=30, maxit=400)
+        assert rc == sd.STOKES_OK and info[0][2] <= 1e-8
+        its[prec] = info[0][0]
+        xh = host(x)
+    assert abs(its[sd.STOKES_FP32] - its[sd.STOKES_FP64]) <= 2
+    off = c3.field_off[0]
+    A = c3.K[0][: off[2], : off[2]]
+    energy = np.sqrt(xh[: off[2]] @ (A @ xh[: off[2]]))
+    assert stokes.divergence_norm(c3, xh) < 1e-6 * energy
