@@ -1118,7 +1118,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       shared = shared && sh;
     }
     if (onv.empty()) continue;
-    // storage order: the bulk-copy bins by m (<= 8, 32, 64, 96), then the rest;
+    // storage order: the bulk-copy bins by m (<= 6, 20, 32, 64, 96), then the rest;
     // a bin whose smallest tile (4 patches per warp group, 3 stages) would not
     // fit in shared memory hands its patches to the CTA-per-patch kernel
     const int npatch = (int)onv.size();
@@ -1132,7 +1132,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
           const int64_t pkp = (m * (m + 1) / 2 + align - 1) / align * align;
           maxblk = std::max(maxblk, (nblk0 * pkp + dim * m * np + np * np + align) * (int64_t)T);
         }
-      const int ppw = b == 0 ? 4 : (b == 1 ? 2 : 1);
+      const int ppw = vanka_tma_bin_ppw(b);
       bin_ok[b] = 3 * 4 * ppw * maxblk <= 160 * 1024;
     }
     // a nearly empty bin (e.g. the few corner patches below m = 8) joins the
@@ -1230,7 +1230,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
         maxblk = std::max(maxblk, (foff[si + 1] - foff[si]) * (int64_t)T);
         bn.max_np = std::max(bn.max_np, pnp[si]);
       }
-      const int ppw = b == 0 ? 4 : (b == 1 ? 2 : 1);  // patches per warp at a time
+      const int ppw = vanka_tma_bin_ppw(b);  // patches per warp at a time
       const int tp = (int)std::max<int64_t>(4 * ppw, std::min<int64_t>(64, 8192 / std::max<int64_t>(maxblk, 1)));
       bn.tp = tp;
       bn.ntiles = (bn.count + tp - 1) / tp;

@@ -45,7 +45,7 @@ cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y
 
 // A bin of patches solved by the bulk-copy kernel: storage patches
 // [start, start + count), all with m in the bin's range.
-constexpr int kTmaBins = 4;
+constexpr int kTmaBins = 5;
 struct TmaBin {
   int start = 0, count = 0, tp = 0, ntiles = 0, grid = 0;
   int fac_bytes = 0, dof_bytes = 0, rhs_elems = 0, max_np = 0;
@@ -104,6 +104,7 @@ size_t vanka_tma_smem(const DevPatches& p, const TmaBin& bn, size_t elem);
 cudaError_t vanka_prepare_kernels();
 int vanka_tma_blocks_per_sm(const DevPatches& p, const TmaBin& bn, int b, size_t elem);
 int vanka_tma_bin_of(int m);
+int vanka_tma_bin_ppw(int b);
 
 template <typename T>
 cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st);

@@ -370,9 +370,9 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     }
     return;
   }
-  constexpr int PPW = 32 / LP;  // patches a warp holds at a time
+  constexpr int PPW = 32 / LP;  // patches a warp holds at a time (lanes past PPW*LP idle)
   T* myrhs = rhsb + (size_t)warp * rhs_elems;
-  const int slot = lane / LP, l = lane % LP;
+  const int slot = lane / LP, l = lane % LP, gbase = slot * LP;
   const int nblk = shared ? 1 : DIM;
   int k = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
       __syncwarp();
       for (int jb = j0; jb < j1; jb += PPW) {
         const int j = jb + slot;
-        const bool valid = j < j1;
+        const bool valid = slot < PPW && j < j1;
         const int4 mt = smeta[valid ? j : jb];
         const int m = mt.y & 0xffff, np = mt.y >> 16, base = mt.x;
         const int mu = DIM * m;
@@ -465,8 +465,13 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
           T part = T(0);
           if (kk < np)
             for (int row = l; row < mu; row += LP) part += U[kk * mu + row] * bb[row];
+          // fixed tree over the LP lanes of the group, then broadcast from its first lane
 #pragma unroll
-          for (int o = LP / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+          for (int o = 1; o < LP; o <<= 1) {
+            const T v = __shfl_down_sync(0xffffffffu, part, o);
+            if ((l & (2 * o - 1)) == 0 && l + o < LP) part += v;
+          }
+          part = __shfl_sync(0xffffffffu, part, gbase < 32 ? gbase : 0);
           tk[kk] = kk < np ? bb[mu + kk] - part : T(0);
         }
 #pragma unroll
@@ -502,9 +507,8 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
   }
 }
 
-// (lanes per patch, rows per lane) of TMA bin b; bins hold m <= 8, 32, 64, 96.
-__host__ __device__ constexpr int bin_lp(int b) { return b == 0 ? 8 : (b == 1 ? 16 : 32); }
-__host__ __device__ constexpr int bin_r(int b) { return b == 0 ? 1 : (b == 1 ? 2 : (b == 2 ? 2 : 3)); }
+// Bins (lanes per patch LP, rows per lane R): m <= 6 (6, 1), m <= 20 (10, 2),
+// m <= 32 (16, 2), m <= 64 (32, 2), m <= 96 (32, 3).
 
 template <typename T, typename TR, int DIM, int NPM, int LP, int R>
 static cudaError_t launch_tma_bin(const DevPatches& p, const TmaBin& bn, const TR* r, T* yp, cudaStream_t st) {
@@ -520,9 +524,10 @@ template <typename T, typename TR, int DIM, int NPM>
 static cudaError_t launch_bin_np(const DevPatches& p, int b, const TR* r, T* yp, cudaStream_t st) {
   const TmaBin& bn = p.bins[b];
   switch (b) {
-    case 0: return launch_tma_bin<T, TR, DIM, NPM, 8, 1>(p, bn, r, yp, st);
-    case 1: return launch_tma_bin<T, TR, DIM, NPM, 16, 2>(p, bn, r, yp, st);
-    case 2: return launch_tma_bin<T, TR, DIM, NPM, 32, 2>(p, bn, r, yp, st);
+    case 0: return launch_tma_bin<T, TR, DIM, NPM, 6, 1>(p, bn, r, yp, st);
+    case 1: return launch_tma_bin<T, TR, DIM, NPM, 10, 2>(p, bn, r, yp, st);
+    case 2: return launch_tma_bin<T, TR, DIM, NPM, 16, 2>(p, bn, r, yp, st);
+    case 3: return launch_tma_bin<T, TR, DIM, NPM, 32, 2>(p, bn, r, yp, st);
     default: return launch_tma_bin<T, TR, DIM, NPM, 32, 3>(p, bn, r, yp, st);
   }
 }
@@ -549,9 +554,10 @@ size_t vanka_tma_smem(const DevPatches& p, const TmaBin& bn, size_t elem) {
 template <typename T, int DIM, int NPM>
 static const void* tma_kernel_ptr(int b) {
   switch (b) {
-    case 0: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 8, 1>;
-    case 1: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 16, 2>;
-    case 2: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 32, 2>;
+    case 0: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 6, 1>;
+    case 1: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 10, 2>;
+    case 2: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 16, 2>;
+    case 3: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 32, 2>;
     default: return (const void*)k_vanka_apply_tma<T, T, DIM, NPM, 32, 3>;
   }
 }
@@ -572,7 +578,10 @@ int vanka_tma_blocks_per_sm(const DevPatches& p, const TmaBin& bn, int b, size_t
   return e == cudaSuccess ? nb : 0;
 }
 
-int vanka_tma_bin_of(int m) { return m <= 8 ? 0 : (m <= 32 ? 1 : (m <= 64 ? 2 : (m <= 96 ? 3 : -1))); }
+int vanka_tma_bin_of(int m) {
+  return m <= 6 ? 0 : (m <= 20 ? 1 : (m <= 32 ? 2 : (m <= 64 ? 3 : (m <= 96 ? 4 : -1))));
+}
+int vanka_tma_bin_ppw(int b) { return b == 0 ? 5 : (b == 1 ? 3 : (b == 2 ? 2 : 1)); }
 
 template <typename T, typename TR>
 cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {

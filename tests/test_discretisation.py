@@ -158,3 +158,28 @@ def test_scott_vogelius_transfers():
     D = pr.Mcg.diagonal()
     ev = np.linalg.eigvals(pr.Mcg.toarray() / D[:, None]).real
     assert ev.min() >= 0.5 - 1e-12 and ev.max() <= 2.0 + 1e-12
+
+
+def test_3d_meshes_and_operators():
+    """Kuhn cube and Bey's red refinement: the cells tile the cube, the eight
+    children of a tetrahedron have equal volume; the 3D Taylor-Hood K0 is
+    symmetric with the pressure constant as null vector, 1^T B = 0 on
+    interior velocity columns, and interior patches hold the 65 P2 nodes of a
+    vertex star (196 DoFs)."""
+    mesh = M.unit_cube(3)
+    vol = M.cell_measure(mesh.x, mesh.cells)
+    assert abs(vol.sum() - 1.0) < 1e-13 and vol.min() > 0
+    V = M.P2Space(mesh)
+    fc, _ = M.uniform_refine_cells(V)
+    fv = M.cell_measure(V.x, fc).reshape(-1, 8)
+    assert np.allclose(fv, vol[:, None] / 8.0, rtol=1e-12)
+    pr = stokes.build_th(M.unit_cube(4), bc="lid", max_levels=3)
+    K = pr.K[0]
+    off = pr.field_off[0]
+    assert abs(K - K.T).max() < 1e-14
+    one = np.zeros(K.shape[0])
+    one[off[3]:] = 1.0
+    assert np.abs(K @ one).max() < 1e-13
+    B = K[off[3]:off[4], : off[3]]
+    assert np.abs(np.asarray(B.sum(axis=0)).ravel()).max() < 1e-13
+    assert np.diff(pr.patches[0].ptr).max() == 196
