@@ -697,9 +697,14 @@ int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
     if (sizeof(T) != 8) TRY(L_zero<double>(h, L0.n, x0d));
   }
   // DC residual in FP64: d = eta (r - K0 x), then R0 (Eq. interp)
-  if (h->disc == STOKES_TH) {  // R0 = injection, fused into the residual
+  if (h->disc == STOKES_TH && L0.Pident) {  // R0 = injection, fused into the residual
     TRY((L_spmv<double, double, double, T, double>(h, L0.K, L0.K.v64, x0d, r64, reinterpret_cast<T*>(L1.b),
                                                    SPMV_SCALED_RES, h->eta_u, h->eta_p, h->kind0)));
+  } else if (h->disc == STOKES_TH) {  // a general R0 = P0^T (HO-AMG hierarchies)
+    TRY((L_spmv<double, double, double, double, double>(h, L0.K, L0.K.v64, x0d, r64, h->d0buf, SPMV_SCALED_RES,
+                                                        h->eta_u, h->eta_p, h->kind0)));
+    TRY((L_spmv<double, double, double, T, double>(h, L0.R, L0.R.v64, h->d0buf, (const double*)nullptr,
+                                                   reinterpret_cast<T*>(L1.b), SPMV_SET)));
   } else {
     TRY(restrict0_sv(h, x0d, r64));
   }
@@ -968,8 +973,6 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       if (p->P[l].nrows != p->K[l].nrows || p->P[l].ncols != p->K[l + 1].nrows)
         return fail(STOKES_ERR_INVALID_ARG, "P size mismatch on level " + std::to_string(l));
     }
-    if (h->disc == STOKES_TH && !is_identity(&p->P[0]))
-      return fail(STOKES_ERR_INVALID_ARG, "Taylor-Hood P0 must be the identity");
     if (h->disc == STOKES_SV) {
       if (!p->R0p || !p->Mcg) return fail(STOKES_ERR_INVALID_ARG, "Scott-Vogelius problems need R0p and Mcg");
       TRY(check_csr(p->R0p, "R0p"));
@@ -1330,6 +1333,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
   }
   if (h->disc == STOKES_SV) TRY(setup_sv(h, probs, ninst, dim));
   if (h->prec == STOKES_FP32) TRY(dalloc(h, &h->x0_64, (size_t)h->lv[0].n));
+  if (!h->d0buf) TRY(dalloc(h, &h->d0buf, (size_t)h->lv[0].n));
   // level-0 row kinds and Dirichlet mask
   {
     std::vector<uint8_t> kind(h->lv[0].n), dir(h->lv[0].n);

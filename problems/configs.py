@@ -86,3 +86,13 @@ def c5(count=64, lo=32, hi=192, seed=5000, workers=None):
     for i, p in zip(order, built):
         out[i] = p
     return out
+
+
+# HO-AMG (Alg. 1 applied to K0, the remark of Sec. 3.2): a standard V-cycle
+# on K0, so eta = 1; omega from the oracle's search on the 16^2 and 32^2 lid
+# problems (0.70 best on both).
+HO_AMG_TH2D = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=1.0, omega=0.70)
+
+
+def ho_amg_th2d(n=16):
+    return stokes.build_ho_amg(M.unit_square(n), nu=1.0, bc="lid", name=f"HO-AMG TH2D {n}^2 lid")

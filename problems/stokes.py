@@ -322,6 +322,38 @@ def manufactured_2d(nu=1.0):
     return u, p, f
 
 
+def build_ho_amg(mesh, nu=1.0, bc="lid", rhs="zero", seed=None, max_levels=10, max_coarse=50, name="ho-amg"):
+    """HO-AMG (the remark in Sec. 3.2): Alg. 1 applied directly to the
+    Taylor-Hood operator K0 - scalar SA on each velocity block of K0 and on
+    the P1 pressure Laplacian, block-diagonal P_l, Galerkin coarse operators.
+    The cycle is then the standard V-cycle on K0 (eta = 1, R0 = P0^T)."""
+    d = mesh.dim
+    exact = {}
+    rhs_fn = None
+    if rhs == "manufactured":
+        u, p, f = manufactured_2d(nu)
+        rhs_fn = f
+        exact = dict(u=u, p=p)
+    k0 = taylor_hood_K0(mesh, nu, bc, rhs_fn=rhs_fn)
+    V, n2, npres, bnd = k0["V"], k0["n2"], k0["npres"], k0["bnd"]
+    A0 = k0["K"][:n2, :n2].tocsr()
+    Ap = pressure_laplacian(mesh)
+    Ks, Ps, offs, Bp = build_hierarchy(k0["K"], A0, Ap, d, n2, npres, max_levels, max_coarse)
+    K, P, field_off = Ks, Ps, offs
+    bpat = {0: k0["Bpat"]}
+    patches = [make_patches(K[l], field_off[l], d, Bpattern=bpat.get(l)) for l in range(len(K) - 1)]
+    L = len(K)
+    cn = np.zeros(K[-1].shape[0])
+    offL = field_off[-1]
+    cn[offL[d]:offL[d + 1]] = Bp[L - 1]
+    prob = Problem(name=name, dim=d, disc=TH, nu=nu, K=K, P=P, field_off=field_off, patches=patches, b=k0["b"],
+                   coarse_null=cn, dirichlet=np.concatenate([bnd] * d + [np.zeros(npres, bool)]), Mp=k0["Mp"],
+                   exact=exact)
+    prob.lambda_A, prob.lambda_S = dlsc_bounds(K, field_off, d)
+    prob.info = dict(mesh=mesh, V=V, n2=n2, npres=npres, Mu=k0["Mu"], ho_amg=True)
+    return prob
+
+
 def build_th(mesh, nu=1.0, bc="lid", rhs="zero", seed=None, max_levels=10,
              max_coarse=50, name="th"):
     """Taylor-Hood P2/P1 K0 with its P1isoP2/P1 K1 and the Alg. 1 hierarchy."""

@@ -241,3 +241,23 @@ def test_c2_full_size_fp32_solve(sd, c2):
     assert abs(res[sd.STOKES_FP32][0] - res[sd.STOKES_FP64][0]) <= 2
     # the two solutions agree to the accuracy the 1e-8 residual allows
     assert rel(res[sd.STOKES_FP32][1], res[sd.STOKES_FP64][1]) < 1e-5
+
+
+def test_ho_amg_cycle_and_solve(sd):
+    """HO-AMG (Alg. 1 applied directly to K0): the cycle runs with a general
+    R0 = P0^T; FP64 parity and FP32 FGMRES within +-2 iterations."""
+    pr = configs.ho_amg_th2d(16)
+    prm = dict(configs.HO_AMG_TH2D)
+    h64 = sd.stokes_setup(pr, dict(prm, precision=sd.STOKES_FP64))
+    sd.stokes_factor_patches(h64)
+    o = make_oracle(pr, prm)
+    r = np.random.default_rng(16).standard_normal(pr.b.size)
+    z = torch.empty(r.size, dtype=torch.float64, device="cuda")
+    sd.stokes_vcycle(h64, dev(r), z)
+    assert rel(host(z), o.apply(r)) < 1e-12
+    _, its_o, _ = krylov.fgmres(pr.K[0], pr.b, o.apply, rtol=1e-8, restart=30, maxit=200)
+    h32 = sd.stokes_setup(pr, dict(prm, precision=sd.STOKES_FP32))
+    sd.stokes_factor_patches(h32)
+    x = torch.zeros(pr.b.size, dtype=torch.float64, device="cuda")
+    rc, info = sd.stokes_fgmres_solve(h32, dev(pr.b), x, rtol=1e-8, restart=30, maxit=200)
+    assert rc == sd.STOKES_OK and info[0][2] <= 1e-8 and abs(info[0][0] - its_o) <= 2

@@ -82,3 +82,15 @@ def test_patches_th_structure():
             assert np.array_equal(dofs[:m] - off[0], dofs[m:2 * m] - off[1])
             assert not pr.dirichlet[dofs].any()
             assert np.all(np.diff(dofs[:m]) > 0)
+
+
+def test_ho_amg_hierarchy():
+    """Alg. 1 on K0 directly: block-diagonal SA interpolation of the P2
+    velocity and P1 pressure, Galerkin coarse operators, null vector."""
+    pr = stokes.build_ho_amg(M.unit_square(16), bc="lid")
+    assert pr.nlevels >= 3
+    for l in range(1, pr.nlevels):
+        Kc = (pr.P[l - 1].T @ pr.K[l - 1] @ pr.P[l - 1]).tocsr()
+        assert abs(Kc - pr.K[l]).max() < 1e-12 * abs(pr.K[l]).max()
+    KL = pr.K[-1]
+    assert np.abs(KL @ pr.coarse_null).max() < 1e-12 * np.abs(KL).max() * np.linalg.norm(pr.coarse_null)
