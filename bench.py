@@ -34,6 +34,9 @@ WORKLOAD = ("2D Taylor-Hood P2/P1 Stokes, unit square 256x256 squares split by t
             "manufactured u = curl(sin^2(pi x) sin^2(pi y)), p = cos(pi x) cos(pi y); FP32 DC-all V(1,1) "
             "additive-Vanka cycle on the P1isoP2/P1 SA hierarchy, FGMRES(30) to 1e-8 true relative residual")
 METRIC = "Stokes solves/s to 1e-8 rel-res (FP32 DC-AMG preconditioned FGMRES)"
+# dram__bytes_read.sum + dram__bytes_write.sum of one level-0 FP32 apply launch, from the ncu
+# capture summarised in profiles/vanka_apply_tma_c2_level0.md (set to None when the kernel changes)
+APPLY_L0_DRAM_BYTES = 76.7e6
 
 
 def dist_env():
@@ -302,9 +305,10 @@ def run_gpu(args):
                    "fp32_GBps": vc[sd.STOKES_FP32][1] / vc[sd.STOKES_FP32][0] / 1e6,
                    "fp64_GBps": vc[sd.STOKES_FP64][1] / vc[sd.STOKES_FP64][0] / 1e6,
                    "fp32_frac_of_measured_hbm": vc[sd.STOKES_FP32][1] / vc[sd.STOKES_FP32][0] / 1e6 / peak},
-        "roofline": {"kernel": "k_vanka_apply_warp (level 0, FP32)", "bound": "hbm", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": None, "bytes_per_launch": kbytes, "avg_launch_ms": kms},
+        "roofline": {"kernel": "k_vanka_apply_tma (level 0, FP32, 66,049 patches)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_kind, "traffic": APPLY_L0_DRAM_BYTES,
+                     "bytes_per_launch": kbytes, "avg_launch_ms": kms},
         "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(16 * n),
                 "d2h_bytes_per_step": int(8 * n), "true_relres": e2e_res},
         "gpu_launches": int(launches),
