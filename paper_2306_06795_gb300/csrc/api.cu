@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -140,6 +141,10 @@ struct stokes_handle {
   void* flush = nullptr;
   size_t flush_bytes = 0;
   int64_t launches = 0;       // kernels launched so far
+  FgState fg{};               // device-side FGMRES state
+  int* hstat = nullptr;       // pinned: running flag after each Arnoldi step
+  std::vector<cudaEvent_t> ev_iter;
+  std::map<std::tuple<int, double, int>, cudaGraphExec_t> iter_graphs;
   int cycle_launches = -1;    // kernels in one DC cycle (from the ledger)
   std::vector<void*> allocs;
   std::vector<int*> err_flags;  // device error flags of every bulk-copy pipeline
@@ -817,6 +822,10 @@ void stokes_destroy(stokes_handle* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : h->iter_graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& e : h->ev_iter)
+    if (e) cudaEventDestroy(e);
+  if (h->hstat) cudaFreeHost(h->hstat);
   for (void* p : h->allocs) cudaFree(p);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -1484,7 +1493,9 @@ int check_pipeline_errors(stokes_handle* h) {
 
 int ensure_krylov(stokes_handle* h, int m) {
   if (h->krylov_m >= m && h->V) return STOKES_OK;
+  if (h->ninst > 1024) return fail(STOKES_ERR_INVALID_ARG, "at most 1024 instances per handle");
   const int64_t n = h->lv[0].n;
+  const int ni = h->ninst;
   h->krylov_m = m;
   h->ldh = m + 2;
   h->ldp = m + 2;
@@ -1492,9 +1503,29 @@ int ensure_krylov(stokes_handle* h, int m) {
   TRY(dalloc(h, &h->Z, (size_t)m * n));
   TRY(dalloc(h, &h->w, (size_t)n));
   TRY(dalloc(h, &h->partial, (size_t)h->nchunks * h->ldp));
-  TRY(dalloc(h, &h->hd, (size_t)h->ninst * h->ldh));
-  TRY(dalloc(h, &h->yd, (size_t)h->ninst * h->ldh));
-  TRY(dalloc(h, &h->actd, (size_t)h->ninst));
+  TRY(dalloc(h, &h->hd, (size_t)ni * h->ldh));
+  TRY(dalloc(h, &h->yd, (size_t)ni * h->ldh));
+  TRY(dalloc(h, &h->actd, (size_t)ni));
+  FgState& f = h->fg;
+  TRY(dalloc(h, &f.H, (size_t)ni * (m + 1) * m));
+  TRY(dalloc(h, &f.cs, (size_t)ni * m));
+  TRY(dalloc(h, &f.sn, (size_t)ni * m));
+  TRY(dalloc(h, &f.g, (size_t)ni * (m + 1)));
+  TRY(dalloc(h, &f.bnorm, (size_t)ni));
+  TRY(dalloc(h, &f.scale, (size_t)ni));
+  TRY(dalloc(h, &f.y, (size_t)ni * h->ldh));
+  TRY(dalloc(h, &f.run, (size_t)ni));
+  TRY(dalloc(h, &f.its, (size_t)ni));
+  TRY(dalloc(h, &f.kcol, (size_t)ni));
+  TRY(dalloc(h, &f.err, 1));
+  TRY(dalloc(h, &f.stat, (size_t)m + 1));
+  if (h->hstat) cudaFreeHost(h->hstat);
+  CK(cudaHostAlloc(reinterpret_cast<void**>(&h->hstat), sizeof(int) * (m + 1), cudaHostAllocDefault));
+  h->ev_iter.resize(m);
+  for (auto& e : h->ev_iter)
+    if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (auto& kv : h->iter_graphs) cudaGraphExecDestroy(kv.second);
+  h->iter_graphs.clear();
   return STOKES_OK;
 }
 
@@ -1505,6 +1536,67 @@ int seg_dots(stokes_handle* h, const double* V, int64_t ldv, int ncols, const do
   return STOKES_OK;
 }
 
+// One Arnoldi step j (Sec. 4, right-preconditioned flexible GMRES):
+// z_j = M_dc^-1 v_j (the DC cycle), w = K0 z_j, classical Gram-Schmidt twice,
+// device-side Givens update and v_{j+1} = w / ||w|| for running instances;
+// the running flag lands in pinned host memory (hstat[j]).
+int arnoldi_step(stokes_handle* h, int j, double rtol, int maxit) {
+  const int64_t n = h->lv[0].n;
+  const int ni = h->ninst;
+  Level& L0 = h->lv[0];
+  double* vj = h->V + (size_t)j * n;
+  double* zj = h->Z + (size_t)j * n;
+  TRY(run_cycle(h, vj, zj));
+  CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, zj, zj, h->w, SPMV_SET, 0, 0, nullptr, h->st)));
+  TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+  CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
+  TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+  CK(multidot_partial(h->nchunks, h->cbeg, h->cend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
+  CK(multidot_finish(ni, h->sc_beg, h->sc_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
+  CK(fg_update(ni, h->krylov_m, j, h->fg, h->yd, h->hd, h->ldh, rtol, maxit, h->st));
+  CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st));
+  CK(cudaMemcpyAsync(h->hstat + j, h->fg.stat + j, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  return STOKES_OK;
+}
+
+// The Arnoldi step of column j as a CUDA graph (captured once per column,
+// tolerance and iteration cap).
+int iter_graph(stokes_handle* h, int j, double rtol, int maxit, cudaGraphExec_t* out) {
+  auto key = std::make_tuple(j, rtol, maxit);
+  auto it = h->iter_graphs.find(key);
+  if (it != h->iter_graphs.end()) {
+    *out = it->second;
+    return STOKES_OK;
+  }
+  if (h->cycle_launches < 0) {
+    h->led = Ledger();
+    h->led.count = true;
+    int rc0 = run_cycle(h, h->V, h->Z);
+    h->led.count = false;
+    TRY(rc0);
+    h->cycle_launches = h->led.launches;
+  }
+  // kernel attributes are set at setup, so capture can start right away
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+  int rc = arnoldi_step(h, j, rtol, maxit);
+  cudaError_t ec = cudaStreamEndCapture(h->st, &g);
+  if (rc != STOKES_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  CK(ec);
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  CK(ei);
+  h->iter_graphs[key] = ge;
+  *out = ge;
+  return STOKES_OK;
+}
+
 }  // namespace
 
 extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x, double rtol, int32_t restart,
@@ -1512,132 +1604,66 @@ extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x,
   if (!h || !b || !x || restart < 1 || maxit < 0 || !(rtol > 0)) return fail(STOKES_ERR_INVALID_ARG, "fgmres arguments");
   if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
   const int m = restart;
+  if (h->krylov_m != m) {
+    h->krylov_m = 0;
+    h->V = nullptr;
+  }
   TRY(ensure_krylov(h, m));
   const int ni = h->ninst;
   const int64_t n = h->lv[0].n;
   Level& L0 = h->lv[0];
-  std::vector<double> bnorm(ni), beta(ni), hbuf((size_t)ni * h->ldh);
-  std::vector<int> its(ni, 0), done(ni, 0), active(ni, 0);
-  std::vector<std::vector<double>> H(ni, std::vector<double>((size_t)(m + 1) * m)), cs(ni, std::vector<double>(m)),
-      sn(ni, std::vector<double>(m)), g(ni, std::vector<double>(m + 1));
-  std::vector<int> kcol(ni, 0), running(ni, 0);
   TRY(join_in(h));
+  CK(cudaMemsetAsync(h->fg.its, 0, sizeof(int) * ni, h->st));
+  CK(cudaMemsetAsync(h->fg.err, 0, sizeof(int), h->st));
   // ||b|| per instance
   TRY(seg_dots(h, b, 0, 1, b, 0));
-  CK(cudaMemcpyAsync(hbuf.data(), h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
-  for (int s = 0; s < ni; ++s) bnorm[s] = std::sqrt(hbuf[(size_t)s * h->ldh]);
+  CK(fg_start(ni, m, h->fg, h->hd, h->ldh, rtol, maxit, 1, h->st));
   int status = STOKES_OK;
   while (true) {
-    // true residual r = b - K0 x into V_0
+    // true residual r = b - K0 x into V_0, its norms, the start of a cycle
     CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, x, b, h->V, SPMV_RES, 0, 0, nullptr, h->st)));
     TRY(seg_dots(h, h->V, 0, 1, h->V, 0));
-    CK(cudaMemcpyAsync(hbuf.data(), h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
+    CK(fg_start(ni, m, h->fg, h->hd, h->ldh, rtol, maxit, 0, h->st));
+    CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->V, h->V, h->fg.scale, h->st));
+    CK(cudaMemcpyAsync(h->hstat + m, h->fg.stat + m, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    bool any = false;
-    for (int s = 0; s < ni; ++s) {
-      beta[s] = std::sqrt(hbuf[(size_t)s * h->ldh]);
-      if (!std::isfinite(beta[s])) return fail(STOKES_ERR_NAN, "non-finite residual");
-      done[s] = (bnorm[s] == 0.0) || beta[s] <= rtol * bnorm[s];
-      active[s] = !done[s] && its[s] < maxit;
-      any = any || active[s];
-    }
-    if (!any) break;
-    CK(cudaMemcpyAsync(h->actd, active.data(), sizeof(int) * ni, cudaMemcpyHostToDevice, h->st));
-    // V_0 = r / beta (inactive instances get zero)
-    CK(seg_scale(h->nchunks, h->cbeg, h->cend, h->cseg, h->V, h->V, h->hd, h->ldh, 0, h->actd, 1, h->st));
-    for (int s = 0; s < ni; ++s) {
-      std::fill(g[s].begin(), g[s].end(), 0.0);
-      g[s][0] = beta[s];
-      kcol[s] = 0;
-      running[s] = active[s];
-    }
+    if (!h->hstat[m]) break;
+    // Arnoldi steps: step j is queued before the flag of step j-1 is read,
+    // so the device never waits for the host; a step queued after every
+    // instance stopped works on zero vectors and changes nothing
+    int last = -1;
     for (int j = 0; j < m; ++j) {
-      double* vj = h->V + (size_t)j * n;
-      double* zj = h->Z + (size_t)j * n;
       cudaGraphExec_t ge;
-      TRY(cycle_graph(h, vj, zj, &ge));
+      TRY(iter_graph(h, j, rtol, maxit, &ge));
       CK(cudaGraphLaunch(ge, h->st));
-      h->launches += h->cycle_launches + 14;  // cycle + SpMV, 2x(dots, finish, axpy), norm, copies, scale
-      CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, zj, zj, h->w, SPMV_SET, 0, 0, nullptr, h->st)));
-      // classical Gram-Schmidt, twice
-      TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-      CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
-      CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
-      TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-      CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
-      // h = first pass + second pass; column j+1 holds ||w||^2
-      CK(multidot_partial(h->nchunks, h->cbeg, h->cend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
-      CK(multidot_finish(ni, h->sc_beg, h->sc_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
-      CK(cudaMemcpyAsync(hbuf.data(), h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
-      std::vector<double> first((size_t)ni * h->ldh);
-      CK(cudaMemcpyAsync(first.data(), h->yd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
-      CK(cudaStreamSynchronize(h->st));
-      // per-instance Arnoldi column and Givens update (host)
-      bool any_running = false;
-      std::vector<int> act2(ni, 0);
-      std::vector<double> hnorm(ni, 0.0);
-      for (int s = 0; s < ni; ++s) {
-        if (!running[s]) continue;
-        double* Hs = H[s].data();
-        for (int i = 0; i <= j; ++i) Hs[(size_t)i * m + j] = first[(size_t)s * h->ldh + i] + hbuf[(size_t)s * h->ldh + i];
-        const double hn = std::sqrt(first[(size_t)s * h->ldh + j + 1]);
-        hnorm[s] = hn;
-        Hs[(size_t)(j + 1) * m + j] = hn;
-        double hmax = 0.0;
-        for (int i = 0; i <= j; ++i) hmax = std::max(hmax, std::fabs(Hs[(size_t)i * m + j]));
-        const bool breakdown = !(hn > 1e-14 * std::max(hmax, 1e-300));
-        for (int i = 0; i < j; ++i) {
-          const double t = cs[s][i] * Hs[(size_t)i * m + j] + sn[s][i] * Hs[(size_t)(i + 1) * m + j];
-          Hs[(size_t)(i + 1) * m + j] = -sn[s][i] * Hs[(size_t)i * m + j] + cs[s][i] * Hs[(size_t)(i + 1) * m + j];
-          Hs[(size_t)i * m + j] = t;
-        }
-        const double den = std::hypot(Hs[(size_t)j * m + j], Hs[(size_t)(j + 1) * m + j]);
-        cs[s][j] = Hs[(size_t)j * m + j] / den;
-        sn[s][j] = Hs[(size_t)(j + 1) * m + j] / den;
-        Hs[(size_t)j * m + j] = den;
-        Hs[(size_t)(j + 1) * m + j] = 0.0;
-        g[s][j + 1] = -sn[s][j] * g[s][j];
-        g[s][j] = cs[s][j] * g[s][j];
-        its[s]++;
-        kcol[s] = j + 1;
-        if (!std::isfinite(g[s][j + 1])) return fail(STOKES_ERR_NAN, "non-finite Arnoldi value");
-        if (std::fabs(g[s][j + 1]) <= rtol * bnorm[s] || breakdown || its[s] >= maxit) running[s] = 0;
-        act2[s] = running[s];
-        any_running = any_running || running[s];
+      h->launches += h->cycle_launches + 14;
+      CK(cudaEventRecord(h->ev_iter[j], h->st));
+      last = j;
+      if (j > 0) {
+        CK(cudaEventSynchronize(h->ev_iter[j - 1]));
+        if (!h->hstat[j - 1]) break;
       }
-      if (!any_running || j + 1 == m) break;
-      // V_{j+1} = w / ||w|| for the instances still running
-      CK(cudaMemcpyAsync(h->actd, act2.data(), sizeof(int) * ni, cudaMemcpyHostToDevice, h->st));
-      CK(seg_scale(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->yd, h->ldh, j + 1,
-                   h->actd, 1, h->st));
     }
-    // x += Z y per instance (y from the triangular system)
-    int kmax = 0;
-    std::vector<double> ycoef((size_t)ni * h->ldh, 0.0);
-    for (int s = 0; s < ni; ++s) {
-      if (!active[s]) continue;
-      const int k = kcol[s];
-      kmax = std::max(kmax, k);
-      std::vector<double> y(k, 0.0);
-      for (int i = k - 1; i >= 0; --i) {
-        double v = g[s][i];
-        for (int q = i + 1; q < k; ++q) v -= H[s][(size_t)i * m + q] * y[q];
-        y[i] = v / H[s][(size_t)i * m + i];
-      }
-      for (int i = 0; i < k; ++i) ycoef[(size_t)s * h->ldh + i] = y[i];
-    }
-    CK(cudaMemcpyAsync(h->yd, ycoef.data(), sizeof(double) * ni * h->ldh, cudaMemcpyHostToDevice, h->st));
-    CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, kmax, h->Z, n, h->yd, h->ldh, 1.0, x, h->st));
+    // x += Z y per instance
+    CK(fg_solve(ni, m, h->fg, h->ldh, h->st));
+    CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, m, h->Z, n, h->fg.y, h->ldh, 1.0, x, h->st));
+    (void)last;
   }
   TRY(check_pipeline_errors(h));
+  std::vector<int> its(ni), ferr(1);
+  CK(cudaMemcpyAsync(its.data(), h->fg.its, sizeof(int) * ni, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(ferr.data(), h->fg.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   // final true residuals
   CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, x, b, h->w, SPMV_RES, 0, 0, nullptr, h->st)));
   TRY(seg_dots(h, h->w, 0, 1, h->w, 0));
+  std::vector<double> hbuf((size_t)ni * h->ldh), bn(ni);
   CK(cudaMemcpyAsync(hbuf.data(), h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(bn.data(), h->fg.bnorm, sizeof(double) * ni, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  if (ferr[0]) return fail(STOKES_ERR_NAN, "non-finite value in the Krylov iteration");
   for (int s = 0; s < ni; ++s) {
-    const double rr = bnorm[s] > 0 ? std::sqrt(hbuf[(size_t)s * h->ldh]) / bnorm[s] : 0.0;
+    const double rr = bn[s] > 0 ? std::sqrt(hbuf[(size_t)s * h->ldh]) / bn[s] : 0.0;
+    if (!std::isfinite(rr)) return fail(STOKES_ERR_NAN, "non-finite residual");
     const int st = rr <= rtol ? STOKES_OK : STOKES_NOT_CONVERGED;
     if (st != STOKES_OK) status = STOKES_NOT_CONVERGED;
     if (info) {

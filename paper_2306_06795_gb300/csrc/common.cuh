@@ -171,6 +171,30 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
 cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
                       const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
                       cudaStream_t st);
+// Device state of restarted FGMRES, per instance.
+struct FgState {
+  double* H;      // [ninst][(m+1)*m], row i column j at i*m + j
+  double* cs;     // [ninst][m]
+  double* sn;     // [ninst][m]
+  double* g;      // [ninst][m+1]
+  double* bnorm;  // [ninst]
+  double* scale;  // [ninst] factor of the next Krylov vector (0 when stopped)
+  double* y;      // [ninst][ldh] coefficients of x += Z y
+  int* run;       // [ninst]
+  int* its;       // [ninst]
+  int* kcol;      // [ninst]
+  int* err;       // [1] non-finite value seen
+  int* stat;      // [m+1] any instance running after step j (index m: after the start)
+};
+cudaError_t fg_start(int ninst, int m, const FgState& st, const double* h, int ldh, double rtol, int maxit, int first,
+                     cudaStream_t s);
+cudaError_t fg_update(int ninst, int m, int j, const FgState& st, const double* h1, const double* h2, int ldh,
+                      double rtol, int maxit, cudaStream_t s);
+cudaError_t fg_solve(int ninst, int m, const FgState& st, int ldh, cudaStream_t s);
+// out[row] = in[row] * f[seg(row)] (0 when f is 0)
+cudaError_t seg_mul(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, const double* in,
+                    double* out, const double* f, cudaStream_t s);
+
 // out[row] = in[row] * scale_inv(seg)  where scale_inv = (den[seg*ldd + kd] > 0 && active[seg]) ? 1/den : 0
 cudaError_t seg_scale(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg,
                       const double* in, double* out, const double* den, int ldd, int kd,
