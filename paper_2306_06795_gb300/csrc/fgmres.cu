@@ -11,7 +11,7 @@ namespace sd {
 
 
 // Start of a restart cycle: h[s*ldh] = ||r_s||^2.
-__global__ void k_fg_start(int ninst, int m, FgState st, const double* __restrict__ h, int ldh, double rtol, int maxit,
+__global__ void __launch_bounds__(256) k_fg_start(int ninst, int m, FgState st, const double* __restrict__ h, int ldh, double rtol, int maxit,
                            int first) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
@@ -37,7 +37,7 @@ __global__ void k_fg_start(int ninst, int m, FgState st, const double* __restric
 
 // Arnoldi step j: column j of H from the two Gram-Schmidt passes (h1 in
 // h1buf, h2 in h2buf, ||w||^2 in h1buf[j+1]), Givens update, convergence.
-__global__ void k_fg_update(int ninst, int m, int j, FgState st, const double* __restrict__ h1buf,
+__global__ void __launch_bounds__(256) k_fg_update(int ninst, int m, int j, FgState st, const double* __restrict__ h1buf,
                             const double* __restrict__ h2buf, int ldh, double rtol, int maxit) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
@@ -113,12 +113,12 @@ __global__ void __launch_bounds__(256) k_seg_mul(const int64_t* __restrict__ cbe
 
 cudaError_t fg_start(int ninst, int m, const FgState& st, const double* h, int ldh, double rtol, int maxit, int first,
                      cudaStream_t s) {
-  k_fg_start<<<1, 1024, 0, s>>>(ninst, m, st, h, ldh, rtol, maxit, first);
+  k_fg_start<<<1, 256, 0, s>>>(ninst, m, st, h, ldh, rtol, maxit, first);
   return cudaGetLastError();
 }
 cudaError_t fg_update(int ninst, int m, int j, const FgState& st, const double* h1, const double* h2, int ldh,
                       double rtol, int maxit, cudaStream_t s) {
-  k_fg_update<<<1, 1024, 0, s>>>(ninst, m, j, st, h1, h2, ldh, rtol, maxit);
+  k_fg_update<<<1, 256, 0, s>>>(ninst, m, j, st, h1, h2, ldh, rtol, maxit);
   return cudaGetLastError();
 }
 cudaError_t fg_solve(int ninst, int m, const FgState& st, int ldh, cudaStream_t s) {
