@@ -141,6 +141,8 @@ struct stokes_handle {
   void* flush = nullptr;
   size_t flush_bytes = 0;
   int64_t launches = 0;       // kernels launched so far
+  int tail_l0 = -1;           // first level of the single-CTA coarse tail (-1: none)
+  TailLevel* tail_dev = nullptr;
   FgState fg{};               // device-side FGMRES state
   int* hstat = nullptr;       // pinned: running flag after each Arnoldi step
   std::vector<cudaEvent_t> ev_iter;
@@ -635,10 +637,28 @@ int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_gues
 // input lv[l].b, output lv[l].x.  Instances whose coarsest level is l take
 // the exact bordered solve on their segment.
 template <typename T>
-int vcycle(stokes_handle* h, int l) {
+int vcycle(stokes_handle* h, int l, bool no_tail = false);
+
+// The small trailing levels l0 .. L-1 in one single-CTA launch.
+template <typename T>
+int tail(stokes_handle* h, int l) {
+  if (h->led.count) {
+    // the same algorithmic bytes as the level-by-level path, one launch
+    const int before = h->led.launches;
+    TRY(vcycle<T>(h, l, true));
+    h->led.launches = before + 1;
+    return STOKES_OK;
+  }
+  CK(tail_cycle<T>(h->tail_dev, h->L - l, h->nu1, h->nu2, h->st));
+  return STOKES_OK;
+}
+
+template <typename T>
+int vcycle(stokes_handle* h, int l, bool no_tail) {
   Level& L = h->lv[l];
   T* x = reinterpret_cast<T*>(L.x);
   T* b = reinterpret_cast<T*>(L.b);
+  if (!no_tail && l == h->tail_l0) return tail<T>(h, l);
   if (l == h->L - 1) return L_coarse<T>(h, L, b, x);
   const bool relax_here = (L.has_patches || L.dlsc) && !(h->schedule == STOKES_DC_SKIP1 && l == 1);
   if (relax_here) TRY(relax<T>(h, l, x, b, h->nu1, true));
@@ -648,7 +668,7 @@ int vcycle(stokes_handle* h, int l) {
   Level& C = h->lv[l + 1];
   TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
   TRY((L_spmv<T, T, T, T, T>(h, L.R, kval<T>(L.R), r, (const T*)nullptr, reinterpret_cast<T*>(C.b), SPMV_SET)));
-  TRY(vcycle<T>(h, l + 1));
+  TRY(vcycle<T>(h, l + 1, no_tail));
   TRY((L_spmv<T, T, T, T, T>(h, L.P, kval<T>(L.P), reinterpret_cast<const T*>(C.x), (const T*)nullptr, x, SPMV_ADD)));
   if (relax_here) TRY(relax<T>(h, l, x, b, h->nu2, false));
   return STOKES_OK;
@@ -938,6 +958,70 @@ static int setup_sv(stokes_handle* h, const stokes_problem* const* probs, int ni
   h->ncg = ncg;
   h->mcg_lo = probs[0]->mcg_lo;
   h->mcg_hi = probs[0]->mcg_hi;
+  return STOKES_OK;
+}
+
+// The coarse tail: the first level l0 >= 2 from which every level is small
+// (at most 16384 rows), relaxes with Vanka (or not at all) and has patches
+// of at most 128 velocity DoFs per component and 4 seeds.
+static int setup_tail(stokes_handle* h) {
+  int l0 = -1;
+  for (int l = h->L - 1; l >= 2; --l) {
+    const Level& L = h->lv[l];
+    const bool ok = L.n <= 16384 && !L.dlsc && (!L.has_patches || (L.pat.max_m <= 128 && L.pat.max_np <= 4));
+    if (!ok) break;
+    l0 = l;
+  }
+  if (l0 < 0 || l0 == h->L - 1) return STOKES_OK;  // nothing to fuse beyond a single coarse solve
+  std::vector<TailLevel> tv;
+  const bool f32 = h->prec == STOKES_FP32;
+  auto csr = [&](const DevCSR& A) {
+    TailCSR t;
+    t.rowptr = A.rowptr;
+    t.col = A.col;
+    t.val = f32 ? (const void*)A.v32 : (const void*)A.v64;
+    t.nrows = A.nrows;
+    return t;
+  };
+  for (int l = l0; l < h->L; ++l) {
+    const Level& L = h->lv[l];
+    TailLevel t{};
+    t.n = (int)L.n;
+    t.dim = h->dim;
+    t.K = csr(L.K);
+    if (l + 1 < h->L) {
+      t.R = csr(L.R);
+      t.P = csr(L.P);
+    }
+    if (L.has_patches) {
+      t.npatch = L.pat.npatch;
+      t.shared = L.pat.shared;
+      t.ptr = L.pat.ptr;
+      t.dof = L.pat.dof;
+      t.nvel = L.pat.nvel;
+      t.npres = L.pat.npres;
+      t.foff = L.pat.foff;
+      t.fac = L.pat.fac;
+      t.tptr = L.pat.tptr;
+      t.tslot = L.pat.tslot;
+    }
+    t.omega = L.omega;
+    t.nblocks = L.coarse.nblocks;
+    t.boff = L.coarse.boff;
+    t.bn = L.coarse.bn;
+    t.koff = L.coarse.koff;
+    t.Kinv = L.coarse.Kinv;
+    t.x = L.x;
+    t.b = L.b;
+    t.r = L.r;
+    t.yp = L.yp;
+    tv.push_back(t);
+  }
+  TailLevel* d = nullptr;
+  TRY(dalloc(h, &d, tv.size()));
+  CK(cudaMemcpy(d, tv.data(), sizeof(TailLevel) * tv.size(), cudaMemcpyHostToDevice));
+  h->tail_dev = d;
+  h->tail_l0 = l0;
   return STOKES_OK;
 }
 
@@ -1231,7 +1315,6 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     dp.nslots = (int64_t)pdof.size();
     // bulk-copy tiles per bin: about 8 KB of factors per stage (at least one
     // patch per consumer lane group), 3 stages
-    dp.stages = 3;
     for (int b = 0; b < kTmaBins; ++b) {
       TmaBin& bn = dp.bins[b];
       bn.start = bin_start[b];
@@ -1285,7 +1368,13 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
         if (bn.count == 0) continue;
         if (vanka_tma_smem(dp, bn, T) > 220 * 1024)
           return fail(STOKES_ERR_INVALID_ARG, "patch tiles exceed shared memory");
-        const int nb = vanka_tma_blocks_per_sm(dp, bn, b, T);
+        // a 2-stage ring when it keeps clearly more CTAs (consumer warps) per SM
+        bn.stages = 3;
+        int nb = vanka_tma_blocks_per_sm(dp, bn, b, T);
+        bn.stages = 2;
+        const int nb2 = vanka_tma_blocks_per_sm(dp, bn, b, T);
+        if (nb2 * 2 >= nb * 3) nb = nb2;
+        else bn.stages = 3;
         if (nb < 1) return fail(STOKES_ERR_INVALID_ARG, "patch tiles do not fit on an SM");
         bn.grid = std::min(bn.ntiles, nsm * nb);
       }
@@ -1341,6 +1430,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     lv.x = x; lv.b = b; lv.r = r; lv.ta = ta; lv.tb = tb;
   }
   if (h->disc == STOKES_SV) TRY(setup_sv(h, probs, ninst, dim));
+  TRY(setup_tail(h));
   if (h->prec == STOKES_FP32) TRY(dalloc(h, &h->x0_64, (size_t)h->lv[0].n));
   if (!h->d0buf) TRY(dalloc(h, &h->d0buf, (size_t)h->lv[0].n));
   // level-0 row kinds and Dirichlet mask

@@ -47,7 +47,7 @@ cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y
 // [start, start + count), all with m in the bin's range.
 constexpr int kTmaBins = 5;
 struct TmaBin {
-  int start = 0, count = 0, tp = 0, ntiles = 0, grid = 0;
+  int start = 0, count = 0, tp = 0, ntiles = 0, grid = 0, stages = 3;
   int fac_bytes = 0, dof_bytes = 0, rhs_elems = 0, max_np = 0;
 };
 
@@ -73,7 +73,6 @@ struct DevPatches {
   int64_t nslots = 0;
   // bulk-copy bins (storage order: bins by m, then the CTA-per-patch rest)
   int4* meta = nullptr;   // [npatch] {ptr, m | np << 16, foff lo, foff hi}
-  int stages = 3;
   bool use_tma = false;
   TmaBin bins[kTmaBins];
   int* err = nullptr;     // device error flags of the pipelines
@@ -171,6 +170,35 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
 cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
                       const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
                       cudaStream_t st);
+// A level of the single-CTA coarse tail (tail.cu): device pointers only.
+struct TailCSR {
+  const int* rowptr;
+  const int* col;
+  const void* val;  // values in the cycle precision
+  int nrows;
+};
+struct TailLevel {
+  int n, dim, shared, npatch;
+  TailCSR K, R, P;
+  const int* ptr;
+  const int* dof;
+  const int* nvel;
+  const int* npres;
+  const int64_t* foff;
+  const void* fac;
+  const int* tptr;
+  const int* tslot;
+  double omega;
+  int nblocks;
+  const int* boff;
+  const int* bn;
+  const int64_t* koff;
+  const double* Kinv;
+  void *x, *b, *r, *yp;
+};
+template <typename T>
+cudaError_t tail_cycle(const TailLevel* lv, int nl, int nu1, int nu2, cudaStream_t st);
+
 // Device state of restarted FGMRES, per instance.
 struct FgState {
   double* H;      // [ninst][(m+1)*m], row i column j at i*m + j

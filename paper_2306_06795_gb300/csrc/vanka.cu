@@ -512,10 +512,10 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
 
 template <typename T, typename TR, int DIM, int NPM, int LP, int R>
 static cudaError_t launch_tma_bin(const DevPatches& p, const TmaBin& bn, const TR* r, T* yp, cudaStream_t st) {
-  const size_t shm = 128 + (size_t)p.stages * (bn.fac_bytes + bn.dof_bytes + bn.tp * 16) +
+  const size_t shm = 128 + (size_t)bn.stages * (bn.fac_bytes + bn.dof_bytes + bn.tp * 16) +
                      (size_t)kNCW * bn.rhs_elems * sizeof(T);
   k_vanka_apply_tma<T, TR, DIM, NPM, LP, R><<<bn.grid, 32 * (kNCW + 1), shm, st>>>(
-      bn.start, bn.count, bn.ntiles, bn.tp, p.stages, bn.fac_bytes, bn.dof_bytes, bn.rhs_elems, p.shared, p.meta,
+      bn.start, bn.count, bn.ntiles, bn.tp, bn.stages, bn.fac_bytes, bn.dof_bytes, bn.rhs_elems, p.shared, p.meta,
       p.ptr, p.foff, p.dof, reinterpret_cast<const T*>(p.fac), r, yp, p.err);
   return cudaGetLastError();
 }
@@ -548,7 +548,8 @@ static cudaError_t apply_tma_bins(const DevPatches& p, const TR* r, T* yp, cudaS
 
 // Shared-memory bytes of a TMA bin's tile configuration.
 size_t vanka_tma_smem(const DevPatches& p, const TmaBin& bn, size_t elem) {
-  return 128 + (size_t)p.stages * (bn.fac_bytes + bn.dof_bytes + bn.tp * 16) + (size_t)kNCW * bn.rhs_elems * elem;
+  (void)p;
+  return 128 + (size_t)bn.stages * (bn.fac_bytes + bn.dof_bytes + bn.tp * 16) + (size_t)kNCW * bn.rhs_elems * elem;
 }
 
 template <typename T, int DIM, int NPM>
