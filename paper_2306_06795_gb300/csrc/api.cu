@@ -141,8 +141,6 @@ struct stokes_handle {
   void* flush = nullptr;
   size_t flush_bytes = 0;
   int64_t launches = 0;       // kernels launched so far
-  int tail_l0 = -1;           // first level of the single-CTA coarse tail (-1: none)
-  TailLevel* tail_dev = nullptr;
   FgState fg{};               // device-side FGMRES state
   int* hstat = nullptr;       // pinned: running flag after each Arnoldi step
   std::vector<cudaEvent_t> ev_iter;
@@ -637,28 +635,10 @@ int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_gues
 // input lv[l].b, output lv[l].x.  Instances whose coarsest level is l take
 // the exact bordered solve on their segment.
 template <typename T>
-int vcycle(stokes_handle* h, int l, bool no_tail = false);
-
-// The small trailing levels l0 .. L-1 in one single-CTA launch.
-template <typename T>
-int tail(stokes_handle* h, int l) {
-  if (h->led.count) {
-    // the same algorithmic bytes as the level-by-level path, one launch
-    const int before = h->led.launches;
-    TRY(vcycle<T>(h, l, true));
-    h->led.launches = before + 1;
-    return STOKES_OK;
-  }
-  CK(tail_cycle<T>(h->tail_dev, h->L - l, h->nu1, h->nu2, h->st));
-  return STOKES_OK;
-}
-
-template <typename T>
-int vcycle(stokes_handle* h, int l, bool no_tail) {
+int vcycle(stokes_handle* h, int l) {
   Level& L = h->lv[l];
   T* x = reinterpret_cast<T*>(L.x);
   T* b = reinterpret_cast<T*>(L.b);
-  if (!no_tail && l == h->tail_l0) return tail<T>(h, l);
   if (l == h->L - 1) return L_coarse<T>(h, L, b, x);
   const bool relax_here = (L.has_patches || L.dlsc) && !(h->schedule == STOKES_DC_SKIP1 && l == 1);
   if (relax_here) TRY(relax<T>(h, l, x, b, h->nu1, true));
@@ -668,7 +648,7 @@ int vcycle(stokes_handle* h, int l, bool no_tail) {
   Level& C = h->lv[l + 1];
   TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
   TRY((L_spmv<T, T, T, T, T>(h, L.R, kval<T>(L.R), r, (const T*)nullptr, reinterpret_cast<T*>(C.b), SPMV_SET)));
-  TRY(vcycle<T>(h, l + 1, no_tail));
+  TRY(vcycle<T>(h, l + 1));
   TRY((L_spmv<T, T, T, T, T>(h, L.P, kval<T>(L.P), reinterpret_cast<const T*>(C.x), (const T*)nullptr, x, SPMV_ADD)));
   if (relax_here) TRY(relax<T>(h, l, x, b, h->nu2, false));
   return STOKES_OK;
@@ -958,70 +938,6 @@ static int setup_sv(stokes_handle* h, const stokes_problem* const* probs, int ni
   h->ncg = ncg;
   h->mcg_lo = probs[0]->mcg_lo;
   h->mcg_hi = probs[0]->mcg_hi;
-  return STOKES_OK;
-}
-
-// The coarse tail: the first level l0 >= 2 from which every level is small
-// (at most 16384 rows), relaxes with Vanka (or not at all) and has patches
-// of at most 128 velocity DoFs per component and 4 seeds.
-static int setup_tail(stokes_handle* h) {
-  int l0 = -1;
-  for (int l = h->L - 1; l >= 2; --l) {
-    const Level& L = h->lv[l];
-    const bool ok = L.n <= 16384 && !L.dlsc && (!L.has_patches || (L.pat.max_m <= 128 && L.pat.max_np <= 4));
-    if (!ok) break;
-    l0 = l;
-  }
-  if (l0 < 0 || l0 == h->L - 1) return STOKES_OK;  // nothing to fuse beyond a single coarse solve
-  std::vector<TailLevel> tv;
-  const bool f32 = h->prec == STOKES_FP32;
-  auto csr = [&](const DevCSR& A) {
-    TailCSR t;
-    t.rowptr = A.rowptr;
-    t.col = A.col;
-    t.val = f32 ? (const void*)A.v32 : (const void*)A.v64;
-    t.nrows = A.nrows;
-    return t;
-  };
-  for (int l = l0; l < h->L; ++l) {
-    const Level& L = h->lv[l];
-    TailLevel t{};
-    t.n = (int)L.n;
-    t.dim = h->dim;
-    t.K = csr(L.K);
-    if (l + 1 < h->L) {
-      t.R = csr(L.R);
-      t.P = csr(L.P);
-    }
-    if (L.has_patches) {
-      t.npatch = L.pat.npatch;
-      t.shared = L.pat.shared;
-      t.ptr = L.pat.ptr;
-      t.dof = L.pat.dof;
-      t.nvel = L.pat.nvel;
-      t.npres = L.pat.npres;
-      t.foff = L.pat.foff;
-      t.fac = L.pat.fac;
-      t.tptr = L.pat.tptr;
-      t.tslot = L.pat.tslot;
-    }
-    t.omega = L.omega;
-    t.nblocks = L.coarse.nblocks;
-    t.boff = L.coarse.boff;
-    t.bn = L.coarse.bn;
-    t.koff = L.coarse.koff;
-    t.Kinv = L.coarse.Kinv;
-    t.x = L.x;
-    t.b = L.b;
-    t.r = L.r;
-    t.yp = L.yp;
-    tv.push_back(t);
-  }
-  TailLevel* d = nullptr;
-  TRY(dalloc(h, &d, tv.size()));
-  CK(cudaMemcpy(d, tv.data(), sizeof(TailLevel) * tv.size(), cudaMemcpyHostToDevice));
-  h->tail_dev = d;
-  h->tail_l0 = l0;
   return STOKES_OK;
 }
 
@@ -1430,7 +1346,6 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     lv.x = x; lv.b = b; lv.r = r; lv.ta = ta; lv.tb = tb;
   }
   if (h->disc == STOKES_SV) TRY(setup_sv(h, probs, ninst, dim));
-  TRY(setup_tail(h));
   if (h->prec == STOKES_FP32) TRY(dalloc(h, &h->x0_64, (size_t)h->lv[0].n));
   if (!h->d0buf) TRY(dalloc(h, &h->d0buf, (size_t)h->lv[0].n));
   // level-0 row kinds and Dirichlet mask
@@ -1638,13 +1553,25 @@ int arnoldi_step(stokes_handle* h, int j, double rtol, int maxit) {
   double* zj = h->Z + (size_t)j * n;
   TRY(run_cycle(h, vj, zj));
   CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, zj, zj, h->w, SPMV_SET, 0, 0, nullptr, h->st)));
-  TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
-  CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
-  TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
-  CK(multidot_partial(h->nchunks, h->cbeg, h->cend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
-  CK(multidot_finish(ni, h->sc_beg, h->sc_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
+  if (j + 1 <= 32) {
+    // h1 = V^T w; [w -= V h1, h2 = V^T w] fused; [w -= V h2, ||w||^2] fused
+    TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+    CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
+    CK(axpy_dot(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->yd, h->ldh, -1.0, h->w, j + 1, 0,
+                h->partial, h->ldp, h->st));
+    CK(multidot_finish(ni, h->sc_beg, h->sc_end, j + 1, h->partial, h->ldp, h->hd, h->ldh, 0, h->st));
+    CK(axpy_dot(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, 0, 1, h->partial,
+                h->ldp, h->st));
+    CK(multidot_finish(ni, h->sc_beg, h->sc_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
+  } else {
+    TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+    CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+    CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
+    TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+    CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+    CK(multidot_partial(h->nchunks, h->cbeg, h->cend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
+    CK(multidot_finish(ni, h->sc_beg, h->sc_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
+  }
   CK(fg_update(ni, h->krylov_m, j, h->fg, h->yd, h->hd, h->ldh, rtol, maxit, h->st));
   CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st));
   CK(cudaMemcpyAsync(h->hstat + j, h->fg.stat + j, sizeof(int), cudaMemcpyDeviceToHost, h->st));

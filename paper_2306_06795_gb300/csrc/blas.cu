@@ -279,6 +279,68 @@ cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, con
   return cudaGetLastError();
 }
 
+// grid: nchunks.  w <- w + sign * sum_k coef[seg*ldh + k] V_k (k < ncols), then,
+// with the updated w, partial[c*ldp + k] = sum_rows V_k w (k < ndot) and
+// partial[c*ldp + ndot] = sum_rows w^2 when with_norm: one pass over V
+// for a Gram-Schmidt update and the next pass's dot products.
+constexpr int kMaxCols = 32;
+__global__ void __launch_bounds__(kRedThreads, 2) k_axpy_dot(const int64_t* __restrict__ cbeg,
+    const int64_t* __restrict__ cend, const int* __restrict__ cseg, int ncols, const double* __restrict__ V,
+    int64_t ldv, const double* __restrict__ coef, int ldh, double sign, double* __restrict__ w, int ndot,
+    int with_norm, double* __restrict__ partial, int ldp) {
+  __shared__ double red[kRedThreads / 32][kMaxCols + 1];
+  const int c = blockIdx.x;
+  const double* cf = coef + cseg[c] * ldh;
+  const int nout = ndot + (with_norm ? 1 : 0);
+  double acc[kMaxCols + 1];
+#pragma unroll
+  for (int k = 0; k <= kMaxCols; ++k) acc[k] = 0.0;
+  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kRedThreads) {
+    double s = 0.0;
+    for (int k0 = 0; k0 < ncols; k0 += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = k0 + u < ncols ? V[(int64_t)(k0 + u) * ldv + r] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < ncols) s += cf[k0 + u] * v[u];
+    }
+    const double wn = w[r] + sign * s;
+    w[r] = wn;
+#pragma unroll
+    for (int k = 0; k < kMaxCols; ++k)
+      if (k < ndot) acc[k] += V[(int64_t)k * ldv + r] * wn;
+    if (with_norm) acc[kMaxCols] += wn * wn;
+  }
+  // fixed-order block reduction of every output
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k <= kMaxCols; ++k) {
+    const bool use = k < ndot || (k == kMaxCols && with_norm);
+    if (!use) continue;
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nout; k += kRedThreads) {
+    const int kk = k < ndot ? k : kMaxCols;
+    double v = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) v += red[q][kk];
+    partial[(int64_t)c * ldp + k] = v;
+  }
+}
+cudaError_t axpy_dot(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
+                     const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w, int ndot,
+                     int with_norm, double* partial, int ldp, cudaStream_t st) {
+  if (nchunks == 0) return cudaSuccess;
+  if (ndot > kMaxCols || ncols > kMaxCols) return cudaErrorInvalidValue;
+  k_axpy_dot<<<nchunks, kRedThreads, 0, st>>>(cbeg, cend, cseg, ncols, V, ldv, coef, ldh, sign, w, ndot, with_norm,
+                                              partial, ldp);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_seg_scale(const int64_t* __restrict__ cbeg,
     const int64_t* __restrict__ cend, const int* __restrict__ cseg, const double* __restrict__ in,
     double* __restrict__ out, const double* __restrict__ den, int ldd, int kd, const int* __restrict__ active,

@@ -170,35 +170,6 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
 cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
                       const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
                       cudaStream_t st);
-// A level of the single-CTA coarse tail (tail.cu): device pointers only.
-struct TailCSR {
-  const int* rowptr;
-  const int* col;
-  const void* val;  // values in the cycle precision
-  int nrows;
-};
-struct TailLevel {
-  int n, dim, shared, npatch;
-  TailCSR K, R, P;
-  const int* ptr;
-  const int* dof;
-  const int* nvel;
-  const int* npres;
-  const int64_t* foff;
-  const void* fac;
-  const int* tptr;
-  const int* tslot;
-  double omega;
-  int nblocks;
-  const int* boff;
-  const int* bn;
-  const int64_t* koff;
-  const double* Kinv;
-  void *x, *b, *r, *yp;
-};
-template <typename T>
-cudaError_t tail_cycle(const TailLevel* lv, int nl, int nu1, int nu2, cudaStream_t st);
-
 // Device state of restarted FGMRES, per instance.
 struct FgState {
   double* H;      // [ninst][(m+1)*m], row i column j at i*m + j
@@ -223,6 +194,11 @@ cudaError_t fg_solve(int ninst, int m, const FgState& st, int ldh, cudaStream_t 
 cudaError_t seg_mul(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, const double* in,
                     double* out, const double* f, cudaStream_t s);
 
+// w += sign * V coef (ncols columns), then partial dots of the new w with
+// V_0..V_{ndot-1} (and its squared norm at index ndot when with_norm)
+cudaError_t axpy_dot(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
+                     const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w, int ndot,
+                     int with_norm, double* partial, int ldp, cudaStream_t st);
 // out[row] = in[row] * scale_inv(seg)  where scale_inv = (den[seg*ldd + kd] > 0 && active[seg]) ? 1/den : 0
 cudaError_t seg_scale(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg,
                       const double* in, double* out, const double* den, int ldd, int kd,

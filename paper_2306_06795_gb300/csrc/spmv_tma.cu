@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(32 * (kSpNCW + 1), 4) k_spmv_tma(
       mbar_init(full + s, 1);
       mbar_init(empty + s, kSpNCW);
     }
+    *reinterpret_cast<volatile int*>(empty + STAGES) = 0;  // consumer abort flag
     mbar_fence_init();
   }
   __syncthreads();
@@ -72,38 +73,49 @@ __global__ void __launch_bounds__(32 * (kSpNCW + 1), 4) k_spmv_tma(
     }
     return;
   }
+  const int ct = threadIdx.x;  // consumer thread 0 .. 32*kSpNCW-1
+  constexpr int NC = 32 * kSpNCW;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + STAGES);
   int k = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     const int s = k % STAGES;
+    // the consumer warps agree on a timed-out wait and leave together, so no
+    // warp is left waiting at the named barrier
     if (!mbar_wait(full + s, (k / STAGES) & 1)) {
       atomicOr(err, 2);
-      return;
+      *abort_flag = 1;
     }
-    const unsigned char* st = stage0 + (size_t)s * stage_bytes;
-    const TA* sv = reinterpret_cast<const TA*>(st);
+    asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
+    if (*abort_flag) return;
+    unsigned char* st = stage0 + (size_t)s * stage_bytes;
+    TA* sv = reinterpret_cast<TA*>(st);
     const int* sc = reinterpret_cast<const int*>(st + val_bytes);
     const int* sp = reinterpret_cast<const int*>(st + val_bytes + col_bytes);
     const int r0 = trow[t], r1 = trow[t + 1];
     const int p0 = r0 / 4 * 4;
-    const int n0 = sp[r0 - p0];
+    const int n0 = sp[r0 - p0], n1 = sp[r1 - p0];
     const int va0 = n0 / VA * VA, c0 = n0 / 4 * 4;
-    for (int r = r0 + warp * 32 + lane; r < r1; r += 32 * kSpNCW) {
+    // products of the whole tile in place, consecutive entries per thread
+    // group (conflict-free), eight x-gathers in flight per thread
+    for (int q0 = n0 + ct; q0 < n1; q0 += 8 * NC) {
+      TX xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * NC;
+        xv[u] = x[q < n1 ? sc[q - c0] : 0];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * NC;
+        if (q < n1) sv[q - va0] = TA(TACC(sv[q - va0]) * TACC(xv[u]));
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");  // consumer warps only
+    // each row summed in its stored order by one thread
+    for (int r = r0 + ct; r < r1; r += NC) {
       const int a = sp[r - p0], e = sp[r + 1 - p0];
       TACC sum = TACC(0);
-      // eight independent gathers of x in flight per lane, then the products
-      // in the row's order
-      for (int q = a; q < e; q += 8) {
-        TA v[8];
-        TX xv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const bool ok = q + u < e;
-          v[u] = ok ? sv[q + u - va0] : TA(0);
-          xv[u] = x[ok ? sc[q + u - c0] : 0];
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) sum += TACC(v[u]) * TACC(xv[u]);
-      }
+      for (int q = a; q < e; ++q) sum += TACC(sv[q - va0]);
       if (MODE == SPMV_SET) {
         y[r] = TY(sum);
       } else if (MODE == SPMV_RES) {
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(32 * (kSpNCW + 1), 4) k_spmv_tma(
         y[r] = TY(sc2 * (TACC(b[r]) - sum));
       }
     }
-    __syncwarp();
+    asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
     if (lane == 0) mbar_arrive(empty + s);
   }
 }
