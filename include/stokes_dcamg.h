@@ -161,7 +161,8 @@ int stokes_vcycle(stokes_handle* h, const double* r_dev, double* z_dev);
  * FP64) or maxit iterations.  x_dev holds the initial guess on entry and
  * the solution on exit.  info[ninstances] (may be NULL) receives per
  * instance the iterations, status and true relative residual.  Returns
- * STOKES_NOT_CONVERGED when any instance missed rtol. */
+ * STOKES_NOT_CONVERGED when any instance missed rtol, STOKES_ERR_INVALID_ARG
+ * for restart outside 1..1024, maxit < 0 or rtol <= 0. */
 int stokes_fgmres_solve(stokes_handle* h, const double* b_dev, double* x_dev,
                         double rtol, int32_t restart, int32_t maxit,
                         stokes_solve_info* info);

@@ -135,9 +135,11 @@ struct stokes_handle {
   int64_t* cbeg = nullptr;
   int64_t* cend = nullptr;
   int* cseg = nullptr;
-  int* sc_beg = nullptr;
-  int* sc_end = nullptr;
-  std::vector<int> h_sc_beg, h_sc_end;
+  int ndchunks = 0;  // larger chunks of the dot products
+  int64_t* dbeg = nullptr;
+  int64_t* dend = nullptr;
+  int* sd_beg = nullptr;
+  int* sd_end = nullptr;
   void* flush = nullptr;
   size_t flush_bytes = 0;
   int64_t launches = 0;       // kernels launched so far
@@ -183,9 +185,14 @@ int choose_tpr(int64_t nnz, int nrows) {
   return 32;
 }
 
-// Operators with at least this many rows use the bulk-copy SpMV.
-constexpr int kTmaRows = 32768;
+// Operators with at least this many rows and no sliced copy use the
+// bulk-copy SpMV.
+constexpr int kTmaRows = 1 << 30;
 constexpr int kTileNnz = 1024, kTileRows = 256;
+// Largest stored/nonzero ratio of a sliced-ELLPACK copy, and the fewest rows
+// for one (smaller operators keep enough warps busy with vector CSR).
+constexpr double kSellMaxPad = 1.25;
+constexpr int kSellRows = 262144;
 
 int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
   d.nrows = c.nrows;
@@ -206,9 +213,40 @@ int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
     TRY(upload(h, &d.v32, v32));
   }
   d.tpr = choose_tpr(d.nnz, d.nrows);
-  // tiles for the bulk-copy SpMV
   int maxrow = 0;
   for (int i = 0; i < c.nrows; ++i) maxrow = std::max(maxrow, c.rowptr[i + 1] - c.rowptr[i]);
+  // sliced ELLPACK copy when the padding to the longest row of each chunk
+  // of 32 rows stays small
+  if (c.nrows >= kSellRows) {
+    const int nch = (c.nrows + 31) / 32;
+    std::vector<int64_t> off(nch + 1, 0);
+    for (int ch = 0; ch < nch; ++ch) {
+      int w = 0;
+      for (int i = ch * 32; i < std::min(c.nrows, ch * 32 + 32); ++i) w = std::max(w, c.rowptr[i + 1] - c.rowptr[i]);
+      off[ch + 1] = off[ch] + 32 * (int64_t)w;
+    }
+    if ((double)off[nch] <= kSellMaxPad * (double)std::max<int64_t>(d.nnz, 1)) {
+      std::vector<int> scol(off[nch], -1);  // padding: column -1
+      std::vector<double> sval(off[nch], 0.0);
+      for (int i = 0; i < c.nrows; ++i) {
+        const int64_t base = off[i / 32] + (i % 32);
+        for (int k = c.rowptr[i]; k < c.rowptr[i + 1]; ++k) {
+          scol[base + 32 * (int64_t)(k - c.rowptr[i])] = c.col[k];
+          sval[base + 32 * (int64_t)(k - c.rowptr[i])] = c.val[k];
+        }
+      }
+      TRY(upload(h, &d.soff, off));
+      TRY(upload(h, &d.scol, scol));
+      TRY(upload(h, &d.sv64, sval));
+      if (h->prec == STOKES_FP32) {
+        std::vector<float> s32(sval.begin(), sval.end());
+        TRY(upload(h, &d.sv32, s32));
+      }
+      d.schunks = nch;
+      return STOKES_OK;
+    }
+  }
+  // tiles for the bulk-copy SpMV
   if (c.nrows >= kTmaRows && maxrow <= kTileNnz - 8) {
     std::vector<int> trow{0};
     int vb = 0, vb32 = 0, cb = 0, pb = 0;
@@ -1301,10 +1339,13 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       int optin = 0, dev = 0;
       CK(cudaGetDevice(&dev));
       CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      std::vector<int> fl, fg;
+      std::vector<int> fl, fg, fw[3];
       int msm = 0;
       for (int si = 0; si < npatch; ++si) {
-        if (vanka_factor_smem(dim, pnv[si], max_np, T, false) <= (size_t)optin) {
+        const int wb = vanka_factor_warp_bin(pnv[si]);
+        if (wb >= 0) {
+          fw[wb].push_back(si);
+        } else if (vanka_factor_smem(dim, pnv[si], max_np, T, false) <= (size_t)optin) {
           fl.push_back(si);
           msm = std::max(msm, pnv[si]);
         } else {
@@ -1314,6 +1355,10 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       dp.nfac_smem = (int)fl.size();
       dp.max_m_fac_smem = msm;
       fl.insert(fl.end(), fg.begin(), fg.end());
+      for (int b = 2; b >= 0; --b) {
+        dp.nfac_warp[b] = (int)fw[b].size();
+        fl.insert(fl.begin(), fw[b].begin(), fw[b].end());
+      }
       TRY(upload(h, &dp.fac_list, fl));
       if (!fg.empty()) {
         if (vanka_factor_smem(dim, max_m, max_np, T, true) > (size_t)optin)
@@ -1363,29 +1408,35 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     TRY(upload(h, &h->kind0, kind));
     TRY(upload(h, &h->dir0, dir));
   }
-  // FGMRES chunks (never straddling an instance)
-  {
+  // FGMRES chunks (never straddling an instance): 512 rows (two per thread
+  // of a 256-thread block) for the updates, 2048 rows for the dot products,
+  // whose block reductions then cost a small share of their FP64 work
+  for (int t = 0; t < 2; ++t) {
     std::vector<int64_t> cb, ce;
-    std::vector<int> cs;
-    h->h_sc_beg.assign(ninst, 0);
-    h->h_sc_end.assign(ninst, 0);
-    const int64_t CH = 2048;  // ~300 chunks for 0.6 M rows: every SM busy
+    std::vector<int> cs, sb(ninst, 0), se(ninst, 0);
+    const int64_t CH = t == 0 ? 512 : 2048;
     for (int k = 0; k < ninst; ++k) {
       const int64_t o = h->lv[0].seg_off[k], n = probs[k]->K[0].nrows;
-      h->h_sc_beg[k] = (int)cb.size();
+      sb[k] = (int)cb.size();
       for (int64_t s = 0; s < n; s += CH) {
         cb.push_back(o + s);
         ce.push_back(o + std::min(n, s + CH));
         cs.push_back(k);
       }
-      h->h_sc_end[k] = (int)cb.size();
+      se[k] = (int)cb.size();
     }
-    h->nchunks = (int)cb.size();
-    TRY(upload(h, &h->cbeg, cb));
-    TRY(upload(h, &h->cend, ce));
-    TRY(upload(h, &h->cseg, cs));
-    TRY(upload(h, &h->sc_beg, h->h_sc_beg));
-    TRY(upload(h, &h->sc_end, h->h_sc_end));
+    if (t == 0) {
+      h->nchunks = (int)cb.size();
+      TRY(upload(h, &h->cbeg, cb));
+      TRY(upload(h, &h->cend, ce));
+      TRY(upload(h, &h->cseg, cs));
+    } else {
+      h->ndchunks = (int)cb.size();
+      TRY(upload(h, &h->dbeg, cb));
+      TRY(upload(h, &h->dend, ce));
+      TRY(upload(h, &h->sd_beg, sb));
+      TRY(upload(h, &h->sd_end, se));
+    }
   }
   return STOKES_OK;
 }
@@ -1536,8 +1587,8 @@ int ensure_krylov(stokes_handle* h, int m) {
 
 // per-segment dots h[s][0..ncols) = V_k . w  (fresh or accumulated)
 int seg_dots(stokes_handle* h, const double* V, int64_t ldv, int ncols, const double* w, int accumulate) {
-  CK(multidot_partial(h->nchunks, h->cbeg, h->cend, ncols, V, ldv, w, h->partial, h->ldp, h->st));
-  CK(multidot_finish(h->ninst, h->sc_beg, h->sc_end, ncols, h->partial, h->ldp, h->hd, h->ldh, accumulate, h->st));
+  CK(multidot_partial(h->ndchunks, h->dbeg, h->dend, ncols, V, ldv, w, h->partial, h->ldp, h->st));
+  CK(multidot_finish(h->ninst, h->sd_beg, h->sd_end, ncols, h->partial, h->ldp, h->hd, h->ldh, accumulate, h->st));
   return STOKES_OK;
 }
 
@@ -1553,25 +1604,14 @@ int arnoldi_step(stokes_handle* h, int j, double rtol, int maxit) {
   double* zj = h->Z + (size_t)j * n;
   TRY(run_cycle(h, vj, zj));
   CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, zj, zj, h->w, SPMV_SET, 0, 0, nullptr, h->st)));
-  if (j + 1 <= 32) {
-    // h1 = V^T w; [w -= V h1, h2 = V^T w] fused; [w -= V h2, ||w||^2] fused
-    TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-    CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
-    CK(axpy_dot(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->yd, h->ldh, -1.0, h->w, j + 1, 0,
-                h->partial, h->ldp, h->st));
-    CK(multidot_finish(ni, h->sc_beg, h->sc_end, j + 1, h->partial, h->ldp, h->hd, h->ldh, 0, h->st));
-    CK(axpy_dot(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, 0, 1, h->partial,
-                h->ldp, h->st));
-    CK(multidot_finish(ni, h->sc_beg, h->sc_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
-  } else {
-    TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-    CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
-    CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
-    TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-    CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
-    CK(multidot_partial(h->nchunks, h->cbeg, h->cend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
-    CK(multidot_finish(ni, h->sc_beg, h->sc_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
-  }
+  // h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
+  TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+  CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
+  TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
+  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+  CK(multidot_partial(h->ndchunks, h->dbeg, h->dend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
+  CK(multidot_finish(ni, h->sd_beg, h->sd_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
   CK(fg_update(ni, h->krylov_m, j, h->fg, h->yd, h->hd, h->ldh, rtol, maxit, h->st));
   CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st));
   CK(cudaMemcpyAsync(h->hstat + j, h->fg.stat + j, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -1618,7 +1658,8 @@ int iter_graph(stokes_handle* h, int j, double rtol, int maxit, cudaGraphExec_t*
 
 extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x, double rtol, int32_t restart,
                                    int32_t maxit, stokes_solve_info* info) {
-  if (!h || !b || !x || restart < 1 || maxit < 0 || !(rtol > 0)) return fail(STOKES_ERR_INVALID_ARG, "fgmres arguments");
+  if (!h || !b || !x || restart < 1 || restart > 1024 || maxit < 0 || !(rtol > 0))
+    return fail(STOKES_ERR_INVALID_ARG, "fgmres arguments");
   if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
   const int m = restart;
   if (h->krylov_m != m) {

@@ -186,36 +186,79 @@ template cudaError_t coarse_solve<double>(int, const int*, const int*, const int
 
 // ------------------------------------------------------------ reductions
 constexpr int kRedThreads = 256;
+constexpr int kMaxAxpyCols = 1024;  // Krylov columns (restart length) one multiaxpy handles
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < kRedThreads / 32; ++k) s += sh[k];
-  return s;  // valid in thread 0
-}
-
-// grid: (nchunks, ncols)
+// grid: (nchunks, ceil(ncols / 8)).  partial[c*ldp + k] = sum over the rows
+// of chunk c of V_k[row] w[row] for eight columns k per block: one row per
+// thread per step with the eight column loads in flight, then a transposed
+// butterfly (xor 16, 8, 4 halve the values a lane holds, xor 2, 1 finish)
+// reduces the eight sums of a warp in 9 additions instead of 40, and the
+// warps' sums are added in warp order.  Fixed order: deterministic.
+constexpr int kDotCols = 8;
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const int64_t* __restrict__ cbeg,
-    const int64_t* __restrict__ cend, const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
-    double* __restrict__ partial, int ldp) {
-  __shared__ double sh[kRedThreads / 32];
-  const int c = blockIdx.x, k = blockIdx.y;
-  const double* v = V + (int64_t)k * ldv;
-  double s = 0.0;
-  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kRedThreads) s += v[r] * w[r];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) partial[(int64_t)c * ldp + k] = s;
+    const int64_t* __restrict__ cend, int ncols, const double* __restrict__ V, int64_t ldv,
+    const double* __restrict__ w, double* __restrict__ partial, int ldp) {
+  __shared__ double red[kRedThreads / 32][kDotCols];
+  const int c = blockIdx.x, k0 = blockIdx.y * kDotCols;
+  const int nk = min(kDotCols, ncols - k0);
+  double acc[kDotCols];
+#pragma unroll
+  for (int u = 0; u < kDotCols; ++u) acc[u] = 0.0;
+  const double* v0 = V + (int64_t)k0 * ldv;
+  const int64_t ce = cend[c];
+  // two rows per thread per step: eighteen loads in flight
+  for (int64_t r = cbeg[c] + threadIdx.x; r < ce; r += 2 * kRedThreads) {
+    const int64_t r2 = r + kRedThreads;
+    const bool has2 = r2 < ce;
+    const double w1 = w[r], w2 = has2 ? w[r2] : 0.0;
+    double v1[kDotCols], v2[kDotCols];
+#pragma unroll
+    for (int u = 0; u < kDotCols; ++u) {
+      v1[u] = u < nk ? v0[(int64_t)u * ldv + r] : 0.0;
+      v2[u] = u < nk && has2 ? v0[(int64_t)u * ldv + r2] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kDotCols; ++u) acc[u] = fma(v2[u], w2, fma(v1[u], w1, acc[u]));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // xor 16: lanes 0-15 keep columns 0-3, lanes 16-31 columns 4-7
+  const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
+  double b4[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const double send = hi16 ? acc[u] : acc[u + 4];
+    const double keep = hi16 ? acc[u + 4] : acc[u];
+    b4[u] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  double b2[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const double send = hi8 ? b4[u] : b4[u + 2];
+    const double keep = hi8 ? b4[u + 2] : b4[u];
+    b2[u] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  double b1;
+  {
+    const double send = hi4 ? b2[0] : b2[1];
+    const double keep = hi4 ? b2[1] : b2[0];
+    b1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  b1 += __shfl_xor_sync(0xffffffffu, b1, 2);
+  b1 += __shfl_xor_sync(0xffffffffu, b1, 1);
+  // lane holds column 4*[lane&16] + 2*[lane&8] + [lane&4]
+  if ((lane & 3) == 0) red[warp][(hi16 ? 4 : 0) + (hi8 ? 2 : 0) + (hi4 ? 1 : 0)] = b1;
+  __syncthreads();
+  if (threadIdx.x < nk) {
+    double t = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) t += red[q][threadIdx.x];
+    partial[(int64_t)c * ldp + k0 + threadIdx.x] = t;
+  }
 }
 cudaError_t multidot_partial(int nchunks, const int64_t* cbeg, const int64_t* cend, int ncols, const double* V,
                              int64_t ldv, const double* w, double* partial, int ldp, cudaStream_t st) {
   if (nchunks == 0 || ncols == 0) return cudaSuccess;
-  k_multidot<<<dim3((unsigned)nchunks, (unsigned)ncols), kRedThreads, 0, st>>>(cbeg, cend, V, ldv, w, partial, ldp);
+  const unsigned gy = (unsigned)((ncols + kDotCols - 1) / kDotCols);
+  k_multidot<<<dim3((unsigned)nchunks, gy), kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp);
   return cudaGetLastError();
 }
 
@@ -246,98 +289,45 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
   return cudaGetLastError();
 }
 
-// grid: (nchunks, kAxpySplit); w[row] += sign * sum_k coef[seg*ldh + k] * V_k[row],
-// one row per thread, the columns' loads issued eight at a time
-constexpr int kAxpySplit = 8;
+// grid: nchunks.  w[row] += sign * sum_k coef[seg*ldh + k] * V_k[row]:
+// two rows per thread per step, the columns' loads issued eight at a time
+// for both rows (sixteen in flight); one DFMA per loaded element.
 __global__ void __launch_bounds__(kRedThreads) k_multiaxpy(const int64_t* __restrict__ cbeg,
     const int64_t* __restrict__ cend, const int* __restrict__ cseg, int ncols, const double* __restrict__ V,
     int64_t ldv, const double* __restrict__ coef, int ldh, double sign, double* __restrict__ w) {
+  __shared__ double cf[kMaxAxpyCols];
   const int c = blockIdx.x;
-  const double* cf = coef + cseg[c] * ldh;
-  const int64_t len = cend[c] - cbeg[c];
-  const int64_t step = (int64_t)kRedThreads * kAxpySplit;
-  for (int64_t o = (int64_t)blockIdx.y * kRedThreads + threadIdx.x; o < len; o += step) {
-    const int64_t r = cbeg[c] + o;
-    double s = 0.0;
+  for (int k = threadIdx.x; k < ncols; k += kRedThreads) cf[k] = coef[cseg[c] * ldh + k];
+  __syncthreads();
+  const int64_t ce = cend[c];
+  for (int64_t r = cbeg[c] + threadIdx.x; r < ce; r += 2 * kRedThreads) {
+    const int64_t r2 = r + kRedThreads;
+    const bool has2 = r2 < ce;
+    double s1 = 0.0, s2 = 0.0;
     for (int k0 = 0; k0 < ncols; k0 += 8) {
-      double v[8];
+      double v1[8], v2[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = k0 + u < ncols ? V[(int64_t)(k0 + u) * ldv + r] : 0.0;
+      for (int u = 0; u < 8; ++u) {
+        v1[u] = k0 + u < ncols ? V[(int64_t)(k0 + u) * ldv + r] : 0.0;
+        v2[u] = k0 + u < ncols && has2 ? V[(int64_t)(k0 + u) * ldv + r2] : 0.0;
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (k0 + u < ncols) s += cf[k0 + u] * v[u];
+        if (k0 + u < ncols) {
+          s1 = fma(cf[k0 + u], v1[u], s1);
+          s2 = fma(cf[k0 + u], v2[u], s2);
+        }
     }
-    w[r] += sign * s;
+    w[r] += sign * s1;
+    if (has2) w[r2] += sign * s2;
   }
 }
 cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
                       const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
                       cudaStream_t st) {
   if (nchunks == 0 || ncols == 0) return cudaSuccess;
-  k_multiaxpy<<<dim3((unsigned)nchunks, kAxpySplit), kRedThreads, 0, st>>>(cbeg, cend, cseg, ncols, V, ldv, coef, ldh,
-                                                                         sign, w);
-  return cudaGetLastError();
-}
-
-// grid: nchunks.  w <- w + sign * sum_k coef[seg*ldh + k] V_k (k < ncols), then,
-// with the updated w, partial[c*ldp + k] = sum_rows V_k w (k < ndot) and
-// partial[c*ldp + ndot] = sum_rows w^2 when with_norm: one pass over V
-// for a Gram-Schmidt update and the next pass's dot products.
-constexpr int kMaxCols = 32;
-__global__ void __launch_bounds__(kRedThreads, 2) k_axpy_dot(const int64_t* __restrict__ cbeg,
-    const int64_t* __restrict__ cend, const int* __restrict__ cseg, int ncols, const double* __restrict__ V,
-    int64_t ldv, const double* __restrict__ coef, int ldh, double sign, double* __restrict__ w, int ndot,
-    int with_norm, double* __restrict__ partial, int ldp) {
-  __shared__ double red[kRedThreads / 32][kMaxCols + 1];
-  const int c = blockIdx.x;
-  const double* cf = coef + cseg[c] * ldh;
-  const int nout = ndot + (with_norm ? 1 : 0);
-  double acc[kMaxCols + 1];
-#pragma unroll
-  for (int k = 0; k <= kMaxCols; ++k) acc[k] = 0.0;
-  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kRedThreads) {
-    double s = 0.0;
-    for (int k0 = 0; k0 < ncols; k0 += 8) {
-      double v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = k0 + u < ncols ? V[(int64_t)(k0 + u) * ldv + r] : 0.0;
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (k0 + u < ncols) s += cf[k0 + u] * v[u];
-    }
-    const double wn = w[r] + sign * s;
-    w[r] = wn;
-#pragma unroll
-    for (int k = 0; k < kMaxCols; ++k)
-      if (k < ndot) acc[k] += V[(int64_t)k * ldv + r] * wn;
-    if (with_norm) acc[kMaxCols] += wn * wn;
-  }
-  // fixed-order block reduction of every output
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k <= kMaxCols; ++k) {
-    const bool use = k < ndot || (k == kMaxCols && with_norm);
-    if (!use) continue;
-    double v = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][k] = v;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < nout; k += kRedThreads) {
-    const int kk = k < ndot ? k : kMaxCols;
-    double v = 0.0;
-    for (int q = 0; q < kRedThreads / 32; ++q) v += red[q][kk];
-    partial[(int64_t)c * ldp + k] = v;
-  }
-}
-cudaError_t axpy_dot(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
-                     const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w, int ndot,
-                     int with_norm, double* partial, int ldp, cudaStream_t st) {
-  if (nchunks == 0) return cudaSuccess;
-  if (ndot > kMaxCols || ncols > kMaxCols) return cudaErrorInvalidValue;
-  k_axpy_dot<<<nchunks, kRedThreads, 0, st>>>(cbeg, cend, cseg, ncols, V, ldv, coef, ldh, sign, w, ndot, with_norm,
-                                              partial, ldp);
+  if (ncols > kMaxAxpyCols) return cudaErrorInvalidValue;
+  k_multiaxpy<<<(unsigned)nchunks, kRedThreads, 0, st>>>(cbeg, cend, cseg, ncols, V, ldv, coef, ldh, sign, w);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,13 @@ struct DevCSR {
   int tile_col_bytes = 0, tile_rp_bytes = 0;
   int tma_grid32 = 0, tma_grid64 = 0;
   int* err = nullptr;
+  // sliced ELLPACK copy (large operators): chunks of 32 rows, entry k of row
+  // 32 c + i at soff[c] + 32 k + i; rows shorter than the chunk are padded
+  int schunks = 0;              // 0: no sliced copy
+  int64_t* soff = nullptr;      // [schunks+1]
+  int* scol = nullptr;
+  double* sv64 = nullptr;
+  float* sv32 = nullptr;
 };
 
 template <typename TA, typename TX, typename TB, typename TY, typename TACC>
@@ -78,12 +85,14 @@ struct DevPatches {
   int* err = nullptr;     // device error flags of the pipelines
   // factorisation: patches whose block fits in shared memory first
   int* fac_list = nullptr;
+  int nfac_warp[3] = {0, 0, 0};  // warp-per-patch bins m <= 8, 20, 32 (first in fac_list)
   int nfac_smem = 0, max_m_fac_smem = 0, fac_chunk = 256;
   void* fac_scratch = nullptr;  // fac_chunk * max_m^2 elements, when needed
   int apply_global_a = 0;       // large-bin apply reads A from global memory
 };
 
 size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool global_a);
+int vanka_factor_warp_bin(int m);  // 0, 1, 2 for m <= 8, 20, 32; -1 above
 
 }  // namespace sd
 struct stokes_handle;
@@ -194,11 +203,6 @@ cudaError_t fg_solve(int ninst, int m, const FgState& st, int ldh, cudaStream_t 
 cudaError_t seg_mul(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, const double* in,
                     double* out, const double* f, cudaStream_t s);
 
-// w += sign * V coef (ncols columns), then partial dots of the new w with
-// V_0..V_{ndot-1} (and its squared norm at index ndot when with_norm)
-cudaError_t axpy_dot(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
-                     const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w, int ndot,
-                     int with_norm, double* partial, int ldp, cudaStream_t st);
 // out[row] = in[row] * scale_inv(seg)  where scale_inv = (den[seg*ldd + kd] > 0 && active[seg]) ? 1/den : 0
 cudaError_t seg_scale(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg,
                       const double* in, double* out, const double* den, int ldd, int kd,

@@ -60,9 +60,103 @@ static cudaError_t launch_mode(const DevCSR& A, const TA* val, const TX* x, cons
   return cudaGetLastError();
 }
 
+// Sliced-ELLPACK product: a warp owns a chunk of 32 consecutive rows, one
+// row per lane, so at step k the warp reads 32 consecutive values and
+// columns (one coalesced line each, streamed past L2) and gathers x through
+// the read-only path.  Padding entries carry column -1 and are skipped, so
+// no row lengths are read.  The loop is software-pipelined: the values and
+// columns of the next U steps (8 for FP32 values, 4 for FP64) are in flight
+// while the x entries of the current U are gathered.  Each row sums its
+// entries in CSR order.
+constexpr int kSellWarps = 8;
+
+template <typename TA, typename TX, typename TB, typename TY, typename TACC, int MODE>
+__global__ void __launch_bounds__(32 * kSellWarps) k_spmv_sell(int nrows, int nchunks,
+    const int64_t* __restrict__ soff, const int* __restrict__ scol, const TA* __restrict__ sval,
+    const TX* __restrict__ x, const TB* __restrict__ b, TY* __restrict__ y, double s0, double s1,
+    const uint8_t* __restrict__ kind) {
+  const int c = blockIdx.x * kSellWarps + (threadIdx.x >> 5);
+  if (c >= nchunks) return;
+  const int lane = threadIdx.x & 31;
+  const int row = c * 32 + lane;
+  const int64_t o0 = soff[c];
+  const int w = (int)((soff[c + 1] - o0) >> 5);  // uniform over the warp
+  const TA* vp = sval + o0 + lane;
+  const int* cp = scol + o0 + lane;
+  constexpr int U = sizeof(TA) == 4 ? 8 : 4;
+  TA v[U];
+  int cc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    v[u] = u < w ? __ldcs(vp + u * 32) : TA(0);
+    cc[u] = u < w ? __ldcs(cp + u * 32) : -1;
+  }
+  TACC sum = TACC(0);
+  for (int k = 0; k < w; k += U) {
+    TA vn[U];
+    int cn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int kk = k + U + u;
+      vn[u] = kk < w ? __ldcs(vp + (int64_t)kk * 32) : TA(0);
+      cn[u] = kk < w ? __ldcs(cp + (int64_t)kk * 32) : -1;
+    }
+    TX xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : TX(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cc[u] >= 0) sum += TACC(v[u]) * TACC(xv[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = vn[u];
+      cc[u] = cn[u];
+    }
+  }
+  if (row >= nrows) return;
+  if (MODE == SPMV_SET) {
+    y[row] = TY(sum);
+  } else if (MODE == SPMV_RES) {
+    y[row] = TY(TACC(b[row]) - sum);
+  } else if (MODE == SPMV_ADD) {
+    y[row] = TY(TACC(y[row]) + sum);
+  } else {
+    const TACC sc = TACC(kind[row] == 1 ? s1 : s0);
+    y[row] = TY(sc * (TACC(b[row]) - sum));
+  }
+}
+
+template <typename TA> const TA* sell_values(const DevCSR& A);
+template <> const float* sell_values<float>(const DevCSR& A) { return A.sv32; }
+template <> const double* sell_values<double>(const DevCSR& A) { return A.sv64; }
+
+template <typename TA, typename TX, typename TB, typename TY, typename TACC>
+static cudaError_t spmv_sell(const DevCSR& A, const TA* sval, const TX* x, const TB* b, TY* y, int mode, double s0,
+                             double s1, const uint8_t* kind, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((A.schunks + kSellWarps - 1) / kSellWarps);
+  const int threads = 32 * kSellWarps;
+  switch (mode) {
+    case SPMV_SET:
+      k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_SET><<<blocks, threads, 0, st>>>(A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
+      break;
+    case SPMV_RES:
+      k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_RES><<<blocks, threads, 0, st>>>(A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
+      break;
+    case SPMV_ADD:
+      k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_ADD><<<blocks, threads, 0, st>>>(A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
+      break;
+    default:
+      k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_SCALED_RES><<<blocks, threads, 0, st>>>(A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
+  }
+  return cudaGetLastError();
+}
+
 template <typename TA, typename TX, typename TB, typename TY, typename TACC>
 cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y, int mode, double s0,
                  double s1, const uint8_t* kind, cudaStream_t st) {
+  // the sliced copy holds the same values as A.v32 / A.v64
+  if (A.schunks > 0 && sell_values<TA>(A) && (const void*)val == (const void*)(sizeof(TA) == 4 ? (const void*)A.v32 : (const void*)A.v64))
+    return spmv_sell<TA, TX, TB, TY, TACC>(A, sell_values<TA>(A), x, b, y, mode, s0, s1, kind, st);
   if (A.ntiles > 0) return spmv_tma<TA, TX, TB, TY, TACC>(A, val, x, b, y, mode, s0, s1, kind, st);
   switch (A.tpr) {
     case 2: return launch_mode<TA, TX, TB, TY, TACC, 2>(A, val, x, b, y, mode, s0, s1, kind, st);

@@ -5,8 +5,7 @@
 
 namespace sd {
 
-// Upper bound on mbarrier polls before a wait gives up (each poll may
-// suspend the thread for a short, hardware-chosen time).
+// Upper bound on mbarrier polls before a wait gives up.
 constexpr uint32_t kWaitLimit = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -31,18 +30,24 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+// One poll that suspends the thread until the phase completes or about
+// kSuspendNs nanoseconds pass (a hint; the hardware may return earlier), so
+// waiting warps do not take issue slots from the warps doing the work.
+constexpr uint32_t kSuspendNs = 2000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
 
 // Wait for the completion of the phase with the given parity; false when
-// the poll limit is reached (the caller records an error and leaves).
+// the poll limit is reached (at most about kWaitLimit * kSuspendNs, ~2 s;
+// the caller records an error and leaves).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   for (uint32_t it = 0; it < kWaitLimit; ++it)
     if (mbar_try_wait(bar, parity)) return true;

@@ -72,13 +72,23 @@ __global__ void __launch_bounds__(128) k_vanka_factor(int nlist, const int* __re
   for (int k = tid; k < mu * np; k += nt) BT[k] = T(0);
   if (tid == 0) misc[1] = T(0);
   __syncthreads();
-  // B^T columns: entries of velocity rows in the seed (pressure) columns
+  // B^T columns: entries of velocity rows in the seed (pressure) columns,
+  // read eight at a time with all loads in flight
   for (int r = tid; r < mu; r += nt) {
     const int g = sdof[r];
-    for (int e = rowptr[g]; e < rowptr[g + 1]; ++e) {
-      const int c = col[e];
-      for (int k = 0; k < np; ++k)
-        if (sdof[mu + k] == c) BT[r * np + k] = T(Kval[e]);
+    const int e1 = rowptr[g + 1];
+    for (int e0 = rowptr[g]; e0 < e1; e0 += 8) {
+      int cc[8];
+      double vv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        cc[u] = e0 + u < e1 ? col[e0 + u] : -1;
+        vv[u] = e0 + u < e1 ? Kval[e0 + u] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        for (int k = 0; k < np; ++k)
+          if (sdof[mu + k] == cc[u]) BT[r * np + k] = T(vv[u]);
     }
   }
   const int nblk = shared ? 1 : dim;
@@ -90,9 +100,20 @@ __global__ void __launch_bounds__(128) k_vanka_factor(int nlist, const int* __re
     __syncthreads();
     for (int a = tid; a < m; a += nt) {
       const int g = sdof[cb * m + a];
-      for (int e = rowptr[g]; e < rowptr[g + 1]; ++e) {
-        const int pos = bsearch_int(sdof + cb * m, m, col[e]);
-        if (pos >= 0) A[a * m + pos] = T(Kval[e]);
+      const int e1 = rowptr[g + 1];
+      for (int e0 = rowptr[g]; e0 < e1; e0 += 8) {
+        int cc[8];
+        double vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          cc[u] = e0 + u < e1 ? col[e0 + u] : -1;
+          vv[u] = e0 + u < e1 ? Kval[e0 + u] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int pos = cc[u] >= 0 ? bsearch_int(sdof + cb * m, m, cc[u]) : -1;
+          if (pos >= 0) A[a * m + pos] = T(vv[u]);
+        }
       }
     }
     __syncthreads();
@@ -181,6 +202,204 @@ __global__ void __launch_bounds__(128) k_vanka_factor(int nlist, const int* __re
   }
 }
 
+// One warp per patch for patches with m <= MAXM (8, 20 or 32) velocity DoFs
+// per component: the same factorisation as above without block-wide
+// barriers.  Lane a owns row a of the block in registers through the
+// Gauss-Jordan sweep; at step k the pivot row goes to shared memory and
+// every lane updates its row with one FMA per entry (the pivot lane's own
+// scaling is written as the same update, row -= (1 - 1/p) row).
+constexpr int kFacWarps = 4;
+
+template <typename T, int MAXM>
+struct FacWarpSmem {
+  static constexpr int kDof = 3 * MAXM + kMaxNp;
+  static constexpr int kStride = MAXM + 1;  // padded rows: conflict-free column reads
+  __host__ __device__ static constexpr size_t bytes() {
+    return ((size_t)kDof * sizeof(int) + 15) / 16 * 16 +
+           sizeof(T) * ((size_t)MAXM * kStride + 2 * (size_t)3 * MAXM * kMaxNp + MAXM + kMaxNp * kMaxNp);
+  }
+};
+
+template <typename T, int MAXM>
+__global__ void __launch_bounds__(kFacWarps * 32) k_vanka_factor_warp(int nlist, const int* __restrict__ list,
+    int dim, int shared, const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
+    const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
+    const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing) {
+  using L = FacWarpSmem<T, MAXM>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kFacWarps + warp;
+  if (gw >= nlist) return;  // warp-uniform; no block barriers below
+  unsigned char* mine = smem_raw + (size_t)warp * L::bytes();
+  int* sdof = reinterpret_cast<int*>(mine);
+  T* Am = reinterpret_cast<T*>(mine + ((size_t)L::kDof * sizeof(int) + 15) / 16 * 16);
+  T* BT = Am + MAXM * L::kStride;
+  T* U = BT + 3 * MAXM * kMaxNp;
+  T* prow = U + 3 * MAXM * kMaxNp;
+  T* S = prow + MAXM;
+  const int i = list[gw];
+  const int base = ptr[i], m = nvel[i], np = npres[i];
+  const int mu = dim * m, mt = mu + np;
+  for (int k = lane; k < mt; k += 32) sdof[k] = dof[base + k];
+  for (int k = lane; k < mu * np; k += 32) BT[k] = T(0);
+  __syncwarp();
+  // B^T columns: entries of velocity rows in the seed (pressure) columns;
+  // each row's entries are read eight at a time, all loads in flight
+  for (int r = lane; r < mu; r += 32) {
+    const int g = sdof[r];
+    const int e1 = rowptr[g + 1];
+    for (int e0 = rowptr[g]; e0 < e1; e0 += 8) {
+      int cc[8];
+      double vv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        cc[u] = e0 + u < e1 ? col[e0 + u] : -1;
+        vv[u] = e0 + u < e1 ? Kval[e0 + u] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        for (int k = 0; k < np; ++k)
+          if (sdof[mu + k] == cc[u]) BT[r * np + k] = T(vv[u]);
+    }
+  }
+  const int nblk = shared ? 1 : dim;
+  const int pkp = padded_pk<T>(m);
+  T* out = fac + foff[i];
+  bool sing = false;
+  for (int cb = 0; cb < nblk; ++cb) {
+    __syncwarp();
+    T row[MAXM];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) row[j] = T(0);
+    if (lane < m) {
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) Am[lane * L::kStride + j] = T(0);
+      const int g = sdof[cb * m + lane];
+      const int e1 = rowptr[g + 1];
+      for (int e0 = rowptr[g]; e0 < e1; e0 += 8) {
+        int cc[8];
+        double vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          cc[u] = e0 + u < e1 ? col[e0 + u] : -1;
+          vv[u] = e0 + u < e1 ? Kval[e0 + u] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int pos = cc[u] >= 0 ? bsearch_int(sdof + cb * m, m, cc[u]) : -1;
+          if (pos >= 0) Am[lane * L::kStride + pos] = T(vv[u]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) row[j] = Am[lane * L::kStride + j];
+    }
+    T dm = lane < m ? fabs(Am[lane * L::kStride + lane]) : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    // Gauss-Jordan inversion in registers; the block is SPD so no pivoting
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k) {
+      if (k < m) {
+        __syncwarp();
+        if (lane == k) {
+#pragma unroll
+          for (int j = 0; j < MAXM; ++j) prow[j] = row[j];
+        }
+        __syncwarp();
+        T piv = prow[k];
+        const bool bad = !(fabs(piv) > T(1e-12) * dm);
+        if (bad) piv = T(1);  // keeps the arithmetic finite; the patch is flagged
+        sing |= bad;
+        const T p = T(1) / piv;
+        const T f = lane == k ? T(1) - p : row[k] * p;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) row[j] = fma(-f, prow[j], row[j]);
+        row[k] = lane == k ? p : -f;
+      }
+    }
+    // packed lower triangle of the (symmetrised) inverse
+    __syncwarp();
+    if (lane < m) {
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) Am[lane * L::kStride + j] = row[j];
+    }
+    __syncwarp();
+    if (lane < m)
+      for (int b = 0; b <= lane; ++b)
+        out[cb * pkp + lane * (lane + 1) / 2 + b] = T(0.5) * (Am[lane * L::kStride + b] + Am[b * L::kStride + lane]);
+    // U rows of the components this block serves: U = A^-1 B^T
+    const int c0 = shared ? 0 : cb, c1 = shared ? dim : cb + 1;
+    if (lane < m)
+      for (int c = c0; c < c1; ++c)
+        for (int k = 0; k < np; ++k) {
+          T s = T(0);
+#pragma unroll
+          for (int b = 0; b < MAXM; ++b)
+            if (b < m) s = fma(row[b], BT[(c * m + b) * np + k], s);
+          U[(c * m + lane) * np + k] = s;
+        }
+  }
+  __syncwarp();
+  // S = -B A^-1 B^T = -(B^T)^T U, np x np
+  for (int kk = 0; kk < np * np; ++kk) {
+    const int k = kk / np, k2 = kk - k * np;
+    T s = T(0);
+    for (int r = lane; r < mu; r += 32) s = fma(BT[r * np + k], U[r * np + k2], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) S[k * kMaxNp + k2] = -s;
+  }
+  T* Uout = out + nblk * pkp;
+  T* Sout = Uout + mu * np;
+  for (int idx = lane; idx < mu * np; idx += 32) {
+    const int r = idx / np, k = idx - r * np;
+    Uout[k * mu + r] = U[r * np + k];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    // S^-1 by Gauss-Jordan with partial pivoting (np <= 4)
+    T M[kMaxNp][2 * kMaxNp];
+    T smax = T(0);
+    for (int a = 0; a < np; ++a)
+      for (int b = 0; b < np; ++b) {
+        M[a][b] = S[a * kMaxNp + b];
+        M[a][np + b] = a == b ? T(1) : T(0);
+        smax = fmax(smax, fabs(M[a][b]));
+      }
+    for (int k = 0; k < np && !sing; ++k) {
+      int pr = k;
+      for (int a = k + 1; a < np; ++a)
+        if (fabs(M[a][k]) > fabs(M[pr][k])) pr = a;
+      if (!(fabs(M[pr][k]) > T(1e-12) * smax)) { sing = true; break; }
+      if (pr != k)
+        for (int b = 0; b < 2 * np; ++b) { T t = M[k][b]; M[k][b] = M[pr][b]; M[pr][b] = t; }
+      const T p = T(1) / M[k][k];
+      for (int b = 0; b < 2 * np; ++b) M[k][b] *= p;
+      for (int a = 0; a < np; ++a)
+        if (a != k) {
+          const T f = M[a][k];
+          for (int b = 0; b < 2 * np; ++b) M[a][b] -= f * M[k][b];
+        }
+    }
+    for (int a = 0; a < np; ++a)
+      for (int b = 0; b < np; ++b) Sout[a * np + b] = sing ? T(0) : M[a][np + b];
+    if (sing) atomicAdd(nsing, 1);
+  }
+}
+
+template <typename T, int MAXM>
+static cudaError_t launch_factor_warp(const DevPatches& p, const DevCSR& K, int start, int count, int* nsingular,
+                                      cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const size_t shm = kFacWarps * FacWarpSmem<T, MAXM>::bytes();
+  const unsigned blocks = (unsigned)((count + kFacWarps - 1) / kFacWarps);
+  k_vanka_factor_warp<T, MAXM><<<blocks, kFacWarps * 32, shm, st>>>(count, p.fac_list + start, p.dim, p.shared,
+      p.ptr, p.dof, p.nvel, p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac), nsingular);
+  return cudaGetLastError();
+}
+
+int vanka_factor_warp_bin(int m) { return m <= 8 ? 0 : m <= 20 ? 1 : m <= 32 ? 2 : -1; }
+
 size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool global_a) {
   return elem * ((global_a ? 0 : (size_t)max_m * max_m) + 2 * (size_t)dim * max_m * max_np + 2 * max_m +
                  kMaxNp * kMaxNp + 4) +
@@ -194,20 +413,32 @@ template <typename T>
 cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st) {
   if (p.npatch == 0) return cudaSuccess;
   const int dm = p.dim;
+  // warp-per-patch bins (m <= 8, 20, 32) lead the list, then the CTA kernel
+  int start = 0;
+  cudaError_t e0 = launch_factor_warp<T, 8>(p, K, start, p.nfac_warp[0], nsingular, st);
+  if (e0 != cudaSuccess) return e0;
+  start += p.nfac_warp[0];
+  e0 = launch_factor_warp<T, 20>(p, K, start, p.nfac_warp[1], nsingular, st);
+  if (e0 != cudaSuccess) return e0;
+  start += p.nfac_warp[1];
+  e0 = launch_factor_warp<T, 32>(p, K, start, p.nfac_warp[2], nsingular, st);
+  if (e0 != cudaSuccess) return e0;
+  start += p.nfac_warp[2];
   if (p.nfac_smem > 0) {
     const size_t shm = vanka_factor_smem(dm, p.max_m_fac_smem, p.max_np, sizeof(T), false);
-    k_vanka_factor<T><<<p.nfac_smem, 128, shm, st>>>(p.nfac_smem, p.fac_list, dm, p.shared, p.ptr, p.dof, p.nvel,
+    k_vanka_factor<T><<<p.nfac_smem, 128, shm, st>>>(p.nfac_smem, p.fac_list + start, dm, p.shared, p.ptr, p.dof, p.nvel,
                                                      p.npres, p.foff, K.rowptr, K.col, K.v64,
                                                      reinterpret_cast<T*>(p.fac), nsingular, p.max_m_fac_smem,
                                                      p.max_np, (T*)nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int nglob = p.npatch - p.nfac_smem;
+  start += p.nfac_smem;
+  const int nglob = p.npatch - start;
   for (int c0 = 0; c0 < nglob; c0 += p.fac_chunk) {
     const int cnt = std::min(p.fac_chunk, nglob - c0);
     const size_t shm = vanka_factor_smem(dm, p.max_m, p.max_np, sizeof(T), true);
-    k_vanka_factor<T><<<cnt, 128, shm, st>>>(cnt, p.fac_list + p.nfac_smem + c0, dm, p.shared, p.ptr, p.dof, p.nvel,
+    k_vanka_factor<T><<<cnt, 128, shm, st>>>(cnt, p.fac_list + start + c0, dm, p.shared, p.ptr, p.dof, p.nvel,
                                              p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac),
                                              nsingular, p.max_m, p.max_np, reinterpret_cast<T*>(p.fac_scratch));
     cudaError_t e = cudaGetLastError();
@@ -346,10 +577,9 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
   if (warp == kNCW) {
     if (lane == 0) {
       const uint64_t pol = policy_evict_first();
-      int k = 0;
+      int k = 0, s = 0, round = 0;  // k = s + round * stages
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-        const int s = k % stages;
-        if (k >= stages && !mbar_wait(empty + s, ((k / stages) - 1) & 1)) {
+        if (round > 0 && !mbar_wait(empty + s, (round - 1) & 1)) {
           atomicOr(err, 1);
           break;
         }
@@ -363,6 +593,10 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
         bulk_g2s(st, fac + f0, fb, full + s, pol);
         bulk_g2s(st + fac_bytes, dof + d0, db, full + s, pol);
         bulk_g2s(st + fac_bytes + dof_bytes, meta + i0, mb, full + s, pol);
+        if (++s == stages) {
+          s = 0;
+          ++round;
+        }
       }
       // every copy issued has landed before this CTA may finish
       for (int kk = max(0, k - stages); kk < k; ++kk)
@@ -374,10 +608,9 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
   T* myrhs = rhsb + (size_t)warp * rhs_elems;
   const int slot = lane / LP, l = lane % LP, gbase = slot * LP;
   const int nblk = shared ? 1 : DIM;
-  int k = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-    const int s = k % stages;
-    if (!mbar_wait(full + s, (k / stages) & 1)) {
+  int s = 0, round = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (!mbar_wait(full + s, round & 1)) {
       atomicOr(err, 2);
       return;
     }
@@ -504,6 +737,10 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty + s);
+    if (++s == stages) {
+      s = 0;
+      ++round;
+    }
   }
 }
 
@@ -621,7 +858,10 @@ cudaError_t vanka_prepare_kernels() {
   std::vector<const void*> ks = {
       (const void*)k_vanka_factor<float>, (const void*)k_vanka_factor<double>,
       (const void*)k_vanka_apply_cta<float, float, 2>, (const void*)k_vanka_apply_cta<float, float, 3>,
-      (const void*)k_vanka_apply_cta<double, double, 2>, (const void*)k_vanka_apply_cta<double, double, 3>};
+      (const void*)k_vanka_apply_cta<double, double, 2>, (const void*)k_vanka_apply_cta<double, double, 3>,
+      (const void*)k_vanka_factor_warp<float, 8>, (const void*)k_vanka_factor_warp<float, 20>,
+      (const void*)k_vanka_factor_warp<float, 32>, (const void*)k_vanka_factor_warp<double, 8>,
+      (const void*)k_vanka_factor_warp<double, 20>, (const void*)k_vanka_factor_warp<double, 32>};
   for (size_t elem : {size_t(4), size_t(8)})
     for (int dim : {2, 3})
       for (bool one : {true, false})
