@@ -193,6 +193,9 @@ constexpr int kTileNnz = 1024, kTileRows = 256;
 // for one (smaller operators keep enough warps busy with vector CSR).
 constexpr double kSellMaxPad = 1.25;
 constexpr int kSellRows = 262144;
+// Operators with kStreamMinRows <= rows < kSellRows use the row-block
+// stream SpMV.
+constexpr int kStreamMinRows = 32768;
 
 int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
   d.nrows = c.nrows;
@@ -215,6 +218,20 @@ int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
   d.tpr = choose_tpr(d.nnz, d.nrows);
   int maxrow = 0;
   for (int i = 0; i < c.nrows; ++i) maxrow = std::max(maxrow, c.rowptr[i + 1] - c.rowptr[i]);
+  // row-block tiles for the stream SpMV (mid-size operators)
+  if (c.nrows >= kStreamMinRows && c.nrows < kSellRows && maxrow <= kStreamNnz) {
+    std::vector<int4> td;
+    int r = 0;
+    while (r < c.nrows) {
+      int r1 = r;
+      while (r1 < c.nrows && r1 - r < kStreamRows && c.rowptr[r1 + 1] - c.rowptr[r] <= kStreamNnz) ++r1;
+      td.push_back(make_int4(r, c.rowptr[r], r1, c.rowptr[r1]));
+      r = r1;
+    }
+    d.stiles = (int)td.size();
+    TRY(upload(h, &d.tdesc, td));
+    return STOKES_OK;
+  }
   // sliced ELLPACK copy when the padding to the longest row of each chunk
   // of 32 rows stays small
   if (c.nrows >= kSellRows) {
@@ -1604,14 +1621,17 @@ int arnoldi_step(stokes_handle* h, int j, double rtol, int maxit) {
   double* zj = h->Z + (size_t)j * n;
   TRY(run_cycle(h, vj, zj));
   CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, zj, zj, h->w, SPMV_SET, 0, 0, nullptr, h->st)));
-  // h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2, ||w||^2
-  TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+  // classical Gram-Schmidt twice: h1 = V^T w, w -= V h1, h2 = V^T w,
+  // w -= V h2, then ||w||^2 (a second pass is needed at nearly every step:
+  // with a good preconditioner w = K0 z_j lies mostly in span V)
+  const int nc = j + 1;
+  TRY(seg_dots(h, h->V, n, nc, h->w, 0));
+  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, nc, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
   CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
-  TRY(seg_dots(h, h->V, n, j + 1, h->w, 0));
-  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, j + 1, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
+  TRY(seg_dots(h, h->V, n, nc, h->w, 0));
+  CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, nc, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
   CK(multidot_partial(h->ndchunks, h->dbeg, h->dend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
-  CK(multidot_finish(ni, h->sd_beg, h->sd_end, 1, h->partial, h->ldp, h->yd + (j + 1), h->ldh, 0, h->st));
+  CK(multidot_finish(ni, h->sd_beg, h->sd_end, 1, h->partial, h->ldp, h->yd + nc, h->ldh, 0, h->st));
   CK(fg_update(ni, h->krylov_m, j, h->fg, h->yd, h->hd, h->ldh, rtol, maxit, h->st));
   CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st));
   CK(cudaMemcpyAsync(h->hstat + j, h->fg.stat + j, sizeof(int), cudaMemcpyDeviceToHost, h->st));

@@ -9,6 +9,8 @@ namespace sd {
 
 // CSR matrix on the device: int32 row pointers and columns (nnz < 2^31),
 // FP64 values and, for an FP32 cycle, an FP32 copy of the values.
+constexpr int kStreamNnz = 2048, kStreamRows = 256;
+
 struct DevCSR {
   int nrows = 0, ncols = 0;
   int64_t nnz = 0;
@@ -25,6 +27,10 @@ struct DevCSR {
   int tile_col_bytes = 0, tile_rp_bytes = 0;
   int tma_grid32 = 0, tma_grid64 = 0;
   int* err = nullptr;
+  // row-block tiles of the stream SpMV: {first row, first entry, end row,
+  // end entry}, at most kStreamRows rows and kStreamNnz entries each
+  int stiles = 0;
+  int4* tdesc = nullptr;
   // sliced ELLPACK copy (large operators): chunks of 32 rows, entry k of row
   // 32 c + i at soff[c] + 32 k + i; rows shorter than the chunk are padded
   int schunks = 0;              // 0: no sliced copy

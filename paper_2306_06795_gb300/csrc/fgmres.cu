@@ -1,8 +1,8 @@
 // Device-side bookkeeping of restarted FGMRES (Sec. 4): per instance, the
 // Hessenberg column, Givens rotations, the residual estimate, the running
-// flag and the scale of the next Krylov vector are updated by one thread,
-// so an Arnoldi step needs no host round trip.  One block handles every
-// instance; its flag reduction and all arithmetic run in a fixed order.
+// flag and the scale of the next Krylov vector are updated on the device,
+// so an Arnoldi step needs no host round trip.  All arithmetic of an
+// instance runs in a fixed order.
 #include <cmath>
 
 #include "common.cuh"
@@ -37,42 +37,60 @@ __global__ void __launch_bounds__(256) k_fg_start(int ninst, int m, FgState st, 
 
 // Arnoldi step j: column j of H from the two Gram-Schmidt passes (h1 in
 // h1buf, h2 in h2buf, ||w||^2 in h1buf[j+1]), Givens update, convergence.
-__global__ void __launch_bounds__(256) k_fg_update(int ninst, int m, int j, FgState st, const double* __restrict__ h1buf,
+// One block per instance: the column and the previous rotations are staged
+// in shared memory by all threads, thread 0 applies the rotations in order,
+// and the running flags are OR-ed into stat[j] (zeroed beforehand).
+__global__ void __launch_bounds__(64) k_fg_update(int ninst, int m, int j, FgState st, const double* __restrict__ h1buf,
                             const double* __restrict__ h2buf, int ldh, double rtol, int maxit) {
-  __shared__ int any;
-  if (threadIdx.x == 0) any = 0;
+  extern __shared__ double fsm[];
+  double* col = fsm;            // [j+2]
+  double* csS = col + (m + 2);  // [j]
+  double* snS = csS + m;        // [j]
+  __shared__ double wmax[2];
+  const int s = blockIdx.x;
+  if (s >= ninst) return;
+  if (!st.run[s]) {  // block-uniform
+    if (threadIdx.x == 0) st.scale[s] = 0.0;
+    return;
+  }
+  double* H = st.H + (size_t)s * (m + 1) * m;
+  double* cs = st.cs + (size_t)s * m;
+  double* sn = st.sn + (size_t)s * m;
+  const double* h1 = h1buf + (size_t)s * ldh;
+  const double* h2 = h2buf + (size_t)s * ldh;
+  double hm = 0.0;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    col[i] = h1[i] + h2[i];
+    hm = fmax(hm, fabs(col[i]));
+  }
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    csS[i] = cs[i];
+    snS[i] = sn[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hm = fmax(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = hm;
   __syncthreads();
-  for (int s = threadIdx.x; s < ninst; s += blockDim.x) {
-    if (!st.run[s]) {
-      st.scale[s] = 0.0;
-      continue;
-    }
-    double* H = st.H + (size_t)s * (m + 1) * m;
-    double* cs = st.cs + (size_t)s * m;
-    double* sn = st.sn + (size_t)s * m;
+  if (threadIdx.x == 0) {
+    const double hmax = fmax(wmax[0], wmax[1]);
     double* g = st.g + (size_t)s * (m + 1);
-    const double* h1 = h1buf + (size_t)s * ldh;
-    const double* h2 = h2buf + (size_t)s * ldh;
-    double hmax = 0.0;
-    for (int i = 0; i <= j; ++i) {
-      H[i * m + j] = h1[i] + h2[i];
-      hmax = fmax(hmax, fabs(H[i * m + j]));
-    }
     const double hn = sqrt(h1[j + 1]);
-    H[(j + 1) * m + j] = hn;
+    col[j + 1] = hn;
     const bool breakdown = !(hn > 1e-14 * fmax(hmax, 1e-300));
     for (int i = 0; i < j; ++i) {
-      const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
-      H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
-      H[i * m + j] = t;
+      const double t = csS[i] * col[i] + snS[i] * col[i + 1];
+      col[i + 1] = -snS[i] * col[i] + csS[i] * col[i + 1];
+      col[i] = t;
     }
-    const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
-    cs[j] = H[j * m + j] / den;
-    sn[j] = H[(j + 1) * m + j] / den;
-    H[j * m + j] = den;
-    H[(j + 1) * m + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
+    const double den = hypot(col[j], col[j + 1]);
+    const double c = col[j] / den, sj = col[j + 1] / den;
+    cs[j] = c;
+    sn[j] = sj;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    const double gj = g[j];
+    g[j + 1] = -sj * gj;
+    g[j] = c * gj;
     st.its[s] += 1;
     st.kcol[s] = j + 1;
     if (!isfinite(g[j + 1])) atomicOr(st.err, 1);
@@ -80,10 +98,10 @@ __global__ void __launch_bounds__(256) k_fg_update(int ninst, int m, int j, FgSt
                      isfinite(g[j + 1]);
     st.run[s] = run;
     st.scale[s] = run ? 1.0 / hn : 0.0;
-    if (run) atomicOr(&any, 1);
+    if (run) atomicOr(st.stat + j, 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) st.stat[j] = any;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[i * m + j] = col[i];
 }
 
 // y of the least-squares problem by back substitution (per instance).
@@ -118,7 +136,11 @@ cudaError_t fg_start(int ninst, int m, const FgState& st, const double* h, int l
 }
 cudaError_t fg_update(int ninst, int m, int j, const FgState& st, const double* h1, const double* h2, int ldh,
                       double rtol, int maxit, cudaStream_t s) {
-  k_fg_update<<<1, 256, 0, s>>>(ninst, m, j, st, h1, h2, ldh, rtol, maxit);
+  // stat[j] collects the running flags of all instances
+  cudaError_t e = cudaMemsetAsync(st.stat + j, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const size_t shm = sizeof(double) * (3 * (size_t)m + 2);
+  k_fg_update<<<ninst, 64, shm, s>>>(ninst, m, j, st, h1, h2, ldh, rtol, maxit);
   return cudaGetLastError();
 }
 cudaError_t fg_solve(int ninst, int m, const FgState& st, int ldh, cudaStream_t s) {
