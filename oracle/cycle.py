@@ -37,7 +37,42 @@ from .vanka import VankaLevel
 from . import dlsc as _dlsc
 
 DC_ALL, DC_SKIP1, DC_SKIP0 = 0, 1, 2
-VANKA, DLSC = 0, 1
+VANKA, DLSC, VANKA_KRYLOV = 0, 1, 2
+
+
+def krylov_relax(K, x, b, precond, k):
+    """Krylov-wrapped relaxation (Sec. 3.3.1): k steps of flexible GMRES on
+    K e = b - K x from e = 0, right-preconditioned by `precond` (one Vanka
+    sweep, undamped, per step), Arnoldi by modified Gram-Schmidt; returns
+    x + Z y with y the least-squares minimiser of ||beta e1 - H y||.  The
+    steps stop early at an exact (lucky) breakdown."""
+    r = b - K @ x
+    beta = np.linalg.norm(r)
+    if beta == 0.0:
+        return x
+    V = [r / beta]
+    Z = []
+    H = np.zeros((k + 1, k))
+    steps = 0
+    for j in range(k):
+        z = precond(V[j])
+        Z.append(z)
+        w = K @ z
+        for i in range(j + 1):
+            H[i, j] = w @ V[i]
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        steps = j + 1
+        if H[j + 1, j] == 0.0:
+            break
+        V.append(w / H[j + 1, j])
+    g = np.zeros(steps + 1)
+    g[0] = beta
+    y = np.linalg.lstsq(H[:steps + 1, :steps], g, rcond=None)[0]
+    e = np.zeros_like(x)
+    for j in range(steps):
+        e = e + y[j] * Z[j]
+    return x + e
 
 
 class Params:
@@ -77,7 +112,7 @@ class Oracle:
         self.vanka = {}
         self.dl = {}
         for l in range(nrel):
-            if self.relax[l] == VANKA:
+            if self.relax[l] in (VANKA, VANKA_KRYLOV):
                 self.vanka[l] = VankaLevel(self.K[l], prob.patches[l])
             else:
                 self.dl[l] = _dlsc.DLSCLevel(prob, l, params)
@@ -98,6 +133,9 @@ class Oracle:
 
     # -- pieces -------------------------------------------------------------
     def relax_level(self, l, x, b, sweeps):
+        if self.relax[l] == VANKA_KRYLOV:
+            # `sweeps` inner FGMRES steps, one Vanka sweep each
+            return krylov_relax(self.K[l], x, b, self.vanka[l].apply, sweeps) if sweeps > 0 else x
         for _ in range(sweeps):
             if self.relax[l] == VANKA:
                 x = self.vanka[l].sweep(self.K[l], x, b, self.omega[l])

@@ -188,77 +188,86 @@ template cudaError_t coarse_solve<double>(int, const int*, const int*, const int
 constexpr int kRedThreads = 256;
 constexpr int kMaxAxpyCols = 1024;  // Krylov columns (restart length) one multiaxpy handles
 
-// grid: (nchunks, ceil(ncols / 8)).  partial[c*ldp + k] = sum over the rows
-// of chunk c of V_k[row] w[row] for eight columns k per block: one row per
-// thread per step with the eight column loads in flight, then a transposed
-// butterfly (xor 16, 8, 4 halve the values a lane holds, xor 2, 1 finish)
-// reduces the eight sums of a warp in 9 additions instead of 40, and the
-// warps' sums are added in warp order.  Fixed order: deterministic.
-constexpr int kDotCols = 8;
+// grid: (nchunks, ceil(ncols / NK)).  partial[c*ldp + k] = sum over the
+// rows of chunk c of V_k[row] w[row] for NK columns k per block (NK = 1, 2,
+// 4 or 8, the smallest power of two covering ncols, at most 8): two rows
+// per thread per step with all column loads in flight, one DFMA per loaded
+// element (columns past ncols are neither loaded nor multiplied: GB300's
+// FP64 rate is the bound), then a transposed butterfly that halves the
+// values a lane holds at each of the first log2(NK) exchanges and adds in
+// full at the others (NK - 1 + 5 - log2(NK) additions per warp instead of
+// 5 NK), and the warps' sums are added in warp order.  Fixed order:
+// deterministic.
+template <int NK>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const int64_t* __restrict__ cbeg,
     const int64_t* __restrict__ cend, int ncols, const double* __restrict__ V, int64_t ldv,
     const double* __restrict__ w, double* __restrict__ partial, int ldp) {
-  __shared__ double red[kRedThreads / 32][kDotCols];
-  const int c = blockIdx.x, k0 = blockIdx.y * kDotCols;
-  const int nk = min(kDotCols, ncols - k0);
-  double acc[kDotCols];
+  __shared__ double red[kRedThreads / 32][NK];
+  const int c = blockIdx.x, k0 = blockIdx.y * NK;
+  const int nk = min(NK, ncols - k0);
+  double acc[NK];
 #pragma unroll
-  for (int u = 0; u < kDotCols; ++u) acc[u] = 0.0;
+  for (int u = 0; u < NK; ++u) acc[u] = 0.0;
   const double* v0 = V + (int64_t)k0 * ldv;
   const int64_t ce = cend[c];
-  // two rows per thread per step: eighteen loads in flight
   for (int64_t r = cbeg[c] + threadIdx.x; r < ce; r += 2 * kRedThreads) {
     const int64_t r2 = r + kRedThreads;
     const bool has2 = r2 < ce;
     const double w1 = w[r], w2 = has2 ? w[r2] : 0.0;
-    double v1[kDotCols], v2[kDotCols];
+    double v1[NK], v2[NK];
 #pragma unroll
-    for (int u = 0; u < kDotCols; ++u) {
+    for (int u = 0; u < NK; ++u) {
       v1[u] = u < nk ? v0[(int64_t)u * ldv + r] : 0.0;
       v2[u] = u < nk && has2 ? v0[(int64_t)u * ldv + r2] : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < kDotCols; ++u) acc[u] = fma(v2[u], w2, fma(v1[u], w1, acc[u]));
+    for (int u = 0; u < NK; ++u)
+      if (u < nk) acc[u] = fma(v2[u], w2, fma(v1[u], w1, acc[u]));
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // xor 16: lanes 0-15 keep columns 0-3, lanes 16-31 columns 4-7
-  const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
-  double b4[4];
+  // halving exchanges: at xor offset 16 >> q the lanes with that bit set
+  // keep the upper half of their values; the lane's column index gathers
+  // those bits
+  int col = 0;
+  double b[NK];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const double send = hi16 ? acc[u] : acc[u + 4];
-    const double keep = hi16 ? acc[u + 4] : acc[u];
-    b4[u] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  double b2[2];
+  for (int u = 0; u < NK; ++u) b[u] = acc[u];
+  int n = NK, off = 16;
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const double send = hi8 ? b4[u] : b4[u + 2];
-    const double keep = hi8 ? b4[u + 2] : b4[u];
-    b2[u] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  for (; n > 1; n >>= 1, off >>= 1) {
+    const bool hi = lane & off;
+#pragma unroll
+    for (int u = 0; u < NK / 2; ++u)
+      if (u < n / 2) {
+        const double send = hi ? b[u] : b[u + n / 2];
+        const double keep = hi ? b[u + n / 2] : b[u];
+        b[u] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    col = 2 * col + (hi ? 1 : 0);
   }
-  double b1;
-  {
-    const double send = hi4 ? b2[0] : b2[1];
-    const double keep = hi4 ? b2[1] : b2[0];
-    b1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  b1 += __shfl_xor_sync(0xffffffffu, b1, 2);
-  b1 += __shfl_xor_sync(0xffffffffu, b1, 1);
-  // lane holds column 4*[lane&16] + 2*[lane&8] + [lane&4]
-  if ((lane & 3) == 0) red[warp][(hi16 ? 4 : 0) + (hi8 ? 2 : 0) + (hi4 ? 1 : 0)] = b1;
+  double t = b[0];
+#pragma unroll
+  for (; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  constexpr int LOG = NK == 1 ? 0 : NK == 2 ? 1 : NK == 4 ? 2 : 3;
+  if ((lane & ((32 >> LOG) - 1)) == 0) red[warp][col] = t;
   __syncthreads();
   if (threadIdx.x < nk) {
-    double t = 0.0;
-    for (int q = 0; q < kRedThreads / 32; ++q) t += red[q][threadIdx.x];
-    partial[(int64_t)c * ldp + k0 + threadIdx.x] = t;
+    double sum = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) sum += red[q][threadIdx.x];
+    partial[(int64_t)c * ldp + k0 + threadIdx.x] = sum;
   }
 }
 cudaError_t multidot_partial(int nchunks, const int64_t* cbeg, const int64_t* cend, int ncols, const double* V,
                              int64_t ldv, const double* w, double* partial, int ldp, cudaStream_t st) {
   if (nchunks == 0 || ncols == 0) return cudaSuccess;
-  const unsigned gy = (unsigned)((ncols + kDotCols - 1) / kDotCols);
-  k_multidot<<<dim3((unsigned)nchunks, gy), kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp);
+  const int nk = ncols >= 8 ? 8 : ncols > 4 ? 8 : ncols > 2 ? 4 : ncols;
+  const dim3 grid((unsigned)nchunks, (unsigned)((ncols + nk - 1) / nk));
+  switch (nk) {
+    case 1: k_multidot<1><<<grid, kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
+    case 2: k_multidot<2><<<grid, kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
+    case 4: k_multidot<4><<<grid, kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
+    default: k_multidot<8><<<grid, kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp);
+  }
   return cudaGetLastError();
 }
 

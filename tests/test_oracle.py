@@ -253,3 +253,74 @@ def test_dlsc_relaxation_reduces_the_error():
     b = K @ xs
     x = dl.sweep(np.zeros_like(b), b)
     assert np.linalg.norm(b - K @ x) < np.linalg.norm(b)
+
+
+# -- Krylov-wrapped relaxation (Sec. 3.3.1) ---------------------------------
+
+def _rand_system(n, seed):
+    rng = np.random.default_rng(seed)
+    K = np.eye(n) * 4.0 + rng.standard_normal((n, n)) * 0.3
+    M = np.eye(n) * 0.25 + rng.standard_normal((n, n)) * 0.02
+    return K, M, rng
+
+
+def test_krylov_relax_identity_operator_is_exact_in_one_step():
+    rng = np.random.default_rng(7)
+    n = 9
+    x = rng.standard_normal(n)
+    b = rng.standard_normal(n)
+    out = cycle.krylov_relax(np.eye(n), x, b, lambda v: v, 1)
+    assert np.allclose(out, b, atol=1e-14)
+
+
+def test_krylov_relax_one_step_is_the_residual_minimising_damping():
+    """One FGMRES step is x + w* M r with w* = (r, KMr) / (KMr, KMr)."""
+    K, M, rng = _rand_system(12, 1)
+    x = rng.standard_normal(12)
+    b = rng.standard_normal(12)
+    r = b - K @ x
+    z = M @ r
+    Kz = K @ z
+    w = (r @ Kz) / (Kz @ Kz)
+    out = cycle.krylov_relax(K, x, b, lambda v: M @ v, 1)
+    assert np.allclose(out, x + w * z, rtol=1e-13, atol=1e-13)
+
+
+def test_krylov_relax_two_steps_minimise_over_the_search_space():
+    """The result's residual is no larger than that of any combination of the
+    two preconditioned directions z1 = M v1, z2 = M v2."""
+    K, M, rng = _rand_system(15, 2)
+    x = rng.standard_normal(15)
+    b = rng.standard_normal(15)
+    out = cycle.krylov_relax(K, x, b, lambda v: M @ v, 2)
+    r = b - K @ x
+    v1 = r / np.linalg.norm(r)
+    z1 = M @ v1
+    w = K @ z1
+    w = w - (w @ v1) * v1
+    v2 = w / np.linalg.norm(w)
+    z2 = M @ v2
+    best = np.linalg.norm(b - K @ out)
+    for _ in range(300):
+        a, c = rng.standard_normal(2) * 3.0
+        assert best <= np.linalg.norm(b - K @ (x + a * z1 + c * z2)) * (1 + 1e-12)
+    # and it attains the least-squares optimum over span{z1, z2}
+    Z = np.stack([z1, z2], axis=1)
+    y = np.linalg.lstsq(K @ Z, r, rcond=None)[0]
+    assert abs(best - np.linalg.norm(r - K @ Z @ y)) <= 1e-12 * np.linalg.norm(r)
+
+
+def test_krylov_relax_n_steps_unpreconditioned_is_a_direct_solve():
+    K, _, rng = _rand_system(8, 3)
+    x = rng.standard_normal(8)
+    b = rng.standard_normal(8)
+    out = cycle.krylov_relax(K, x, b, lambda v: v, 8)
+    assert np.allclose(K @ out, b, atol=1e-10)
+
+
+def test_fgmres_with_krylov_wrapped_relaxation_solves_c1(c1):
+    nrel = c1.nlevels - 1
+    prm = cycle.Params(nu1=2, nu2=2, eta_u=1.0, eta_p=1.0, relax=[cycle.VANKA_KRYLOV] * nrel)
+    orc = cycle.Oracle(c1, prm)
+    x, its, rel = krylov.fgmres(c1.K[0], c1.b, orc.apply, rtol=1e-8, restart=30, maxit=100)
+    assert rel <= 1e-8 and its <= 30
