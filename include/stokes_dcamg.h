@@ -55,7 +55,13 @@ enum {
 
 enum { STOKES_TH = 0, STOKES_SV = 1 };                       /* K0 element pair */
 enum { STOKES_DC_ALL = 0, STOKES_DC_SKIP1 = 1, STOKES_DC_SKIP0 = 2 };  /* Sec. 4 schedules */
-enum { STOKES_RELAX_VANKA = 0, STOKES_RELAX_DLSC = 1 };
+/* Relaxation per level.  VANKA: nu damped additive Vanka sweeps
+ * x += omega M^-1 (b - K x) (Eq. vanka).  DLSC: the Chebyshev LSC-DGS sweep
+ * of Alg. 2 (levels >= 1).  VANKA_KRYLOV: the Krylov-wrapped relaxation of
+ * Sec. 3.3.1, nu steps of flexible GMRES on K e = b - K x, each
+ * right-preconditioned by one undamped Vanka sweep, then x += Z y with y
+ * the least-squares minimiser (nu <= 4; omega unused). */
+enum { STOKES_RELAX_VANKA = 0, STOKES_RELAX_DLSC = 1, STOKES_RELAX_VANKA_KRYLOV = 2 };
 enum { STOKES_FP32 = 0, STOKES_FP64 = 1 };                   /* cycle precision */
 
 /* A sparse matrix in CSR form, host memory, FP64 values.  Column indices
@@ -184,7 +190,9 @@ int stokes_fgmres_solve_host(stokes_handle* h, const double* b_host, double* x_h
  *   STOKES_OP_PROLONG   y = P_l x                     (x: level l+1, y: level l)
  *   STOKES_OP_VANKA     y = M_l^-1 x, Eq. vanka (sum of weighted patch solves)
  *   STOKES_OP_RELAX     y = x + omega_l M_l^-1 (b - K_l x), one sweep
- *                       (one DLSC sweep when level l relaxes with DLSC)
+ *                       (one DLSC sweep when level l relaxes with DLSC; one
+ *                       Krylov-wrapped relaxation of max(nu1, nu2) steps
+ *                       when it relaxes with STOKES_RELAX_VANKA_KRYLOV)
  *   STOKES_OP_COARSE    y = exact bordered solve with the coarsest K (l = nlevels-1)
  */
 enum {

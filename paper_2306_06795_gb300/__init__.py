@@ -25,7 +25,7 @@ STOKES_ERR_NAN = -5
 STOKES_ERR_STATE = -6
 STOKES_TH, STOKES_SV = 0, 1
 STOKES_DC_ALL, STOKES_DC_SKIP1, STOKES_DC_SKIP0 = 0, 1, 2
-STOKES_RELAX_VANKA, STOKES_RELAX_DLSC = 0, 1
+STOKES_RELAX_VANKA, STOKES_RELAX_DLSC, STOKES_RELAX_VANKA_KRYLOV = 0, 1, 2
 STOKES_FP32, STOKES_FP64 = 0, 1
 STOKES_KERNEL_VANKA_APPLY, STOKES_KERNEL_SCATTER, STOKES_KERNEL_SPMV, STOKES_KERNEL_DC_RESIDUAL = range(4)
 (STOKES_OP_SPMV, STOKES_OP_SPMV_F64, STOKES_OP_RESIDUAL, STOKES_OP_RESTRICT,

@@ -85,6 +85,15 @@ struct Level {
   std::vector<int64_t> seg_off;  // per instance, -1 when absent
   bool dlsc = false;
   DLSCData dl;
+  // Krylov-wrapped relaxation (Sec. 3.3.1)
+  bool krylov = false;
+  int kmax = 0, lds = 0, ldp = 0;
+  KrChunks kch;
+  void* kV = nullptr;  // kmax + 1 level vectors
+  void* kZ = nullptr;  // kmax level vectors
+  void* kw = nullptr;
+  double* kS = nullptr;       // per-instance scalars
+  double* kpart = nullptr;    // chunk partials
 };
 
 struct Ledger {
@@ -469,7 +478,8 @@ int L_apply(stokes_handle* h, const Level& lv, const TR* r, T* yp) {
     // factors + patch index lists + per-patch metadata + gathered r + patch-major output
     h->led.bytes += double(p.fac_elems) * sizeof(T) + double(p.nslots) * (4 + sizeof(TR) + sizeof(T)) +
                     double(p.npatch) * (4 + 4 + 4 + 8 + 4);
-    h->led.launches += (p.nsmall > 0) + (p.nlarge > 0);
+    for (int b = 0; b < kTmaBins; ++b) h->led.launches += p.nsmall > 0 && p.bins[b].count > 0;
+    h->led.launches += p.nlarge > 0;
     return STOKES_OK;
   }
   CK((vanka_apply<T, TR>(p, r, yp, h->st)));
@@ -655,6 +665,65 @@ int dlsc_sweep(stokes_handle* h, int l, T* x, const T* b) {
   return STOKES_OK;
 }
 
+// Krylov-wrapped relaxation (Sec. 3.3.1): k steps of flexible GMRES on
+// K e = b - K x from e = 0, right-preconditioned by one undamped Vanka sweep
+// per step (classical Gram-Schmidt, per-instance scalars on the device),
+// then x += Z y.  zero_guess: x starts at 0 and the residual is b.  On level
+// 0 the update also writes the FP64 copy x64 and/or the cycle output out64.
+template <typename T>
+int relax_krylov(stokes_handle* h, int l, T* x, const T* b, int k, bool zero_guess, const double* r64,
+                 double* out64, double* x64) {
+  Level& L = h->lv[l];
+  const int64_t n = L.n;
+  const int ni = h->ninst;
+  T* V = reinterpret_cast<T*>(L.kV);
+  T* Z = reinterpret_cast<T*>(L.kZ);
+  T* w = reinterpret_cast<T*>(L.kw);
+  T* yp = reinterpret_cast<T*>(L.yp);
+  const int lds = L.lds;
+  const KrChunks& ch = L.kch;
+  const double Tb = sizeof(T);
+  const T* r = b;
+  if (!zero_guess) {
+    TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, V, SPMV_RES)));
+    r = V;
+  }
+  if (h->led.count) {
+    // beta, v0; per step: Vanka, K z, projections, update + norm, next v; least squares; x update
+    double bytes = 2 * n * Tb + 2 * n * Tb;
+    int launches = 2 + 1;
+    for (int j = 0; j < k; ++j) {
+      bytes += (j + 2) * n * Tb + (j + 3) * n * Tb + (j + 1 < k ? 2 * n * Tb : 0.0);
+      launches += 2 + 2 + (j + 1 < k ? 1 : 0);
+    }
+    bytes += (k + 2) * n * Tb + (x64 ? 8.0 * n : 0.0) + (out64 ? 17.0 * n : 0.0);
+    launches += 2;
+    h->led.bytes += bytes;
+    h->led.launches += launches;
+  } else {
+    CK(kr_dot<T>(ch, 1, r, 0, r, L.kpart, L.ldp, L.kS, lds, 0, ni, h->st));
+    CK(kr_scale<T>(ch, r, V, L.kS, lds, 0, h->st));
+  }
+  for (int j = 0; j < k; ++j) {
+    T* vj = V + (size_t)j * n;
+    T* zj = Z + (size_t)j * n;
+    TRY((L_apply<T, T>(h, L, vj, yp)));
+    TRY(L_scatter<T>(h, L, yp, zj, 1.0, 0));
+    TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), zj, (const T*)nullptr, w, SPMV_SET)));
+    if (h->led.count) continue;
+    const int col = 1 + j * (k + 1);
+    CK(kr_dot<T>(ch, j + 1, V, n, w, L.kpart, L.ldp, L.kS, lds, col, ni, h->st));
+    CK(kr_axpy_norm<T>(ch, j + 1, V, n, col, w, L.kpart, L.ldp, L.kS, lds, col + j + 1, ni, h->st));
+    if (j + 1 < k) CK(kr_scale<T>(ch, w, V + (size_t)(j + 1) * n, L.kS, lds, col + j + 1, h->st));
+  }
+  if (!h->led.count) {
+    CK(kr_ls(ni, k, L.kS, lds, h->st));
+    CK(kr_update<T>(ch, k, Z, n, L.kS, lds, 1 + k * (k + 1), x, zero_guess ? 1 : 0, x64, h->dir0, r64, out64,
+                    h->st));
+  }
+  return STOKES_OK;
+}
+
 // nsweeps sweeps of x <- x + omega M^-1 (b - K x) (Eq. vanka); the first
 // sweep from a zero guess needs no residual (r = b).  When out64 is given,
 // the last scatter writes the level-0 output (Dirichlet rows take r64).
@@ -663,6 +732,15 @@ template <typename T>
 int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_guess, const double* r64 = nullptr,
           double* out64 = nullptr, double* x64 = nullptr) {
   Level& L = h->lv[l];
+  if (L.krylov) {
+    if (nsweeps == 0) {
+      if (zero_guess) TRY(L_zero<T>(h, L.n, x));
+      if (out64) TRY(L_finalize<T>(h, L.n, x, r64, out64));
+      else if (x64) TRY((L_cast<T, double>(h, L.n, x, x64)));
+      return STOKES_OK;
+    }
+    return relax_krylov<T>(h, l, x, b, nsweeps, zero_guess, r64, out64, x64);
+  }
   if (L.dlsc) {
     if (zero_guess) TRY(L_zero<T>(h, L.n, x));
     for (int s = 0; s < nsweeps * h->dlsc_sweeps; ++s) TRY(dlsc_sweep<T>(h, l, x, b));
@@ -996,6 +1074,49 @@ static int setup_sv(stokes_handle* h, const stokes_problem* const* probs, int ni
   return STOKES_OK;
 }
 
+// Krylov-wrapped relaxation on level l: chunk tables over the level's
+// instance segments (2048 rows, never straddling an instance), the basis
+// vectors and the per-instance scalars.
+static int setup_krylov_relax(stokes_handle* h, Level& lv, const stokes_problem* const* probs, int ninst, int l) {
+  lv.krylov = true;
+  lv.kmax = std::max(std::max(h->nu1, h->nu2), 1);
+  const int k = lv.kmax;
+  lv.lds = 1 + k * (k + 1) + k;
+  lv.ldp = kKrMaxSteps + 1;
+  std::vector<int64_t> cb, ce;
+  std::vector<int> cs, sb(ninst, 0), se(ninst, 0);
+  const int64_t CH = 2048;
+  for (int q = 0; q < ninst; ++q) {
+    sb[q] = (int)cb.size();
+    if (lv.seg_off[q] >= 0) {
+      const int64_t o = lv.seg_off[q], n = probs[q]->K[l].nrows;
+      for (int64_t r = 0; r < n; r += CH) {
+        cb.push_back(o + r);
+        ce.push_back(o + std::min(n, r + CH));
+        cs.push_back(q);
+      }
+    }
+    se[q] = (int)cb.size();
+  }
+  lv.kch.n = (int)cb.size();
+  TRY(upload(h, &lv.kch.beg, cb));
+  TRY(upload(h, &lv.kch.end, ce));
+  TRY(upload(h, &lv.kch.seg, cs));
+  TRY(upload(h, &lv.kch.sbeg, sb));
+  TRY(upload(h, &lv.kch.send, se));
+  const size_t T = esz(h);
+  char *V, *Z, *w;
+  TRY(dalloc(h, &V, (size_t)(k + 1) * lv.n * T));
+  TRY(dalloc(h, &Z, (size_t)k * lv.n * T));
+  TRY(dalloc(h, &w, (size_t)lv.n * T));
+  lv.kV = V;
+  lv.kZ = Z;
+  lv.kw = w;
+  TRY(dalloc(h, &lv.kS, (size_t)ninst * lv.lds));
+  TRY(dalloc(h, &lv.kpart, (size_t)std::max(lv.kch.n, 1) * lv.ldp));
+  return STOKES_OK;
+}
+
 static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int ninst, const stokes_params* prm) {
   const int dim = probs[0]->dim;
   h->dim = dim;
@@ -1058,8 +1179,10 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
   for (int l = 0; l + 1 < L; ++l) {
     if (prm->omega) omega[l] = prm->omega[l];
     if (prm->relax) relaxk[l] = prm->relax[l];
-    if (relaxk[l] != STOKES_RELAX_VANKA && relaxk[l] != STOKES_RELAX_DLSC)
+    if (relaxk[l] != STOKES_RELAX_VANKA && relaxk[l] != STOKES_RELAX_DLSC && relaxk[l] != STOKES_RELAX_VANKA_KRYLOV)
       return fail(STOKES_ERR_INVALID_ARG, "unknown relaxation");
+    if (relaxk[l] == STOKES_RELAX_VANKA_KRYLOV && std::max(prm->nu1, prm->nu2) > kKrMaxSteps)
+      return fail(STOKES_ERR_INVALID_ARG, "Krylov-wrapped relaxation: at most 4 inner steps (nu1, nu2)");
     if (relaxk[l] == STOKES_RELAX_DLSC) {
       if (l == 0) return fail(STOKES_ERR_INVALID_ARG, "DLSC is available on levels >= 1 (Mu = I)");
       for (int k = 0; k < ninst; ++k) {
@@ -1407,6 +1530,8 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     TRY(dalloc(h, &tb, (size_t)lv.n * T));
     lv.x = x; lv.b = b; lv.r = r; lv.ta = ta; lv.tb = tb;
   }
+  for (int l = 0; l + 1 < L; ++l)
+    if (h->lv[l].relax == STOKES_RELAX_VANKA_KRYLOV) TRY(setup_krylov_relax(h, h->lv[l], probs, ninst, l));
   if (h->disc == STOKES_SV) TRY(setup_sv(h, probs, ninst, dim));
   if (h->prec == STOKES_FP32) TRY(dalloc(h, &h->x0_64, (size_t)h->lv[0].n));
   if (!h->d0buf) TRY(dalloc(h, &h->d0buf, (size_t)h->lv[0].n));
@@ -1898,8 +2023,9 @@ static int level_op_impl(stokes_handle* h, int32_t op, int32_t l, const double* 
       }
       TRY(in_cast(lv.n, x, lv.tb));
       TRY(in_cast(lv.n, b, lv.ta));
-      if (f32) TRY(relax<float>(h, l, (float*)lv.tb, (const float*)lv.ta, 1, false));
-      else TRY(relax<double>(h, l, (double*)lv.tb, (const double*)lv.ta, 1, false));
+      const int sweeps = lv.krylov ? lv.kmax : 1;
+      if (f32) TRY(relax<float>(h, l, (float*)lv.tb, (const float*)lv.ta, sweeps, false));
+      else TRY(relax<double>(h, l, (double*)lv.tb, (const double*)lv.ta, sweeps, false));
       return out_cast(lv.n, lv.tb, y);
     }
     case STOKES_OP_COARSE: {

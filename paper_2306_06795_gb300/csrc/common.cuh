@@ -185,6 +185,35 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
 cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
                       const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
                       cudaStream_t st);
+// Krylov-wrapped relaxation (krylov.cu).  Rows of a level cut into chunks
+// that never straddle an instance; sbeg/send: chunk range of each instance.
+constexpr int kKrMaxSteps = 4;  // inner FGMRES steps per relaxation call
+struct KrChunks {
+  int n = 0;
+  int64_t* beg = nullptr;
+  int64_t* end = nullptr;
+  int* seg = nullptr;
+  int* sbeg = nullptr;
+  int* send = nullptr;
+};
+// S[inst*lds + o + i] = sum over the instance's rows of A_i * B, i < nv
+template <typename T>
+cudaError_t kr_dot(const KrChunks& ch, int nv, const T* A, int64_t lda, const T* B, double* partial, int ldp,
+                   double* S, int lds, int o, int ninst, cudaStream_t st);
+// W -= sum_i S[inst*lds + c0 + i] A_i (i < nv), then S[inst*lds + o] = ||W||^2 per instance
+template <typename T>
+cudaError_t kr_axpy_norm(const KrChunks& ch, int nv, const T* A, int64_t lda, int c0, T* W, double* partial, int ldp,
+                         double* S, int lds, int o, int ninst, cudaStream_t st);
+// out = in / sqrt(S[inst*lds + o]) (0 when that is 0)
+template <typename T>
+cudaError_t kr_scale(const KrChunks& ch, const T* in, T* out, const double* S, int lds, int o, cudaStream_t st);
+// y of min ||beta e1 - H y|| per instance (scalar layout in krylov.cu)
+cudaError_t kr_ls(int ninst, int k, double* S, int lds, cudaStream_t st);
+// x = (set ? 0 : x) + sum_j y_j Z_j; optional FP64 copy and level-0 output
+template <typename T>
+cudaError_t kr_update(const KrChunks& ch, int k, const T* Z, int64_t ldz, const double* S, int lds, int oy, T* x,
+                      int set, double* x64, const uint8_t* dir, const double* r64, double* out64, cudaStream_t st);
+
 // Device state of restarted FGMRES, per instance.
 struct FgState {
   double* H;      // [ninst][(m+1)*m], row i column j at i*m + j
