@@ -91,9 +91,9 @@ struct Level {
   KrChunks kch;
   void* kV = nullptr;  // kmax + 1 level vectors
   void* kZ = nullptr;  // kmax level vectors
-  void* kw = nullptr;
   double* kS = nullptr;       // per-instance scalars
   double* kpart = nullptr;    // chunk partials
+  int* kcnt = nullptr;        // per-instance completion counters (0 between calls)
 };
 
 struct Ledger {
@@ -475,8 +475,8 @@ template <typename T, typename TR>
 int L_apply(stokes_handle* h, const Level& lv, const TR* r, T* yp) {
   const DevPatches& p = lv.pat;
   if (h->led.count) {
-    // factors + patch index lists + per-patch metadata + gathered r + patch-major output
-    h->led.bytes += double(p.fac_elems) * sizeof(T) + double(p.nslots) * (4 + sizeof(TR) + sizeof(T)) +
+    // factors + patch index lists + output positions + per-patch metadata + gathered r + output
+    h->led.bytes += double(p.fac_elems) * sizeof(T) + double(p.nslots) * (4 + 4 + sizeof(TR) + sizeof(T)) +
                     double(p.npatch) * (4 + 4 + 4 + 8 + 4);
     for (int b = 0; b < kTmaBins; ++b) h->led.launches += p.nsmall > 0 && p.bins[b].count > 0;
     h->led.launches += p.nlarge > 0;
@@ -491,7 +491,7 @@ int L_scatter(stokes_handle* h, const Level& lv, const T* yp, T* x, double omega
               const double* r64 = nullptr, double* out64 = nullptr, double* x64 = nullptr) {
   const DevPatches& p = lv.pat;
   if (h->led.count) {
-    double b = 4.0 * (lv.n + 1) + double(p.nslots) * (4 + sizeof(T));
+    double b = 4.0 * (lv.n + 1) + double(p.nslots) * sizeof(T);
     if (mode == 0) b += double(lv.n) * sizeof(T);
     else if (mode == 1) b += 2.0 * lv.n * sizeof(T);
     else b += double(lv.n) * (sizeof(T) + 1 + 8);
@@ -667,60 +667,49 @@ int dlsc_sweep(stokes_handle* h, int l, T* x, const T* b) {
 
 // Krylov-wrapped relaxation (Sec. 3.3.1): k steps of flexible GMRES on
 // K e = b - K x from e = 0, right-preconditioned by one undamped Vanka sweep
-// per step (classical Gram-Schmidt, per-instance scalars on the device),
-// then x += Z y.  zero_guess: x starts at 0 and the residual is b.  On level
-// 0 the update also writes the FP64 copy x64 and/or the cycle output out64.
+// per step (classical Gram-Schmidt on unnormalised vectors, per-instance
+// scalars on the device), then x += Z y.  zero_guess: x starts at 0 and
+// the residual is b.  On level 0 the update also writes the FP64 copy x64
+// and/or the cycle output out64.
 template <typename T>
 int relax_krylov(stokes_handle* h, int l, T* x, const T* b, int k, bool zero_guess, const double* r64,
                  double* out64, double* x64) {
   Level& L = h->lv[l];
   const int64_t n = L.n;
-  const int ni = h->ninst;
-  T* V = reinterpret_cast<T*>(L.kV);
+  T* U = reinterpret_cast<T*>(L.kV);
   T* Z = reinterpret_cast<T*>(L.kZ);
-  T* w = reinterpret_cast<T*>(L.kw);
   T* yp = reinterpret_cast<T*>(L.yp);
   const int lds = L.lds;
   const KrChunks& ch = L.kch;
   const double Tb = sizeof(T);
   const T* r = b;
   if (!zero_guess) {
-    TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, V, SPMV_RES)));
-    r = V;
+    TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, U, SPMV_RES)));
+    r = U;
   }
   if (h->led.count) {
-    // beta, v0; per step: Vanka, K z, projections, update + norm, next v; least squares; x update
-    double bytes = 2 * n * Tb + 2 * n * Tb;
-    int launches = 2 + 1;
-    for (int j = 0; j < k; ++j) {
-      bytes += (j + 2) * n * Tb + (j + 3) * n * Tb + (j + 1 < k ? 2 * n * Tb : 0.0);
-      launches += 2 + 2 + (j + 1 < k ? 1 : 0);
-    }
-    bytes += (k + 2) * n * Tb + (x64 ? 8.0 * n : 0.0) + (out64 ? 17.0 * n : 0.0);
-    launches += 2;
+    // ||r||^2 (+ copy); per step: projections and the orthogonalised update + norm; x update
+    double bytes = (zero_guess ? 2.0 : 1.0) * n * Tb;
+    for (int j = 0; j < k; ++j) bytes += (j + 2) * n * Tb + (j + 3) * n * Tb;
+    bytes += (k + (zero_guess ? 1 : 2)) * n * Tb + (x64 ? 8.0 * n : 0.0) + (out64 ? 17.0 * n : 0.0);
     h->led.bytes += bytes;
-    h->led.launches += launches;
+    h->led.launches += 1 + 2 * k + 1;
   } else {
-    CK(kr_dot<T>(ch, 1, r, 0, r, L.kpart, L.ldp, L.kS, lds, 0, ni, h->st));
-    CK(kr_scale<T>(ch, r, V, L.kS, lds, 0, h->st));
+    CK(kr_norm0<T>(ch, r, U, L.kpart, L.ldp, L.kcnt, L.kS, lds, h->st));
   }
   for (int j = 0; j < k; ++j) {
-    T* vj = V + (size_t)j * n;
+    T* uj = U + (size_t)j * n;
     T* zj = Z + (size_t)j * n;
-    TRY((L_apply<T, T>(h, L, vj, yp)));
+    T* w = U + (size_t)(j + 1) * n;
+    TRY((L_apply<T, T>(h, L, uj, yp)));
     TRY(L_scatter<T>(h, L, yp, zj, 1.0, 0));
     TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), zj, (const T*)nullptr, w, SPMV_SET)));
     if (h->led.count) continue;
-    const int col = 1 + j * (k + 1);
-    CK(kr_dot<T>(ch, j + 1, V, n, w, L.kpart, L.ldp, L.kS, lds, col, ni, h->st));
-    CK(kr_axpy_norm<T>(ch, j + 1, V, n, col, w, L.kpart, L.ldp, L.kS, lds, col + j + 1, ni, h->st));
-    if (j + 1 < k) CK(kr_scale<T>(ch, w, V + (size_t)(j + 1) * n, L.kS, lds, col + j + 1, h->st));
+    CK(kr_project<T>(ch, j, k, U, n, w, L.kpart, L.ldp, L.kcnt, L.kS, lds, h->st));
+    CK(kr_orthogonalise<T>(ch, j, k, U, n, w, L.kpart, L.ldp, L.kcnt, L.kS, lds, h->st));
   }
-  if (!h->led.count) {
-    CK(kr_ls(ni, k, L.kS, lds, h->st));
-    CK(kr_update<T>(ch, k, Z, n, L.kS, lds, 1 + k * (k + 1), x, zero_guess ? 1 : 0, x64, h->dir0, r64, out64,
-                    h->st));
-  }
+  if (!h->led.count)
+    CK(kr_update<T>(ch, k, Z, n, L.kS, lds, x, zero_guess ? 1 : 0, x64, h->dir0, r64, out64, h->st));
   return STOKES_OK;
 }
 
@@ -1082,10 +1071,10 @@ static int setup_krylov_relax(stokes_handle* h, Level& lv, const stokes_problem*
   lv.kmax = std::max(std::max(h->nu1, h->nu2), 1);
   const int k = lv.kmax;
   lv.lds = 1 + k * (k + 1) + k;
-  lv.ldp = kKrMaxSteps + 1;
+  lv.ldp = kKrMaxSteps;
   std::vector<int64_t> cb, ce;
   std::vector<int> cs, sb(ninst, 0), se(ninst, 0);
-  const int64_t CH = 2048;
+  const int64_t CH = 2048;  // few chunks: each reduction's completion sums one partial per chunk
   for (int q = 0; q < ninst; ++q) {
     sb[q] = (int)cb.size();
     if (lv.seg_off[q] >= 0) {
@@ -1105,15 +1094,15 @@ static int setup_krylov_relax(stokes_handle* h, Level& lv, const stokes_problem*
   TRY(upload(h, &lv.kch.sbeg, sb));
   TRY(upload(h, &lv.kch.send, se));
   const size_t T = esz(h);
-  char *V, *Z, *w;
+  char *V, *Z;
   TRY(dalloc(h, &V, (size_t)(k + 1) * lv.n * T));
   TRY(dalloc(h, &Z, (size_t)k * lv.n * T));
-  TRY(dalloc(h, &w, (size_t)lv.n * T));
   lv.kV = V;
   lv.kZ = Z;
-  lv.kw = w;
   TRY(dalloc(h, &lv.kS, (size_t)ninst * lv.lds));
   TRY(dalloc(h, &lv.kpart, (size_t)std::max(lv.kch.n, 1) * lv.ldp));
+  TRY(dalloc(h, &lv.kcnt, (size_t)ninst));
+  CK(cudaMemset(lv.kcnt, 0, sizeof(int) * ninst));
   return STOKES_OK;
 }
 
@@ -1448,7 +1437,13 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     TRY(upload(h, &dp.small, small));
     TRY(upload(h, &dp.large, large));
     TRY(upload(h, &dp.tptr, tptr));
-    TRY(upload(h, &dp.tslot, tslot));
+    {
+      // the apply writes slot q to yp[pdst[q]]: DoF-major, so the scatter reads each DoF's
+      // solutions contiguously (same order as the transpose map)
+      std::vector<int> pdst(pdof.size() + 8, 0);
+      for (size_t t = 0; t < tslot.size(); ++t) pdst[tslot[t]] = (int)t;
+      TRY(upload(h, &dp.pdst, pdst));
+    }
     TRY(upload(h, &dp.meta, meta));
     TRY(dalloc(h, &dp.err, 1));
     CK(cudaMemset(dp.err, 0, sizeof(int)));

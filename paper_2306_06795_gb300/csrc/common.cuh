@@ -81,8 +81,9 @@ struct DevPatches {
   int* large = nullptr;   // patch ids with m > 32
   int nlarge = 0;
   int max_m = 0, max_np = 0, max_m_large = 0;
-  int* tptr = nullptr;    // [n+1] transpose map: DoF -> patch-major slots
-  int* tslot = nullptr;
+  int* tptr = nullptr;    // [n+1] DoF j's patch solutions are yp[tptr[j] .. tptr[j+1])
+  int* pdst = nullptr;    // [nslots + 8] position in yp of each patch-major slot (DoF-major,
+                          // ascending original patch order within a DoF)
   int64_t nslots = 0;
   // bulk-copy bins (storage order: bins by m, then the CTA-per-patch rest)
   int4* meta = nullptr;   // [npatch] {ptr, m | np << 16, foff lo, foff hi}
@@ -196,23 +197,26 @@ struct KrChunks {
   int* sbeg = nullptr;
   int* send = nullptr;
 };
-// S[inst*lds + o + i] = sum over the instance's rows of A_i * B, i < nv
+struct KrCols {
+  int c[kKrMaxSteps];  // scalar slots of a multi-column reduction
+};
+// n_0 = ||r||^2 per instance (scalar slot 0); u0 receives r unless u0 == r
 template <typename T>
-cudaError_t kr_dot(const KrChunks& ch, int nv, const T* A, int64_t lda, const T* B, double* partial, int ldp,
-                   double* S, int lds, int o, int ninst, cudaStream_t st);
-// W -= sum_i S[inst*lds + c0 + i] A_i (i < nv), then S[inst*lds + o] = ||W||^2 per instance
+cudaError_t kr_norm0(const KrChunks& ch, const T* r, T* u0, double* partial, int ldp, int* cnt, double* S, int lds,
+                     cudaStream_t st);
+// c_ij = (w, U_i), i <= j, per instance
 template <typename T>
-cudaError_t kr_axpy_norm(const KrChunks& ch, int nv, const T* A, int64_t lda, int c0, T* W, double* partial, int ldp,
-                         double* S, int lds, int o, int ninst, cudaStream_t st);
-// out = in / sqrt(S[inst*lds + o]) (0 when that is 0)
+cudaError_t kr_project(const KrChunks& ch, int j, int k, const T* U, int64_t ldu, const T* w, double* partial,
+                       int ldp, int* cnt, double* S, int lds, cudaStream_t st);
+// w -= sum_{i<=j} (c_ij / n_i) U_i, then n_{j+1} = ||w||^2, per instance
 template <typename T>
-cudaError_t kr_scale(const KrChunks& ch, const T* in, T* out, const double* S, int lds, int o, cudaStream_t st);
-// y of min ||beta e1 - H y|| per instance (scalar layout in krylov.cu)
-cudaError_t kr_ls(int ninst, int k, double* S, int lds, cudaStream_t st);
-// x = (set ? 0 : x) + sum_j y_j Z_j; optional FP64 copy and level-0 output
+cudaError_t kr_orthogonalise(const KrChunks& ch, int j, int k, const T* U, int64_t ldu, T* w, double* partial,
+                             int ldp, int* cnt, double* S, int lds, cudaStream_t st);
+// least squares from the scalars, then x = (set ? 0 : x) + Z coef; optional
+// FP64 copy and level-0 output
 template <typename T>
-cudaError_t kr_update(const KrChunks& ch, int k, const T* Z, int64_t ldz, const double* S, int lds, int oy, T* x,
-                      int set, double* x64, const uint8_t* dir, const double* r64, double* out64, cudaStream_t st);
+cudaError_t kr_update(const KrChunks& ch, int k, const T* Z, int64_t ldz, const double* S, int lds, T* x, int set,
+                      double* x64, const uint8_t* dir, const double* r64, double* out64, cudaStream_t st);
 
 // Device state of restarted FGMRES, per instance.
 struct FgState {

@@ -2,14 +2,21 @@
 // GMRES on K e = b - K x from e = 0, right-preconditioned by one undamped
 // additive Vanka sweep per step, then x += Z y with y minimising
 // ||beta e1 - H y||.  These kernels hold its vector and scalar parts; the
-// sweeps and products are the level's Vanka and SpMV kernels.  Rows are cut
-// into chunks that never straddle an instance, and every reduction sums the
-// chunk partials of an instance in a fixed order, so results are
-// deterministic; each instance keeps its own scalars.
+// sweeps and products are the level's Vanka and SpMV kernels.
 //
-// Scalars of an instance (FP64, stride lds): [0] = ||r||^2, then column j
-// of H at 1 + j (k+1) + i (i <= j: projections, i = j+1: the squared norm
-// of the orthogonalised vector), then y at 1 + k (k+1) + j.
+// The Arnoldi vectors are kept unnormalised (u_0 = r, u_{j+1} = K z_j minus
+// its projections), which saves a scaling pass per step: with
+// c_ij = (K z_j, u_i) and n_i = ||u_i||^2, the normalised Hessenberg matrix
+// is H_ij = c_ij / sqrt(n_i n_j) (i <= j), H_{j+1,j} = sqrt(n_{j+1} / n_j),
+// beta = sqrt(n_0), and x += sum_j (y_j / sqrt(n_j)) z_j.
+//
+// Rows are cut into chunks that never straddle an instance; a reduction's
+// last chunk block of an instance (found with a per-instance counter) adds
+// that instance's chunk partials in a fixed order, so results are
+// deterministic and need no second launch; each instance keeps its own
+// scalars.  Scalars of an instance (FP64, stride lds): n_0 at 0, then for
+// step j at 1 + j (k+1): c_0j .. c_jj, then n_{j+1}; then the k
+// coefficients of the z_j (solved once by the last orthogonalisation).
 #include <cmath>
 
 #include "common.cuh"
@@ -18,109 +25,108 @@ namespace sd {
 
 constexpr int kKrThreads = 256;
 
-// partial[c*ldp + i] = sum over chunk c of A_i[row] * B[row], i < nv
-// (A_i = A + i*lda); per-thread sums in T, warp and block sums in FP64.
-template <typename T, int NV>
-__global__ void __launch_bounds__(kKrThreads) k_kdot(const int64_t* __restrict__ cbeg,
-    const int64_t* __restrict__ cend, int nv, const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
-    double* __restrict__ partial, int ldp) {
+__device__ __forceinline__ int kr_nidx(int i, int k) { return i == 0 ? 0 : 1 + (i - 1) * (k + 1) + i; }
+
+// Last-block completion of a chunked reduction: every block stores its
+// partials; the block that finishes last for its instance sums the
+// instance's partials (thread t takes chunks t, t+256, ... in order, then a
+// fixed block tree) into S and resets the counter.  Returns true in the
+// completing block.
+template <int NV>
+__device__ __forceinline__ bool kr_complete(const KrChunks& ch, int c, int nv, const double (&bsum)[NV],
+                                            double* __restrict__ partial, int ldp, int* __restrict__ cnt,
+                                            double* __restrict__ S, int lds, const int* __restrict__ cols) {
+  __shared__ int last;
+  __shared__ double red[kKrThreads / 32];
+  const int s = ch.seg[c];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nv; ++i) partial[(int64_t)c * ldp + i] = bsum[i];
+    __threadfence();
+    const int done = atomicAdd(cnt + s, 1);
+    last = done == ch.send[s] - ch.sbeg[s] - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = 0; i < nv; ++i) {
+    double v = 0.0;
+#pragma unroll 4
+    for (int q = ch.sbeg[s] + threadIdx.x; q < ch.send[s]; q += kKrThreads) v += __ldcg(partial + (int64_t)q * ldp + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < kKrThreads / 32; ++q) t += red[q];
+      S[(int64_t)s * lds + cols[i]] = t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cnt[s] = 0;
+  return true;
+}
+
+template <int NV>
+__device__ __forceinline__ void kr_block_sums(const double (&v)[NV], int nv, double (&out)[NV]) {
   __shared__ double red[kKrThreads / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[warp][i] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = 0.0;
+    if (i < nv)
+      for (int q = 0; q < kKrThreads / 32; ++q) s += red[q][i];
+    out[i] = s;
+  }
+}
+
+// S[inst][cols[i]] = sum over the instance's rows of A_i[row] * B[row]
+// (i < nv, A_i = A + i*lda); copy, when given, receives B.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kKrThreads) k_kdot(KrChunks ch, int nv, const T* __restrict__ A, int64_t lda,
+    const T* __restrict__ B, T* __restrict__ copy, double* __restrict__ partial, int ldp, int* __restrict__ cnt,
+    double* __restrict__ S, int lds, KrCols cols) {
   const int c = blockIdx.x;
   T acc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = T(0);
-  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kKrThreads) {
+  for (int64_t r = ch.beg[c] + threadIdx.x; r < ch.end[c]; r += kKrThreads) {
     const T bv = B[r];
+    if (copy) copy[r] = bv;
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       if (i < nv) acc[i] += A[(int64_t)i * lda + r] * bv;
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[NV], bs[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double v = (double)acc[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][i] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double s = 0.0;
-    for (int q = 0; q < kKrThreads / 32; ++q) s += red[q][threadIdx.x];
-    partial[(int64_t)c * ldp + threadIdx.x] = s;
-  }
+  for (int i = 0; i < NV; ++i) v[i] = (double)acc[i];
+  kr_block_sums<NV>(v, nv, bs);
+  kr_complete<NV>(ch, c, nv, bs, partial, ldp, cnt, S, lds, cols.c);
 }
 
-// W[row] -= sum_{i<nv} coef_i A_i[row] (coef of the row's instance at
-// S[inst*lds + c0 + i]), then partial[c*ldp] = sum over chunk c of W^2.
-template <typename T>
-__global__ void __launch_bounds__(kKrThreads) k_kaxpy_norm(const int64_t* __restrict__ cbeg,
-    const int64_t* __restrict__ cend, const int* __restrict__ cseg, int nv, const T* __restrict__ A, int64_t lda,
-    const double* __restrict__ S, int lds, int c0, T* __restrict__ W, double* __restrict__ partial, int ldp) {
-  __shared__ double red[kKrThreads / 32];
-  __shared__ T cf[kKrMaxSteps + 1];
-  const int c = blockIdx.x;
-  if (threadIdx.x < nv) cf[threadIdx.x] = T(S[(int64_t)cseg[c] * lds + c0 + threadIdx.x]);
-  __syncthreads();
-  T acc = T(0);
-  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kKrThreads) {
-    T s = T(0);
-    for (int i = 0; i < nv; ++i) s += cf[i] * A[(int64_t)i * lda + r];
-    const T wn = W[r] - s;
-    W[r] = wn;
-    acc += wn * wn;
-  }
-  double v = (double)acc;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int q = 0; q < kKrThreads / 32; ++q) s += red[q];
-    partial[(int64_t)c * ldp] = s;
-  }
-}
-
-// One warp per (instance, column): S[inst*lds + o + col] = sum of the
-// instance's chunk partials in chunk order.
-__global__ void __launch_bounds__(128) k_kfinish(int ninst, const int* __restrict__ sc_beg,
-    const int* __restrict__ sc_end, int ncols, const double* __restrict__ partial, int ldp, double* __restrict__ S,
-    int lds, int o) {
-  const int idx = blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (idx >= ninst * ncols) return;
-  const int s = idx / ncols, k = idx - s * ncols;
-  double v = 0.0;
-  for (int c = sc_beg[s] + lane; c < sc_end[s]; c += 32) v += partial[(int64_t)c * ldp + k];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if (lane == 0) S[(int64_t)s * lds + o + k] = v;
-}
-
-// out[row] = in[row] / sqrt(S[inst*lds + o]) (0 when that squared norm is 0)
-template <typename T>
-__global__ void __launch_bounds__(kKrThreads) k_kscale(const int64_t* __restrict__ cbeg,
-    const int64_t* __restrict__ cend, const int* __restrict__ cseg, const T* __restrict__ in, T* __restrict__ out,
-    const double* __restrict__ S, int lds, int o) {
-  const int c = blockIdx.x;
-  const double n2 = S[(int64_t)cseg[c] * lds + o];
-  const T f = n2 > 0.0 ? T(1.0 / sqrt(n2)) : T(0);
-  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kKrThreads) out[r] = in[r] * f;
-}
-
-// Least squares min ||beta e1 - H y|| per instance by Givens rotations;
-// a zero pivot (exact breakdown, or a zero residual) gives y_j = 0.
-__global__ void k_kls(int ninst, int k, double* __restrict__ S, int lds) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= ninst) return;
-  double* q = S + (size_t)s * lds;
-  double R[kKrMaxSteps + 1][kKrMaxSteps], g[kKrMaxSteps + 1];
+// Least squares min ||beta e1 - H y|| by Givens rotations from the scalars
+// (a zero pivot, an exact breakdown or a zero residual, gives y_j = 0);
+// returns the coefficients of the unnormalised z_j.
+__device__ void kr_solve(const double* __restrict__ q, int k, double* __restrict__ coef) {
+  double R[kKrMaxSteps + 1][kKrMaxSteps], g[kKrMaxSteps + 1], nrm[kKrMaxSteps + 1];
+  for (int i = 0; i <= k; ++i) nrm[i] = sqrt(fmax(q[kr_nidx(i, k)], 0.0));
   for (int j = 0; j < k; ++j) {
-    for (int i = 0; i <= j; ++i) R[i][j] = q[1 + j * (k + 1) + i];
-    R[j + 1][j] = sqrt(fmax(q[1 + j * (k + 1) + j + 1], 0.0));
+    for (int i = 0; i <= j; ++i) {
+      const double d = nrm[i] * nrm[j];
+      R[i][j] = d > 0.0 ? q[1 + j * (k + 1) + i] / d : 0.0;
+    }
+    R[j + 1][j] = nrm[j] > 0.0 ? nrm[j + 1] / nrm[j] : 0.0;
   }
-  g[0] = sqrt(fmax(q[0], 0.0));
+  g[0] = nrm[0];
   for (int i = 1; i <= k; ++i) g[i] = 0.0;
   for (int j = 0; j < k; ++j) {
     const double a = R[j][j], b = R[j + 1][j];
@@ -141,21 +147,57 @@ __global__ void k_kls(int ninst, int k, double* __restrict__ S, int lds) {
     for (int jj = j + 1; jj < k; ++jj) v -= R[j][jj] * y[jj];
     y[j] = R[j][j] != 0.0 ? v / R[j][j] : 0.0;
   }
-  for (int j = 0; j < k; ++j) q[1 + k * (k + 1) + j] = y[j];
+  for (int j = 0; j < k; ++j) coef[j] = nrm[j] > 0.0 ? y[j] / nrm[j] : 0.0;
 }
 
-// x[row] = (set ? 0 : x[row]) + sum_j y_j Z_j[row]; optionally the FP64
-// copy x64 and the level-0 cycle output out64 = dir ? r64 : x.
+// Step j: W -= sum_{i<=j} (c_ij / n_i) U_i, then n_{j+1} = ||W||^2.
 template <typename T>
-__global__ void __launch_bounds__(kKrThreads) k_kupdate(const int64_t* __restrict__ cbeg,
-    const int64_t* __restrict__ cend, const int* __restrict__ cseg, int k, const T* __restrict__ Z, int64_t ldz,
-    const double* __restrict__ S, int lds, int oy, T* __restrict__ x, int set, double* __restrict__ x64,
+__global__ void __launch_bounds__(kKrThreads) k_kaxpy_norm(KrChunks ch, int j, int k, const T* __restrict__ U,
+    int64_t ldu, T* __restrict__ W, double* __restrict__ partial, int ldp, int* __restrict__ cnt,
+    double* __restrict__ S, int lds) {
+  __shared__ T cf[kKrMaxSteps];
+  const int c = blockIdx.x;
+  const double* q = S + (int64_t)ch.seg[c] * lds;
+  if (threadIdx.x <= j) {
+    const double n = q[kr_nidx(threadIdx.x, k)];
+    cf[threadIdx.x] = n > 0.0 ? T(q[1 + j * (k + 1) + threadIdx.x] / n) : T(0);
+  }
+  __syncthreads();
+  T acc = T(0);
+  for (int64_t r = ch.beg[c] + threadIdx.x; r < ch.end[c]; r += kKrThreads) {
+    T s = T(0);
+    for (int i = 0; i <= j; ++i) s += cf[i] * U[(int64_t)i * ldu + r];
+    const T wn = W[r] - s;
+    W[r] = wn;
+    acc += wn * wn;
+  }
+  double v[1] = {(double)acc}, bs[1];
+  kr_block_sums<1>(v, 1, bs);
+  KrCols col;
+  col.c[0] = kr_nidx(j + 1, k);
+  const bool done = kr_complete<1>(ch, c, 1, bs, partial, ldp, cnt, S, lds, col.c);
+  // after the last step, the completing block solves the least-squares
+  // problem of its instance once and stores the coefficients of the z_j
+  if (done && j + 1 == k && threadIdx.x == 0) {
+    double* qs = S + (int64_t)ch.seg[c] * lds;
+    double coef[kKrMaxSteps];
+    kr_solve(qs, k, coef);
+    for (int jj = 0; jj < k; ++jj) qs[1 + k * (k + 1) + jj] = coef[jj];
+  }
+}
+
+// x = (set ? 0 : x) + sum_j coef_j Z_j with the coefficients the last
+// orthogonalisation stored; optionally the FP64 copy x64 and the level-0
+// cycle output out64 = dir ? r64 : x.
+template <typename T>
+__global__ void __launch_bounds__(kKrThreads) k_kupdate(KrChunks ch, int k, const T* __restrict__ Z, int64_t ldz,
+    const double* __restrict__ S, int lds, T* __restrict__ x, int set, double* __restrict__ x64,
     const uint8_t* __restrict__ dir, const double* __restrict__ r64, double* __restrict__ out64) {
   __shared__ T y[kKrMaxSteps];
   const int c = blockIdx.x;
-  if (threadIdx.x < k) y[threadIdx.x] = T(S[(int64_t)cseg[c] * lds + oy + threadIdx.x]);
+  if (threadIdx.x < k) y[threadIdx.x] = T(S[(int64_t)ch.seg[c] * lds + 1 + k * (k + 1) + threadIdx.x]);
   __syncthreads();
-  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += kKrThreads) {
+  for (int64_t r = ch.beg[c] + threadIdx.x; r < ch.end[c]; r += kKrThreads) {
     T v = set ? T(0) : x[r];
     for (int j = 0; j < k; ++j) v += y[j] * Z[(int64_t)j * ldz + r];
     x[r] = v;
@@ -166,62 +208,53 @@ __global__ void __launch_bounds__(kKrThreads) k_kupdate(const int64_t* __restric
 
 // ------------------------------------------------------------- launchers
 template <typename T>
-cudaError_t kr_dot(const KrChunks& ch, int nv, const T* A, int64_t lda, const T* B, double* partial, int ldp,
-                   double* S, int lds, int o, int ninst, cudaStream_t st) {
-  if (ch.n == 0 || nv == 0) return cudaSuccess;
-  if (nv > kKrMaxSteps + 1) return cudaErrorInvalidValue;
-  if (nv == 1)
-    k_kdot<T, 1><<<ch.n, kKrThreads, 0, st>>>(ch.beg, ch.end, nv, A, lda, B, partial, ldp);
-  else
-    k_kdot<T, kKrMaxSteps + 1><<<ch.n, kKrThreads, 0, st>>>(ch.beg, ch.end, nv, A, lda, B, partial, ldp);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_kfinish<<<(ninst * nv + 3) / 4, 128, 0, st>>>(ninst, ch.sbeg, ch.send, nv, partial, ldp, S, lds, o);
+cudaError_t kr_norm0(const KrChunks& ch, const T* r, T* u0, double* partial, int ldp, int* cnt, double* S, int lds,
+                     cudaStream_t st) {
+  if (ch.n == 0) return cudaSuccess;
+  KrCols cols;
+  cols.c[0] = 0;
+  k_kdot<T, 1><<<ch.n, kKrThreads, 0, st>>>(ch, 1, r, 0, r, u0 == r ? nullptr : u0, partial, ldp, cnt, S, lds, cols);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t kr_axpy_norm(const KrChunks& ch, int nv, const T* A, int64_t lda, int c0, T* W, double* partial, int ldp,
-                         double* S, int lds, int o, int ninst, cudaStream_t st) {
+cudaError_t kr_project(const KrChunks& ch, int j, int k, const T* U, int64_t ldu, const T* w, double* partial,
+                       int ldp, int* cnt, double* S, int lds, cudaStream_t st) {
   if (ch.n == 0) return cudaSuccess;
-  if (nv > kKrMaxSteps + 1) return cudaErrorInvalidValue;
-  k_kaxpy_norm<T><<<ch.n, kKrThreads, 0, st>>>(ch.beg, ch.end, ch.seg, nv, A, lda, S, lds, c0, W, partial, ldp);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_kfinish<<<(ninst + 3) / 4, 128, 0, st>>>(ninst, ch.sbeg, ch.send, 1, partial, ldp, S, lds, o);
+  if (j >= kKrMaxSteps || k > kKrMaxSteps) return cudaErrorInvalidValue;
+  KrCols cols;
+  for (int i = 0; i <= j; ++i) cols.c[i] = 1 + j * (k + 1) + i;
+  k_kdot<T, kKrMaxSteps><<<ch.n, kKrThreads, 0, st>>>(ch, j + 1, U, ldu, w, (T*)nullptr, partial, ldp, cnt, S, lds,
+                                                      cols);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t kr_scale(const KrChunks& ch, const T* in, T* out, const double* S, int lds, int o, cudaStream_t st) {
+cudaError_t kr_orthogonalise(const KrChunks& ch, int j, int k, const T* U, int64_t ldu, T* w, double* partial,
+                             int ldp, int* cnt, double* S, int lds, cudaStream_t st) {
   if (ch.n == 0) return cudaSuccess;
-  k_kscale<T><<<ch.n, kKrThreads, 0, st>>>(ch.beg, ch.end, ch.seg, in, out, S, lds, o);
+  if (j >= kKrMaxSteps || k > kKrMaxSteps) return cudaErrorInvalidValue;
+  k_kaxpy_norm<T><<<ch.n, kKrThreads, 0, st>>>(ch, j, k, U, ldu, w, partial, ldp, cnt, S, lds);
   return cudaGetLastError();
 }
 
-cudaError_t kr_ls(int ninst, int k, double* S, int lds, cudaStream_t st) {
+template <typename T>
+cudaError_t kr_update(const KrChunks& ch, int k, const T* Z, int64_t ldz, const double* S, int lds, T* x, int set,
+                      double* x64, const uint8_t* dir, const double* r64, double* out64, cudaStream_t st) {
+  if (ch.n == 0) return cudaSuccess;
   if (k > kKrMaxSteps) return cudaErrorInvalidValue;
-  k_kls<<<(ninst + 63) / 64, 64, 0, st>>>(ninst, k, S, lds);
+  k_kupdate<T><<<ch.n, kKrThreads, 0, st>>>(ch, k, Z, ldz, S, lds, x, set, x64, dir, r64, out64);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t kr_update(const KrChunks& ch, int k, const T* Z, int64_t ldz, const double* S, int lds, int oy, T* x,
-                      int set, double* x64, const uint8_t* dir, const double* r64, double* out64, cudaStream_t st) {
-  if (ch.n == 0) return cudaSuccess;
-  k_kupdate<T><<<ch.n, kKrThreads, 0, st>>>(ch.beg, ch.end, ch.seg, k, Z, ldz, S, lds, oy, x, set, x64, dir, r64,
-                                            out64);
-  return cudaGetLastError();
-}
-
-#define SD_KR(T)                                                                                              \
-  template cudaError_t kr_dot<T>(const KrChunks&, int, const T*, int64_t, const T*, double*, int, double*, int, \
-                                 int, int, cudaStream_t);                                                      \
-  template cudaError_t kr_axpy_norm<T>(const KrChunks&, int, const T*, int64_t, int, T*, double*, int, double*, \
-                                       int, int, int, cudaStream_t);                                           \
-  template cudaError_t kr_scale<T>(const KrChunks&, const T*, T*, const double*, int, int, cudaStream_t);        \
-  template cudaError_t kr_update<T>(const KrChunks&, int, const T*, int64_t, const double*, int, int, T*, int,  \
-                                    double*, const uint8_t*, const double*, double*, cudaStream_t);
+#define SD_KR(T)                                                                                                   \
+  template cudaError_t kr_norm0<T>(const KrChunks&, const T*, T*, double*, int, int*, double*, int, cudaStream_t); \
+  template cudaError_t kr_project<T>(const KrChunks&, int, int, const T*, int64_t, const T*, double*, int, int*,  \
+                                     double*, int, cudaStream_t);                                                \
+  template cudaError_t kr_orthogonalise<T>(const KrChunks&, int, int, const T*, int64_t, T*, double*, int, int*,  \
+                                           double*, int, cudaStream_t);                                          \
+  template cudaError_t kr_update<T>(const KrChunks&, int, const T*, int64_t, const double*, int, T*, int, double*, \
+                                    const uint8_t*, const double*, double*, cudaStream_t);
 SD_KR(float)
 SD_KR(double)
 #undef SD_KR

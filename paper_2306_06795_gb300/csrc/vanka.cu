@@ -469,7 +469,7 @@ template <typename T, typename TR, int DIM>
 __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* __restrict__ list,
     const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, int shared, const T* __restrict__ fac,
-    const TR* __restrict__ r, T* __restrict__ yp, int max_m, int global_a) {
+    const TR* __restrict__ r, T* __restrict__ yp, int max_m, int global_a, const int* __restrict__ pdst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NT = 128, RPT = 4;  // rows per thread: m <= 512
   const int bi = blockIdx.x;
@@ -534,10 +534,10 @@ __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* _
     for (int c = 0; c < DIM; ++c) {
       T x = yu[c][q];
       for (int k = 0; k < np; ++k) x -= U[(int64_t)k * mu + c * m + a] * ypk[k];
-      yp[base + c * m + a] = x;
+      yp[pdst[base + c * m + a]] = x;
     }
   }
-  if (tid < np) yp[base + mu + tid] = ypk[tid];
+  if (tid < np) yp[pdst[base + mu + tid]] = ypk[tid];
 }
 
 // Persistent, warp-specialised patch solves.  Patches are stored bin by bin
@@ -556,12 +556,13 @@ template <typename T, typename TR, int DIM, int NPM, int LP, int R>
 __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     int pstart, int pcount, int ntiles, int tp, int stages, int fac_bytes, int dof_bytes, int rhs_elems, int shared,
     const int4* __restrict__ meta, const int* __restrict__ pptr, const int64_t* __restrict__ foff,
-    const int* __restrict__ dof, const T* __restrict__ fac, const TR* __restrict__ r, T* __restrict__ yp,
-    int* __restrict__ err) {
+    const int* __restrict__ dof, const int* __restrict__ pdst, const T* __restrict__ fac, const TR* __restrict__ r,
+    T* __restrict__ yp, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + stages;
-  const int stage_bytes = fac_bytes + dof_bytes + tp * 16;
+  // stage: factors | index lists | output positions | metadata
+  const int stage_bytes = fac_bytes + 2 * dof_bytes + tp * 16;
   unsigned char* stage0 = smem + 128;
   T* rhsb = reinterpret_cast<T*>(stage0 + (size_t)stages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -589,10 +590,11 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
         const uint32_t fb = (uint32_t)((f1 - f0) * (int64_t)sizeof(T));
         const uint32_t db = (uint32_t)(d1 - d0) * 4u, mb = (uint32_t)(i1 - i0) * 16u;
         unsigned char* st = stage0 + (size_t)s * stage_bytes;
-        mbar_expect_tx(full + s, fb + db + mb);
+        mbar_expect_tx(full + s, fb + 2 * db + mb);
         bulk_g2s(st, fac + f0, fb, full + s, pol);
         bulk_g2s(st + fac_bytes, dof + d0, db, full + s, pol);
-        bulk_g2s(st + fac_bytes + dof_bytes, meta + i0, mb, full + s, pol);
+        bulk_g2s(st + fac_bytes + dof_bytes, pdst + d0, db, full + s, pol);
+        bulk_g2s(st + fac_bytes + 2 * dof_bytes, meta + i0, mb, full + s, pol);
         if (++s == stages) {
           s = 0;
           ++round;
@@ -617,7 +619,8 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     const unsigned char* st = stage0 + (size_t)s * stage_bytes;
     const T* sfac = reinterpret_cast<const T*>(st);
     const int* sdof = reinterpret_cast<const int*>(st + fac_bytes);
-    const int4* smeta = reinterpret_cast<const int4*>(st + fac_bytes + dof_bytes);
+    const int* sdst = reinterpret_cast<const int*>(st + fac_bytes + dof_bytes);
+    const int4* smeta = reinterpret_cast<const int4*>(st + fac_bytes + 2 * dof_bytes);
     const int cnt = min(tp, pend - (pstart + t * tp));
     const int per = (cnt + kNCW - 1) / kNCW;
     const int j0 = min(warp * per, cnt), j1 = min(j0 + per, cnt);
@@ -726,12 +729,12 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
 #pragma unroll
                 for (int kk = 0; kk < NPM; ++kk)
                   if (kk < np) x -= U[kk * mu + c * m + a] * yk[kk];
-                yp[base + c * m + a] = x;
+                yp[sdst[base - a0 + c * m + a]] = x;
               }
             }
 #pragma unroll
           for (int kk = 0; kk < NPM; ++kk)
-            if (kk < np && l == kk) yp[base + mu + kk] = yk[kk];
+            if (kk < np && l == kk) yp[sdst[base - a0 + mu + kk]] = yk[kk];
         }
       }
     }
@@ -749,11 +752,11 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
 
 template <typename T, typename TR, int DIM, int NPM, int LP, int R>
 static cudaError_t launch_tma_bin(const DevPatches& p, const TmaBin& bn, const TR* r, T* yp, cudaStream_t st) {
-  const size_t shm = 128 + (size_t)bn.stages * (bn.fac_bytes + bn.dof_bytes + bn.tp * 16) +
+  const size_t shm = 128 + (size_t)bn.stages * (bn.fac_bytes + 2 * bn.dof_bytes + bn.tp * 16) +
                      (size_t)kNCW * bn.rhs_elems * sizeof(T);
   k_vanka_apply_tma<T, TR, DIM, NPM, LP, R><<<bn.grid, 32 * (kNCW + 1), shm, st>>>(
       bn.start, bn.count, bn.ntiles, bn.tp, bn.stages, bn.fac_bytes, bn.dof_bytes, bn.rhs_elems, p.shared, p.meta,
-      p.ptr, p.foff, p.dof, reinterpret_cast<const T*>(p.fac), r, yp, p.err);
+      p.ptr, p.foff, p.dof, p.pdst, reinterpret_cast<const T*>(p.fac), r, yp, p.err);
   return cudaGetLastError();
 }
 
@@ -786,7 +789,8 @@ static cudaError_t apply_tma_bins(const DevPatches& p, const TR* r, T* yp, cudaS
 // Shared-memory bytes of a TMA bin's tile configuration.
 size_t vanka_tma_smem(const DevPatches& p, const TmaBin& bn, size_t elem) {
   (void)p;
-  return 128 + (size_t)bn.stages * (bn.fac_bytes + bn.dof_bytes + bn.tp * 16) + (size_t)kNCW * bn.rhs_elems * elem;
+  return 128 + (size_t)bn.stages * (bn.fac_bytes + 2 * bn.dof_bytes + bn.tp * 16) +
+         (size_t)kNCW * bn.rhs_elems * elem;
 }
 
 template <typename T, int DIM, int NPM>
@@ -834,10 +838,12 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
     cudaError_t e;
     if (p.dim == 2) {
       k_vanka_apply_cta<T, TR, 2><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga);
+                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga,
+                                                             p.pdst);
     } else {
       k_vanka_apply_cta<T, TR, 3><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga);
+                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga,
+                                                             p.pdst);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -874,21 +880,22 @@ cudaError_t vanka_prepare_kernels() {
 }
 
 // -------------------------------------------------------------- scatter
+// One thread per DoF: the apply stored the DoF's patch solutions
+// contiguously (DoF-major, ascending original patch order), so the thread
+// reads yp[tptr[j] .. tptr[j+1]) with four loads in flight, sums in that
+// order and adds omega * sum / count.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_vanka_scatter(int64_t n, const int* __restrict__ tptr,
-    const int* __restrict__ tslot, const T* __restrict__ yp, T* __restrict__ x, T omega,
-    const uint8_t* __restrict__ dir, const double* __restrict__ r64, double* __restrict__ out64,
-    double* __restrict__ x64) {
+    const T* __restrict__ yp, T* __restrict__ x, T omega, const uint8_t* __restrict__ dir,
+    const double* __restrict__ r64, double* __restrict__ out64, double* __restrict__ x64) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int b = tptr[j], e = tptr[j + 1];
   T s = T(0);
-  // slots of the DoF in ascending patch order; four independent loads in
-  // flight, summed in that order
   for (int k = b; k < e; k += 4) {
     T v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = k + u < e ? yp[tslot[k + u]] : T(0);
+    for (int u = 0; u < 4; ++u) v[u] = k + u < e ? yp[k + u] : T(0);
 #pragma unroll
     for (int u = 0; u < 4; ++u) s += v[u];
   }
@@ -908,11 +915,11 @@ cudaError_t vanka_scatter(const DevPatches& p, int64_t n, const T* yp, T* x, dou
   if (n == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (mode == 0)
-    k_vanka_scatter<T, 0><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64, x64);
+    k_vanka_scatter<T, 0><<<blocks, 256, 0, st>>>(n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
   else if (mode == 1)
-    k_vanka_scatter<T, 1><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64, x64);
+    k_vanka_scatter<T, 1><<<blocks, 256, 0, st>>>(n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
   else
-    k_vanka_scatter<T, 2><<<blocks, 256, 0, st>>>(n, p.tptr, p.tslot, yp, x, T(omega), dir, r64, out64, x64);
+    k_vanka_scatter<T, 2><<<blocks, 256, 0, st>>>(n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
   return cudaGetLastError();
 }
 template cudaError_t vanka_scatter<float>(const DevPatches&, int64_t, const float*, float*, double, int,
