@@ -36,7 +36,7 @@ WORKLOAD = ("2D Taylor-Hood P2/P1 Stokes, unit square 256x256 squares split by t
 METRIC = "Stokes solves/s to 1e-8 rel-res (FP32 DC-AMG preconditioned FGMRES)"
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-0 FP32 apply launch, from the ncu
 # capture summarised in profiles/vanka_apply_tma_c2_level0.md (set to None when the kernel changes)
-APPLY_L0_DRAM_BYTES = None  # the apply now also reads its output positions: counters to be retaken
+APPLY_L0_DRAM_BYTES = 87.55e6
 
 
 def dist_env():
@@ -258,6 +258,32 @@ def run_gpu(args):
         vck = g0.elapsed_time(g1) / 10
         sd.stokes_destroy(hk)
 
+        # the paper's comparison preconditioner BTP (Sec. 4) on the same solve
+        from problems import btp as pbtp
+        pr.btp = pbtp.build_btp(pr)
+        hb = sd.stokes_setup(pr, dict(prm, precision=sd.STOKES_FP32, preconditioner=sd.STOKES_PRECOND_BTP,
+                                      btp_steps=2), stream=stream.cuda_stream)
+        xb = torch.zeros_like(b)
+
+        def step_btp():
+            xb.zero_()
+            rc, info = sd.stokes_fgmres_solve(hb, b, xb, rtol=rtol, restart=restart, maxit=maxit)
+            if rc != sd.STOKES_OK:
+                raise RuntimeError(f"BTP solve did not converge: {info}")
+            return info[0]
+
+        for _ in range(2):
+            infob = step_btp()
+        torch.cuda.synchronize()
+        g0.record(stream)
+        for _ in range(kk):
+            infob = step_btp()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        msb = g0.elapsed_time(g1) / kk
+        sd.stokes_destroy(hb)
+        pr.btp = None
+
         # batched patch factorisation alone
         fct = {}
         for prec, hh in handles.items():
@@ -342,6 +368,12 @@ def run_gpu(args):
                                   "eta 1, FP32 cycle",
                          "value": 1000.0 / msk, "unit": "solves/s", "ms_per_step": msk, "iters": int(infok[0]),
                          "true_relres": float(infok[2]), "vcycle_ms": vck},
+        "btp": {"preconditioner": "block-triangular BTP (Sec. 4): SA V-cycle on A, SA V-cycle on M_p/nu, "
+                                  "2 Krylov-wrapped Jacobi steps, FP32 cycles",
+                "value": 1000.0 / msb, "unit": "solves/s", "ms_per_step": msb, "iters": int(infob[0]),
+                "true_relres": float(infob[2]),
+                "dc_solve_ms_without_factorisation": ms - fct[sd.STOKES_FP32],
+                "dc_solve_time_over_btp": (ms - fct[sd.STOKES_FP32]) / msb if msb > 0 else None},
         "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(16 * n),
                 "d2h_bytes_per_step": int(8 * n), "true_relres": e2e_res},
         "gpu_launches": int(launches),

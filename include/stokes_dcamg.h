@@ -63,6 +63,9 @@ enum { STOKES_DC_ALL = 0, STOKES_DC_SKIP1 = 1, STOKES_DC_SKIP0 = 2 };  /* Sec. 4
  * the least-squares minimiser (nu <= 4; omega unused). */
 enum { STOKES_RELAX_VANKA = 0, STOKES_RELAX_DLSC = 1, STOKES_RELAX_VANKA_KRYLOV = 2 };
 enum { STOKES_FP32 = 0, STOKES_FP64 = 1 };                   /* cycle precision */
+/* Preconditioner of the FGMRES solve (and of stokes_vcycle): the DC cycle,
+ * or the block-triangular comparison preconditioner BTP of Sec. 4. */
+enum { STOKES_PRECOND_DC = 0, STOKES_PRECOND_BTP = 1 };
 
 /* A sparse matrix in CSR form, host memory, FP64 values.  Column indices
  * must be sorted ascending and unique within each row. */
@@ -87,6 +90,26 @@ typedef struct {
   const int32_t* nvel;  /* [npatch * dim] */
   const int32_t* npres; /* [npatch] */
 } stokes_patches;
+
+/* Data of the block-triangular preconditioner BTP (Sec. 4), built by the
+ * host setup step: with [r_u, r_p] = r it returns
+ *   du = Q_A^-1 r_u,   dp = Q_B^-1 (B du - r_p),
+ * Q_A^-1 one SA V-cycle on the vector Laplacian A (levels A[l], prolongators
+ * PA[l] mapping level l+1 to l, Galerkin coarse operators, btp_steps
+ * Krylov-wrapped Jacobi steps before and after the coarse correction, exact
+ * coarsest solve), Q_B^-1 the same kind of V-cycle on M (M[0] = M_p / nu,
+ * Taylor-Hood) or the exact inverse Minv (Scott-Vogelius, block diagonal).
+ * Dirichlet velocity rows return r_u. */
+typedef struct {
+  int32_t nlevels_a;              /* >= 1 */
+  const stokes_csr* A;            /* [nlevels_a]: A[0] = velocity block of K0 */
+  const stokes_csr* PA;           /* [nlevels_a - 1] */
+  const stokes_csr* B;            /* pressure rows x velocity columns of K0 */
+  int32_t nlevels_m;              /* levels of the M hierarchy, 0 when Minv is given */
+  const stokes_csr* M;            /* [nlevels_m] */
+  const stokes_csr* PM;           /* [nlevels_m - 1] */
+  const stokes_csr* Minv;         /* exact inverse of M_p / nu, or NULL */
+} stokes_btp;
 
 /* One Stokes problem and its solver hierarchy, built by a host setup step.
  * Level 0 is K0 (high order), level 1 the P1isoP2/P1 operator K1, levels
@@ -114,6 +137,9 @@ typedef struct {
   /* DLSC (Sec. 3.3.2): largest-eigenvalue estimates per level, may be NULL */
   const double* lambda_A;         /* [nlevels] of the velocity block A */
   const double* lambda_S;         /* [nlevels] of B Mu^-1 B^T */
+  /* BTP (Sec. 4), used when stokes_params.preconditioner is
+   * STOKES_PRECOND_BTP (single-instance handles); may be NULL otherwise */
+  const stokes_btp* btp;
 } stokes_problem;
 
 /* Parameters of the defect-correction cycle (Table param_ref). */
@@ -127,6 +153,8 @@ typedef struct {
   int32_t dlsc_sweeps;       /* DLSC sweeps per relaxation call */
   int32_t mcg_deg;           /* Chebyshev-Jacobi degree of the SV mass-matrix solve */
   int32_t precision;         /* STOKES_FP32 or STOKES_FP64 cycle */
+  int32_t preconditioner;    /* STOKES_PRECOND_DC or STOKES_PRECOND_BTP */
+  int32_t btp_steps;         /* BTP: Krylov-wrapped Jacobi steps per relaxation (1..4) */
 } stokes_params;
 
 typedef struct {

@@ -26,6 +26,7 @@ STOKES_ERR_STATE = -6
 STOKES_TH, STOKES_SV = 0, 1
 STOKES_DC_ALL, STOKES_DC_SKIP1, STOKES_DC_SKIP0 = 0, 1, 2
 STOKES_RELAX_VANKA, STOKES_RELAX_DLSC, STOKES_RELAX_VANKA_KRYLOV = 0, 1, 2
+STOKES_PRECOND_DC, STOKES_PRECOND_BTP = 0, 1
 STOKES_FP32, STOKES_FP64 = 0, 1
 STOKES_KERNEL_VANKA_APPLY, STOKES_KERNEL_SCATTER, STOKES_KERNEL_SPMV, STOKES_KERNEL_DC_RESIDUAL = range(4)
 (STOKES_OP_SPMV, STOKES_OP_SPMV_F64, STOKES_OP_RESIDUAL, STOKES_OP_RESTRICT,
@@ -50,6 +51,12 @@ class stokes_patches(C.Structure):
                 ("nvel", C.POINTER(C.c_int32)), ("npres", C.POINTER(C.c_int32))]
 
 
+class stokes_btp(C.Structure):
+    _fields_ = [("nlevels_a", C.c_int32), ("A", C.POINTER(stokes_csr)), ("PA", C.POINTER(stokes_csr)),
+                ("B", C.POINTER(stokes_csr)), ("nlevels_m", C.c_int32), ("M", C.POINTER(stokes_csr)),
+                ("PM", C.POINTER(stokes_csr)), ("Minv", C.POINTER(stokes_csr))]
+
+
 class stokes_problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("disc", C.c_int32), ("nlevels", C.c_int32),
                 ("field_off", C.POINTER(C.c_int64)), ("K", C.POINTER(stokes_csr)),
@@ -57,14 +64,16 @@ class stokes_problem(C.Structure):
                 ("coarse_null", C.POINTER(C.c_double)), ("dirichlet", C.POINTER(C.c_uint8)),
                 ("R0p", C.POINTER(stokes_csr)), ("Mcg", C.POINTER(stokes_csr)),
                 ("mcg_lo", C.c_double), ("mcg_hi", C.c_double),
-                ("lambda_A", C.POINTER(C.c_double)), ("lambda_S", C.POINTER(C.c_double))]
+                ("lambda_A", C.POINTER(C.c_double)), ("lambda_S", C.POINTER(C.c_double)),
+                ("btp", C.POINTER(stokes_btp))]
 
 
 class stokes_params(C.Structure):
     _fields_ = [("schedule", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("eta_u", C.c_double), ("eta_p", C.c_double), ("omega", C.POINTER(C.c_double)),
                 ("relax", C.POINTER(C.c_int32)), ("cheb_deg", C.c_int32 * 3), ("dlsc_sweeps", C.c_int32),
-                ("mcg_deg", C.c_int32), ("precision", C.c_int32)]
+                ("mcg_deg", C.c_int32), ("precision", C.c_int32), ("preconditioner", C.c_int32),
+                ("btp_steps", C.c_int32)]
 
 
 class stokes_solve_info(C.Structure):
@@ -185,6 +194,30 @@ def _problem(keep, pr):
         ls = keep.arr(pr.lambda_S, np.float64)
         p.lambda_A = _p(la, C.c_double)
         p.lambda_S = _p(ls, C.c_double)
+    bt = getattr(pr, "btp", None)
+    if bt is not None:
+        q = stokes_btp()
+        As = (stokes_csr * len(bt.A))(*[_csr(keep, a) for a in bt.A])
+        PAs = (stokes_csr * max(len(bt.PA), 1))(*[_csr(keep, a) for a in bt.PA])
+        Bc = _csr(keep, bt.B)
+        keep.refs += [As, PAs, Bc, q]
+        q.nlevels_a = len(bt.A)
+        q.A = C.cast(As, C.POINTER(stokes_csr))
+        q.PA = C.cast(PAs, C.POINTER(stokes_csr))
+        q.B = C.pointer(Bc)
+        if bt.Minv is not None:
+            mi = _csr(keep, bt.Minv)
+            keep.refs.append(mi)
+            q.Minv = C.pointer(mi)
+            q.nlevels_m = 0
+        else:
+            Ms = (stokes_csr * len(bt.M))(*[_csr(keep, a) for a in bt.M])
+            PMs = (stokes_csr * max(len(bt.PM), 1))(*[_csr(keep, a) for a in bt.PM])
+            keep.refs += [Ms, PMs]
+            q.nlevels_m = len(bt.M)
+            q.M = C.cast(Ms, C.POINTER(stokes_csr))
+            q.PM = C.cast(PMs, C.POINTER(stokes_csr))
+        p.btp = C.pointer(q)
     return p
 
 
@@ -213,6 +246,8 @@ def _params(keep, prm, nlevels):
     s.dlsc_sweeps = int(prm.get("dlsc_sweeps", 2))
     s.mcg_deg = int(prm.get("mcg_deg", 32))
     s.precision = int(prm.get("precision", STOKES_FP32))
+    s.preconditioner = int(prm.get("preconditioner", STOKES_PRECOND_DC))
+    s.btp_steps = int(prm.get("btp_steps", 2))
     return s
 
 

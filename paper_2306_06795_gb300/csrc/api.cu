@@ -85,8 +85,11 @@ struct Level {
   std::vector<int64_t> seg_off;  // per instance, -1 when absent
   bool dlsc = false;
   DLSCData dl;
-  // Krylov-wrapped relaxation (Sec. 3.3.1)
+  // Krylov-wrapped relaxation (Sec. 3.3.1); jacobi: its inner
+  // preconditioner is diag(K)^-1 instead of a Vanka sweep (BTP's SA cycles)
   bool krylov = false;
+  bool jacobi = false;
+  void* dinv = nullptr;
   int kmax = 0, lds = 0, ldp = 0;
   KrChunks kch;
   void* kV = nullptr;  // kmax + 1 level vectors
@@ -106,6 +109,12 @@ struct Ledger {
 
 struct stokes_handle {
   int ninst = 0, dim = 2, disc = STOKES_TH, prec = STOKES_FP32, L = 0;
+  // preconditioner: the DC cycle, or the block-triangular BTP (Sec. 4)
+  int precond = STOKES_PRECOND_DC;
+  int btp_steps = 2;
+  std::vector<Level> btpA, btpM;  // SA hierarchies of A and of M_p / nu (TH)
+  DevCSR btpB, btpMinv;           // B (pressure rows x velocity columns); SV exact mass inverse
+  void* btp_tp = nullptr;         // level-0 pressure work vector
   int schedule = 0, nu1 = 1, nu2 = 1;
   double eta_u = 1.0, eta_p = 1.0;
   cudaStream_t st = nullptr;
@@ -390,14 +399,15 @@ bool components_share_block(const stokes_csr* K, const int64_t* off, int dim) {
 // Dense inverse of the bordered coarsest matrix [K n; n^T 0] by LU with
 // partial pivoting (FP64); returns the leading n x n block row-major.
 int bordered_inverse(const stokes_csr* K, const double* nullv, std::vector<double>& out) {
-  const int n = K->nrows, nb = n + 1;
+  const int n = K->nrows, nb = nullv ? n + 1 : n;  // no border: the plain inverse
   std::vector<double> M((size_t)nb * nb, 0.0), I((size_t)nb * nb, 0.0);
   for (int i = 0; i < n; ++i)
     for (int64_t k = K->rowptr[i]; k < K->rowptr[i + 1]; ++k) M[(size_t)i * nb + K->col[k]] = K->val[k];
-  for (int i = 0; i < n; ++i) {
-    M[(size_t)i * nb + n] = nullv[i];
-    M[(size_t)n * nb + i] = nullv[i];
-  }
+  if (nullv)
+    for (int i = 0; i < n; ++i) {
+      M[(size_t)i * nb + n] = nullv[i];
+      M[(size_t)n * nb + i] = nullv[i];
+    }
   for (int i = 0; i < nb; ++i) I[(size_t)i * nb + i] = 1.0;
   double amax = 0.0;
   for (double v : M) amax = std::max(amax, std::fabs(v));
@@ -527,6 +537,17 @@ int L_axpy(stokes_handle* h, int64_t n, double a, const TI* x, T* y) {
 }
 
 template <typename T>
+int L_diag_scale(stokes_handle* h, int64_t n, const T* d, const T* u, T* z) {
+  if (h->led.count) {
+    h->led.bytes += 3.0 * n * sizeof(T);
+    h->led.launches += n > 0;
+    return STOKES_OK;
+  }
+  CK(diag_scale<T>(n, d, u, z, h->st));
+  return STOKES_OK;
+}
+
+template <typename T>
 int L_zero(stokes_handle* h, int64_t n, T* y) {
   if (h->led.count) {
     h->led.bytes += double(n) * sizeof(T);
@@ -636,8 +657,8 @@ namespace {
 // One DLSC sweep (Alg. 2) on level l with Mu = I: momentum, continuity and
 // pressure-correction Chebyshev solves, then the velocity correction.
 template <typename T>
-int dlsc_sweep(stokes_handle* h, int l, T* x, const T* b) {
-  Level& L = h->lv[l];
+int dlsc_sweep(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b) {
+  Level& L = lvs[l];
   DLSCData& D = L.dl;
   T** v = reinterpret_cast<T**>(D.v);
   T *res = v[0], *vs = v[1], *q = v[2], *dp = v[3], *t1 = v[4], *t2 = v[5], *cr = v[6], *c0 = v[7], *c1 = v[8];
@@ -672,9 +693,9 @@ int dlsc_sweep(stokes_handle* h, int l, T* x, const T* b) {
 // the residual is b.  On level 0 the update also writes the FP64 copy x64
 // and/or the cycle output out64.
 template <typename T>
-int relax_krylov(stokes_handle* h, int l, T* x, const T* b, int k, bool zero_guess, const double* r64,
-                 double* out64, double* x64) {
-  Level& L = h->lv[l];
+int relax_krylov(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b, int k, bool zero_guess,
+                 const double* r64, double* out64, double* x64) {
+  Level& L = lvs[l];
   const int64_t n = L.n;
   T* U = reinterpret_cast<T*>(L.kV);
   T* Z = reinterpret_cast<T*>(L.kZ);
@@ -701,8 +722,12 @@ int relax_krylov(stokes_handle* h, int l, T* x, const T* b, int k, bool zero_gue
     T* uj = U + (size_t)j * n;
     T* zj = Z + (size_t)j * n;
     T* w = U + (size_t)(j + 1) * n;
-    TRY((L_apply<T, T>(h, L, uj, yp)));
-    TRY(L_scatter<T>(h, L, yp, zj, 1.0, 0));
+    if (L.jacobi) {
+      TRY(L_diag_scale<T>(h, L.n, reinterpret_cast<const T*>(L.dinv), uj, zj));
+    } else {
+      TRY((L_apply<T, T>(h, L, uj, yp)));
+      TRY(L_scatter<T>(h, L, yp, zj, 1.0, 0));
+    }
     TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), zj, (const T*)nullptr, w, SPMV_SET)));
     if (h->led.count) continue;
     CK(kr_project<T>(ch, j, k, U, n, w, L.kpart, L.ldp, L.kcnt, L.kS, lds, h->st));
@@ -718,9 +743,9 @@ int relax_krylov(stokes_handle* h, int l, T* x, const T* b, int k, bool zero_gue
 // the last scatter writes the level-0 output (Dirichlet rows take r64).
 // A DLSC level runs nsweeps calls of dlsc_sweeps DLSC sweeps instead.
 template <typename T>
-int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_guess, const double* r64 = nullptr,
-          double* out64 = nullptr, double* x64 = nullptr) {
-  Level& L = h->lv[l];
+int relax(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b, int nsweeps, bool zero_guess,
+          const double* r64 = nullptr, double* out64 = nullptr, double* x64 = nullptr) {
+  Level& L = lvs[l];
   if (L.krylov) {
     if (nsweeps == 0) {
       if (zero_guess) TRY(L_zero<T>(h, L.n, x));
@@ -728,11 +753,11 @@ int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_gues
       else if (x64) TRY((L_cast<T, double>(h, L.n, x, x64)));
       return STOKES_OK;
     }
-    return relax_krylov<T>(h, l, x, b, nsweeps, zero_guess, r64, out64, x64);
+    return relax_krylov<T>(h, lvs, l, x, b, nsweeps, zero_guess, r64, out64, x64);
   }
   if (L.dlsc) {
     if (zero_guess) TRY(L_zero<T>(h, L.n, x));
-    for (int s = 0; s < nsweeps * h->dlsc_sweeps; ++s) TRY(dlsc_sweep<T>(h, l, x, b));
+    for (int s = 0; s < nsweeps * h->dlsc_sweeps; ++s) TRY(dlsc_sweep<T>(h, lvs, l, x, b));
     return STOKES_OK;
   }
   T* r = reinterpret_cast<T*>(L.r);
@@ -753,26 +778,29 @@ int relax(stokes_handle* h, int l, T* x, const T* b, int nsweeps, bool zero_gues
   return STOKES_OK;
 }
 
-// Galerkin V-cycle on level l >= 1 (Eq. TG-operator), zero initial guess:
-// input lv[l].b, output lv[l].x.  Instances whose coarsest level is l take
-// the exact bordered solve on their segment.
+// Galerkin V-cycle on level l of the hierarchy lvs (Eq. TG-operator for
+// the DC cycle's K1 hierarchy, l >= 1; the SA cycles of BTP from l = 0),
+// zero initial guess: input lvs[l].b, output lvs[l].x.  Instances whose
+// coarsest level is l take the exact (bordered) solve on their segment.
 template <typename T>
-int vcycle(stokes_handle* h, int l) {
-  Level& L = h->lv[l];
+int vcycle(stokes_handle* h, std::vector<Level>& lvs, int l) {
+  Level& L = lvs[l];
   T* x = reinterpret_cast<T*>(L.x);
   T* b = reinterpret_cast<T*>(L.b);
-  if (l == h->L - 1) return L_coarse<T>(h, L, b, x);
-  const bool relax_here = (L.has_patches || L.dlsc) && !(h->schedule == STOKES_DC_SKIP1 && l == 1);
-  if (relax_here) TRY(relax<T>(h, l, x, b, h->nu1, true));
+  if (l == (int)lvs.size() - 1) return L_coarse<T>(h, L, b, x);
+  const bool main = &lvs == &h->lv;
+  const bool relax_here = (L.has_patches || L.dlsc || L.jacobi) && !(main && h->schedule == STOKES_DC_SKIP1 && l == 1);
+  const int nu1 = main ? h->nu1 : h->btp_steps, nu2 = main ? h->nu2 : h->btp_steps;
+  if (relax_here) TRY(relax<T>(h, lvs, l, x, b, nu1, true));
   else TRY(L_zero<T>(h, L.n, x));
   TRY(L_coarse<T>(h, L, b, x));
   T* r = reinterpret_cast<T*>(L.r);
-  Level& C = h->lv[l + 1];
+  Level& C = lvs[l + 1];
   TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
   TRY((L_spmv<T, T, T, T, T>(h, L.R, kval<T>(L.R), r, (const T*)nullptr, reinterpret_cast<T*>(C.b), SPMV_SET)));
-  TRY(vcycle<T>(h, l + 1));
+  TRY(vcycle<T>(h, lvs, l + 1));
   TRY((L_spmv<T, T, T, T, T>(h, L.P, kval<T>(L.P), reinterpret_cast<const T*>(C.x), (const T*)nullptr, x, SPMV_ADD)));
-  if (relax_here) TRY(relax<T>(h, l, x, b, h->nu2, false));
+  if (relax_here) TRY(relax<T>(h, lvs, l, x, b, nu2, false));
   return STOKES_OK;
 }
 
@@ -818,7 +846,7 @@ int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
   // so that residual converts each entry once instead of once per nonzero
   double* x0d = sizeof(T) == 8 ? reinterpret_cast<double*>(x0) : h->x0_64;
   const bool pre = !skip0 && h->nu1 > 0;
-  if (pre) TRY(relax<T>(h, 0, x0, r0, h->nu1, true, nullptr, nullptr, sizeof(T) == 8 ? nullptr : x0d));
+  if (pre) TRY(relax<T>(h, h->lv, 0, x0, r0, h->nu1, true, nullptr, nullptr, sizeof(T) == 8 ? nullptr : x0d));
   else {
     TRY(L_zero<T>(h, L0.n, x0));
     if (sizeof(T) != 8) TRY(L_zero<double>(h, L0.n, x0d));
@@ -835,15 +863,57 @@ int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
   } else {
     TRY(restrict0_sv(h, x0d, r64));
   }
-  TRY(vcycle<T>(h, 1));
+  TRY(vcycle<T>(h, h->lv, 1));
   if (L0.Pident) TRY((L_axpy<T, T>(h, L0.n, 1.0, reinterpret_cast<const T*>(L1.x), x0)));  // P0 = I
   else TRY((L_spmv<T, T, T, T, T>(h, L0.P, kval<T>(L0.P), reinterpret_cast<const T*>(L1.x), (const T*)nullptr, x0, SPMV_ADD)));
-  if (!skip0 && h->nu2 > 0) TRY(relax<T>(h, 0, x0, r0, h->nu2, false, r64, z64));
+  if (!skip0 && h->nu2 > 0) TRY(relax<T>(h, h->lv, 0, x0, r0, h->nu2, false, r64, z64));
   else TRY(L_finalize<T>(h, L0.n, x0, r64, z64));
   return STOKES_OK;
 }
 
+template <typename T>
+int L_btp_out(stokes_handle* h, int64_t nu, int64_t np, const T* du, const T* dp, double sp, const double* r64,
+              double* z) {
+  if (h->led.count) {
+    h->led.bytes += double(nu) * (sizeof(T) + 1 + 8 + 8) + double(np) * (sizeof(T) + 8);
+    h->led.launches += nu + np > 0;
+    return STOKES_OK;
+  }
+  CK(btp_out<T>(nu, np, du, dp, sp, h->dir0, r64, z, h->st));
+  return STOKES_OK;
+}
+
+// BTP (Sec. 4): du = Q_A^-1 r_u (SA V-cycle on A), y = r_p - B du,
+// Q_B^-1 y (SA V-cycle on M_p / nu, or the exact block inverse), and the
+// pressure update dp = -Q_B^-1 y = Q_B^-1 (B du - r_p).
+template <typename T>
+int btp_cycle(stokes_handle* h, const double* r64, double* z64) {
+  Level& A0 = h->btpA[0];
+  const int64_t nu = A0.n, np = h->lv[0].n - nu;
+  T* tp = reinterpret_cast<T*>(h->btp_tp);
+  TRY((L_cast<double, T>(h, nu, r64, reinterpret_cast<T*>(A0.b))));
+  TRY((L_cast<double, T>(h, np, r64 + nu, tp)));
+  TRY(vcycle<T>(h, h->btpA, 0));
+  const T* du = reinterpret_cast<const T*>(A0.x);
+  const T* dq;
+  if (!h->btpM.empty()) {
+    Level& M0 = h->btpM[0];
+    TRY((L_spmv<T, T, T, T, T>(h, h->btpB, kval<T>(h->btpB), du, tp, reinterpret_cast<T*>(M0.b), SPMV_RES)));
+    TRY(vcycle<T>(h, h->btpM, 0));
+    dq = reinterpret_cast<const T*>(M0.x);
+  } else {
+    T* y = tp + np;
+    T* w = tp + 2 * np;
+    TRY((L_spmv<T, T, T, T, T>(h, h->btpB, kval<T>(h->btpB), du, tp, y, SPMV_RES)));
+    TRY((L_spmv<T, T, T, T, T>(h, h->btpMinv, kval<T>(h->btpMinv), y, (const T*)nullptr, w, SPMV_SET)));
+    dq = w;
+  }
+  return L_btp_out<T>(h, nu, np, du, dq, -1.0, r64, z64);
+}
+
 int run_cycle(stokes_handle* h, const double* r, double* z) {
+  if (h->precond == STOKES_PRECOND_BTP)
+    return h->prec == STOKES_FP32 ? btp_cycle<float>(h, r, z) : btp_cycle<double>(h, r, z);
   return h->prec == STOKES_FP32 ? dc_cycle<float>(h, r, z) : dc_cycle<double>(h, r, z);
 }
 
@@ -1106,6 +1176,147 @@ static int setup_krylov_relax(stokes_handle* h, Level& lv, const stokes_problem*
   return STOKES_OK;
 }
 
+// BTP (Sec. 4): the SA hierarchies of A and of M_p / nu (or the exact
+// block inverse), B, Jacobi diagonals, Krylov-relaxation chunks and work
+// vectors.  Single-instance handles only.
+static int setup_btp_levels(stokes_handle* h, std::vector<Level>& lvs, const stokes_csr* K, const stokes_csr* P,
+                            int nl, const char* what) {
+  lvs.assign(nl, Level());
+  const size_t T = esz(h);
+  for (int l = 0; l < nl; ++l) {
+    TRY(check_csr(&K[l], what));
+    if (K[l].nrows != K[l].ncols) return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": operator not square");
+    if (l + 1 < nl) {
+      TRY(check_csr(&P[l], what));
+      if (P[l].nrows != K[l].nrows || P[l].ncols != K[l + 1].nrows)
+        return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": prolongator sizes");
+    }
+  }
+  for (int l = 0; l < nl; ++l) {
+    Level& lv = lvs[l];
+    lv.n = K[l].nrows;
+    lv.seg_off.assign(1, 0);
+    HostCSR Kh;
+    Kh.nrows = Kh.ncols = (int)lv.n;
+    append_block(Kh, &K[l], 0);
+    TRY(upload_csr(h, lv.K, Kh));
+    if (l + 1 < nl) {
+      HostCSR Ph;
+      Ph.nrows = (int)lv.n;
+      Ph.ncols = K[l + 1].nrows;
+      append_block(Ph, &P[l], 0);
+      lv.hasP = true;
+      TRY(upload_csr(h, lv.P, Ph));
+      TRY(upload_csr(h, lv.R, transpose(Ph)));
+      // Jacobi diagonals
+      std::vector<double> d(lv.n, 0.0);
+      for (int i = 0; i < K[l].nrows; ++i)
+        for (int64_t k = K[l].rowptr[i]; k < K[l].rowptr[i + 1]; ++k)
+          if (K[l].col[k] == i) d[i] = K[l].val[k];
+      for (auto& v : d) {
+        if (!(v != 0.0)) return fail(STOKES_ERR_INVALID_ARG, std::string(what) + ": zero diagonal");
+        v = 1.0 / v;
+      }
+      char* dv = nullptr;
+      if (h->prec == STOKES_FP32) {
+        std::vector<float> f(d.begin(), d.end());
+        float* q = nullptr;
+        TRY(upload(h, &q, f));
+        dv = reinterpret_cast<char*>(q);
+      } else {
+        double* q = nullptr;
+        TRY(upload(h, &q, d));
+        dv = reinterpret_cast<char*>(q);
+      }
+      lv.dinv = dv;
+      lv.jacobi = true;
+      lv.relax = STOKES_RELAX_VANKA_KRYLOV;
+      lv.krylov = true;
+      lv.kmax = h->btp_steps;
+      const int k = lv.kmax;
+      lv.lds = 1 + k * (k + 1) + k;
+      lv.ldp = kKrMaxSteps;
+      std::vector<int64_t> cb, ce;
+      std::vector<int> cs, sb{0}, se;
+      for (int64_t r = 0; r < lv.n; r += 2048) {
+        cb.push_back(r);
+        ce.push_back(std::min<int64_t>(lv.n, r + 2048));
+        cs.push_back(0);
+      }
+      se.push_back((int)cb.size());
+      lv.kch.n = (int)cb.size();
+      TRY(upload(h, &lv.kch.beg, cb));
+      TRY(upload(h, &lv.kch.end, ce));
+      TRY(upload(h, &lv.kch.seg, cs));
+      TRY(upload(h, &lv.kch.sbeg, sb));
+      TRY(upload(h, &lv.kch.send, se));
+      char *V, *Z;
+      TRY(dalloc(h, &V, (size_t)(k + 1) * lv.n * T));
+      TRY(dalloc(h, &Z, (size_t)k * lv.n * T));
+      lv.kV = V;
+      lv.kZ = Z;
+      TRY(dalloc(h, &lv.kS, (size_t)lv.lds));
+      TRY(dalloc(h, &lv.kpart, (size_t)std::max(lv.kch.n, 1) * lv.ldp));
+      TRY(dalloc(h, &lv.kcnt, 1));
+      CK(cudaMemset(lv.kcnt, 0, sizeof(int)));
+    } else {
+      std::vector<double> inv;
+      TRY(bordered_inverse(&K[l], nullptr, inv));
+      std::vector<int> boff{0}, bn{K[l].nrows};
+      std::vector<int64_t> koff{0};
+      TRY(upload(h, &lv.coarse.boff, boff));
+      TRY(upload(h, &lv.coarse.bn, bn));
+      TRY(upload(h, &lv.coarse.koff, koff));
+      TRY(upload(h, &lv.coarse.Kinv, inv));
+      lv.coarse.nblocks = 1;
+      lv.coarse.max_n = K[l].nrows;
+      lv.coarse.kinv_elems = (int64_t)inv.size();
+    }
+    char *x, *b, *r, *ta, *tb;
+    TRY(dalloc(h, &x, (size_t)lv.n * T));
+    TRY(dalloc(h, &b, (size_t)lv.n * T));
+    TRY(dalloc(h, &r, (size_t)lv.n * T));
+    TRY(dalloc(h, &ta, (size_t)lv.n * T));
+    TRY(dalloc(h, &tb, (size_t)lv.n * T));
+    lv.x = x; lv.b = b; lv.r = r; lv.ta = ta; lv.tb = tb;
+  }
+  return STOKES_OK;
+}
+
+static int setup_btp(stokes_handle* h, const stokes_problem* p, int dim) {
+  const stokes_btp* q = p->btp;
+  if (!q) return fail(STOKES_ERR_INVALID_ARG, "BTP needs stokes_problem.btp");
+  if (q->nlevels_a < 1 || !q->A || (q->nlevels_a > 1 && !q->PA) || !q->B)
+    return fail(STOKES_ERR_INVALID_ARG, "btp: A hierarchy or B missing");
+  const int64_t nu = p->field_off[dim], np = p->field_off[dim + 1] - nu;
+  if (q->A[0].nrows != nu) return fail(STOKES_ERR_INVALID_ARG, "btp: A[0] is not the velocity block of K0");
+  TRY(check_csr(q->B, "btp B"));
+  if (q->B->nrows != np || q->B->ncols != nu) return fail(STOKES_ERR_INVALID_ARG, "btp: B sizes");
+  TRY(setup_btp_levels(h, h->btpA, q->A, q->PA, q->nlevels_a, "btp A"));
+  HostCSR Bh;
+  Bh.nrows = (int)np;
+  Bh.ncols = (int)nu;
+  append_block(Bh, q->B, 0);
+  TRY(upload_csr(h, h->btpB, Bh));
+  if (q->Minv) {
+    TRY(check_csr(q->Minv, "btp Minv"));
+    if (q->Minv->nrows != np || q->Minv->ncols != np) return fail(STOKES_ERR_INVALID_ARG, "btp: Minv sizes");
+    HostCSR Mh;
+    Mh.nrows = Mh.ncols = (int)np;
+    append_block(Mh, q->Minv, 0);
+    TRY(upload_csr(h, h->btpMinv, Mh));
+  } else {
+    if (q->nlevels_m < 1 || !q->M || (q->nlevels_m > 1 && !q->PM))
+      return fail(STOKES_ERR_INVALID_ARG, "btp: give the M hierarchy or Minv");
+    if (q->M[0].nrows != np) return fail(STOKES_ERR_INVALID_ARG, "btp: M[0] size");
+    TRY(setup_btp_levels(h, h->btpM, q->M, q->PM, q->nlevels_m, "btp M"));
+  }
+  char* tp = nullptr;
+  TRY(dalloc(h, &tp, (size_t)3 * np * esz(h)));
+  h->btp_tp = tp;
+  return STOKES_OK;
+}
+
 static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int ninst, const stokes_params* prm) {
   const int dim = probs[0]->dim;
   h->dim = dim;
@@ -1117,6 +1328,14 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
   h->eta_u = prm->eta_u;
   h->eta_p = prm->eta_p;
   if (h->prec != STOKES_FP32 && h->prec != STOKES_FP64) return fail(STOKES_ERR_INVALID_ARG, "precision");
+  h->precond = prm->preconditioner;
+  h->btp_steps = prm->btp_steps;
+  if (h->precond != STOKES_PRECOND_DC && h->precond != STOKES_PRECOND_BTP)
+    return fail(STOKES_ERR_INVALID_ARG, "unknown preconditioner");
+  if (h->precond == STOKES_PRECOND_BTP) {
+    if (ninst != 1) return fail(STOKES_ERR_INVALID_ARG, "BTP handles hold one instance");
+    if (h->btp_steps < 1 || h->btp_steps > kKrMaxSteps) return fail(STOKES_ERR_INVALID_ARG, "btp_steps must be 1..4");
+  }
   if (prm->nu1 < 0 || prm->nu2 < 0 || prm->schedule < 0 || prm->schedule > 2)
     return fail(STOKES_ERR_INVALID_ARG, "schedule or sweep counts");
   if (h->disc != STOKES_TH && h->disc != STOKES_SV) return fail(STOKES_ERR_INVALID_ARG, "disc must be TH or SV");
@@ -1528,6 +1747,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
   for (int l = 0; l + 1 < L; ++l)
     if (h->lv[l].relax == STOKES_RELAX_VANKA_KRYLOV) TRY(setup_krylov_relax(h, h->lv[l], probs, ninst, l));
   if (h->disc == STOKES_SV) TRY(setup_sv(h, probs, ninst, dim));
+  if (h->precond == STOKES_PRECOND_BTP) TRY(setup_btp(h, probs[0], dim));
   if (h->prec == STOKES_FP32) TRY(dalloc(h, &h->x0_64, (size_t)h->lv[0].n));
   if (!h->d0buf) TRY(dalloc(h, &h->d0buf, (size_t)h->lv[0].n));
   // level-0 row kinds and Dirichlet mask
@@ -1641,7 +1861,7 @@ int stokes_factor_patches(stokes_handle* h, int64_t* nsingular) {
 
 int stokes_vcycle(stokes_handle* h, const double* r_dev, double* z_dev) {
   if (!h || !r_dev || !z_dev) return fail(STOKES_ERR_INVALID_ARG, "null argument");
-  if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
+  if (!h->factored && h->precond == STOKES_PRECOND_DC) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
   if ((const void*)r_dev == (void*)z_dev) return fail(STOKES_ERR_INVALID_ARG, "r and z alias");
   cudaGraphExec_t g;
   TRY(join_in(h));
@@ -1800,7 +2020,7 @@ extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x,
                                    int32_t maxit, stokes_solve_info* info) {
   if (!h || !b || !x || restart < 1 || restart > 1024 || maxit < 0 || !(rtol > 0))
     return fail(STOKES_ERR_INVALID_ARG, "fgmres arguments");
-  if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
+  if (!h->factored && h->precond == STOKES_PRECOND_DC) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
   const int m = restart;
   if (h->krylov_m != m) {
     h->krylov_m = 0;
@@ -2019,8 +2239,8 @@ static int level_op_impl(stokes_handle* h, int32_t op, int32_t l, const double* 
       TRY(in_cast(lv.n, x, lv.tb));
       TRY(in_cast(lv.n, b, lv.ta));
       const int sweeps = lv.krylov ? lv.kmax : 1;
-      if (f32) TRY(relax<float>(h, l, (float*)lv.tb, (const float*)lv.ta, sweeps, false));
-      else TRY(relax<double>(h, l, (double*)lv.tb, (const double*)lv.ta, sweeps, false));
+      if (f32) TRY(relax<float>(h, h->lv, l, (float*)lv.tb, (const float*)lv.ta, sweeps, false));
+      else TRY(relax<double>(h, h->lv, l, (double*)lv.tb, (const double*)lv.ta, sweeps, false));
       return out_cast(lv.n, lv.tb, y);
     }
     case STOKES_OP_COARSE: {

@@ -52,6 +52,42 @@ cudaError_t fill_zero(int64_t n, T* y, cudaStream_t st) {
 template cudaError_t fill_zero<float>(int64_t, float*, cudaStream_t);
 template cudaError_t fill_zero<double>(int64_t, double*, cudaStream_t);
 
+// z = d .* u (the Jacobi step inside a Krylov-wrapped relaxation)
+template <typename T>
+__global__ void k_diag_scale(int64_t n, const T* __restrict__ d, const T* __restrict__ u, T* __restrict__ z) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) z[j] = d[j] * u[j];
+}
+template <typename T>
+cudaError_t diag_scale(int64_t n, const T* d, const T* u, T* z, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_diag_scale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d, u, z);
+  return cudaGetLastError();
+}
+template cudaError_t diag_scale<float>(int64_t, const float*, const float*, float*, cudaStream_t);
+template cudaError_t diag_scale<double>(int64_t, const double*, const double*, double*, cudaStream_t);
+
+// BTP output in FP64: velocity rows take du (Dirichlet rows r), pressure
+// rows sp * dp.
+template <typename T>
+__global__ void k_btp_out(int64_t nu, int64_t np, const T* __restrict__ du, const T* __restrict__ dp, double sp,
+                          const uint8_t* __restrict__ dir, const double* __restrict__ r64, double* __restrict__ z) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nu) z[j] = dir[j] ? r64[j] : (double)du[j];
+  else if (j < nu + np) z[j] = sp * (double)dp[j - nu];
+}
+template <typename T>
+cudaError_t btp_out(int64_t nu, int64_t np, const T* du, const T* dp, double sp, const uint8_t* dir,
+                    const double* r64, double* z, cudaStream_t st) {
+  if (nu + np == 0) return cudaSuccess;
+  k_btp_out<<<(unsigned)((nu + np + 255) / 256), 256, 0, st>>>(nu, np, du, dp, sp, dir, r64, z);
+  return cudaGetLastError();
+}
+template cudaError_t btp_out<float>(int64_t, int64_t, const float*, const float*, double, const uint8_t*,
+                                    const double*, double*, cudaStream_t);
+template cudaError_t btp_out<double>(int64_t, int64_t, const double*, const double*, double, const uint8_t*,
+                                     const double*, double*, cudaStream_t);
+
 template <typename T>
 __global__ void k_finalize(int64_t n, const T* __restrict__ x, const uint8_t* __restrict__ dir,
                            const double* __restrict__ r64, double* __restrict__ out) {

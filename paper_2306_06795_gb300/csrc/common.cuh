@@ -146,6 +146,12 @@ template <typename T, typename TI>
 cudaError_t axpy_into(int64_t n, double a, const TI* xin, T* y, cudaStream_t st);   // y += a x
 template <typename T>
 cudaError_t fill_zero(int64_t n, T* y, cudaStream_t st);
+template <typename T>
+cudaError_t diag_scale(int64_t n, const T* d, const T* u, T* z, cudaStream_t st);  // z = d .* u
+// z[j] = dir[j] ? r64[j] : du[j] (j < nu); z[nu + i] = sp * dp[i] (i < np)
+template <typename T>
+cudaError_t btp_out(int64_t nu, int64_t np, const T* du, const T* dp, double sp, const uint8_t* dir,
+                    const double* r64, double* z, cudaStream_t st);
 // out_j = dir_j ? r64_j : double(x_j)
 template <typename T>
 cudaError_t finalize_out(int64_t n, const T* x, const uint8_t* dir, const double* r64, double* out, cudaStream_t st);
