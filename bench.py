@@ -187,6 +187,12 @@ def run_gpu(args):
         return info[0]
 
     with torch.cuda.stream(stream):
+        # setup-time tuning of the Vanka bins (tiles, ring depth), not timed
+        tune = {}
+        for prec, hh in handles.items():
+            sd.stokes_factor_patches(hh)
+            sd.stokes_autotune(hh, 5)
+            tune[prec] = json.loads(sd.stokes_autotune_report(hh))
         for _ in range(max(args.warmup, 3)):
             info32 = step(h, x)
         torch.cuda.synchronize()
@@ -376,6 +382,7 @@ def run_gpu(args):
                 "dc_solve_time_over_btp": (ms - fct[sd.STOKES_FP32]) / msb if msb > 0 else None},
         "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(16 * n),
                 "d2h_bytes_per_step": int(8 * n), "true_relres": e2e_res},
+        "autotune_fp32": tune[sd.STOKES_FP32]["bins"],
         "gpu_launches": int(launches),
         "clocks": clk,
     }

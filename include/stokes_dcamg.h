@@ -207,6 +207,18 @@ int stokes_fgmres_solve_host(stokes_handle* h, const double* b_host, double* x_h
                              double rtol, int32_t restart, int32_t maxit,
                              stokes_solve_info* info);
 
+/* Autotuner of the Vanka apply (the paper has no counterpart: a tiling
+ * choice of this implementation).  For every level and patch bin, times the
+ * bulk-copy apply for patches per tile in {t/2, t, 2t} around the setup's
+ * choice t and a 2- or 3-stage shared-memory ring, `reps` launches each
+ * (CUDA events on the handle's stream), and keeps the fastest.  Results do
+ * not change (the per-patch arithmetic is independent of the tiling);
+ * CUDA graphs captured before are dropped and recaptured on next use.
+ * Requires stokes_factor_patches.  stokes_autotune_report returns the
+ * choices as JSON, owned by the handle. */
+int stokes_autotune(stokes_handle* h, int32_t reps);
+const char* stokes_autotune_report(const stokes_handle* h);
+
 /* Single steps of the cycle on one level, for testing and measurement.
  * All vectors are device FP64 of the sizes stated; the operation runs in
  * the cycle precision unless its name says FP64.

@@ -35,7 +35,8 @@ STOKES_KERNEL_VANKA_APPLY, STOKES_KERNEL_SCATTER, STOKES_KERNEL_SPMV, STOKES_KER
 EXPORTS = ["stokes_setup", "stokes_factor_patches", "stokes_vcycle", "stokes_fgmres_solve",
            "stokes_fgmres_solve_host", "stokes_level_op", "stokes_num_levels", "stokes_level_size",
            "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_time_kernel",
-           "stokes_kernel_launches", "stokes_vanka_noalloc", "stokes_destroy",
+           "stokes_kernel_launches", "stokes_vanka_noalloc", "stokes_destroy", "stokes_autotune",
+           "stokes_autotune_report",
            "stokes_status_string", "stokes_last_error"]
 
 
@@ -107,6 +108,10 @@ def _load():
     lib.stokes_kernel_launches.restype = C.c_int64
     lib.stokes_vanka_noalloc.argtypes = [vp, C.c_int32, vp, vp]
     lib.stokes_destroy.argtypes = [vp]
+    lib.stokes_autotune.argtypes = [vp, C.c_int32]
+    lib.stokes_autotune.restype = C.c_int
+    lib.stokes_autotune_report.argtypes = [vp]
+    lib.stokes_autotune_report.restype = C.c_char_p
     lib.stokes_destroy.restype = None
     lib.stokes_status_string.argtypes = [C.c_int]
     lib.stokes_status_string.restype = C.c_char_p
@@ -313,6 +318,14 @@ def stokes_fgmres_solve_host(h, b, x, rtol=1e-8, restart=30, maxit=1000):
                                              restart, maxit, info),
                 "stokes_fgmres_solve_host", allow_not_converged=True)
     return rc, [(i.iters, i.status, i.true_relres) for i in info]
+
+
+def stokes_autotune(h, reps=5):
+    _check(lib.stokes_autotune(h.ptr, reps), "stokes_autotune")
+
+
+def stokes_autotune_report(h):
+    return lib.stokes_autotune_report(h.ptr).decode()
 
 
 def stokes_level_op(h, op, level, x, b, y):

@@ -85,6 +85,8 @@ struct Level {
   std::vector<int64_t> seg_off;  // per instance, -1 when absent
   bool dlsc = false;
   DLSCData dl;
+  std::vector<int64_t> hfoff;  // host copies of the patch factor offsets and list pointers
+  std::vector<int> hpptr;      // (bin re-tiling by the autotuner)
   // Krylov-wrapped relaxation (Sec. 3.3.1); jacobi: its inner
   // preconditioner is diag(K)^-1 instead of a Vanka sweep (BTP's SA cycles)
   bool krylov = false;
@@ -111,6 +113,7 @@ struct stokes_handle {
   int ninst = 0, dim = 2, disc = STOKES_TH, prec = STOKES_FP32, L = 0;
   // preconditioner: the DC cycle, or the block-triangular BTP (Sec. 4)
   int precond = STOKES_PRECOND_DC;
+  std::string tune_report = "{}";  // autotuner choices (JSON)
   int btp_steps = 2;
   std::vector<Level> btpA, btpM;  // SA hierarchies of A and of M_p / nu (TH)
   DevCSR btpB, btpMinv;           // B (pressure rows x velocity columns); SV exact mass inverse
@@ -1025,6 +1028,88 @@ void stokes_destroy(stokes_handle* h) {
   delete h;
 }
 
+static bool configure_bin(const DevPatches& dp, TmaBin& bn, int b, int tp, int stages,
+                          const std::vector<int64_t>& foff, const std::vector<int>& pptr, size_t T, int nsm);
+
+// Autotuner of the bulk-copy Vanka bins: for every level and bin, time the
+// bin's apply for patches-per-tile in {tp/2, tp, 2 tp} and a 2- or 3-stage
+// ring (CUDA events, after one warm-up launch) and keep the fastest.  The
+// per-patch arithmetic does not depend on the tiling, so results are
+// unchanged; captured graphs are dropped because they hold the old launch
+// configurations.
+int stokes_autotune(stokes_handle* h, int32_t reps) {
+  if (!h) return fail(STOKES_ERR_INVALID_ARG, "null handle");
+  if (!h->factored) return fail(STOKES_ERR_STATE, "stokes_factor_patches must run first");
+  if (reps < 1) reps = 5;
+  TRY(join_in(h));
+  int nsm = 0, dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const size_t T = esz(h);
+  const bool f32 = h->prec == STOKES_FP32;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::string rep = "{\"bins\": [";
+  bool first = true;
+  int rc = STOKES_OK;
+  for (int l = 0; l < h->L && rc == STOKES_OK; ++l) {
+    Level& lv = h->lv[l];
+    if (!lv.has_patches || !lv.pat.use_tma) continue;
+    DevPatches& dp = lv.pat;
+    CK(cudaMemsetAsync(lv.r, 0, (size_t)lv.n * T, h->st));
+    for (int b = 0; b < kTmaBins; ++b) {
+      TmaBin& bn = dp.bins[b];
+      if (bn.count == 0) continue;
+      const TmaBin base = bn;
+      const int ppw = vanka_tma_bin_ppw(b);
+      TmaBin best = base;
+      float best_ms = -1.f;
+      for (int tp : {base.tp / 2, base.tp, base.tp * 2}) {
+        if (tp < 4 * ppw || tp > 128) continue;
+        for (int stages : {2, 3}) {
+          TmaBin cand = base;
+          if (!configure_bin(dp, cand, b, tp, stages, lv.hfoff, lv.hpptr, T, nsm)) continue;
+          bn = cand;
+          CK(vanka_apply_bin(dp, b, lv.r, lv.yp, f32, h->st));
+          CK(cudaEventRecord(e0, h->st));
+          for (int q = 0; q < reps; ++q) CK(vanka_apply_bin(dp, b, lv.r, lv.yp, f32, h->st));
+          CK(cudaEventRecord(e1, h->st));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          ms /= reps;
+          if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = cand;
+          }
+        }
+      }
+      bn = best;
+      char buf[256];
+      snprintf(buf, sizeof buf,
+               "%s{\"level\": %d, \"bin\": %d, \"patches\": %d, \"tile_patches\": %d, \"stages\": %d, "
+               "\"grid\": %d, \"us\": %.2f}",
+               first ? "" : ", ", l, b, bn.count, bn.tp, bn.stages, bn.grid, best_ms * 1000.f);
+      rep += buf;
+      first = false;
+    }
+  }
+  rep += "]}";
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TRY(check_pipeline_errors(h));
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  for (auto& kv : h->iter_graphs) cudaGraphExecDestroy(kv.second);
+  h->iter_graphs.clear();
+  h->tune_report = rep;
+  TRY(join_out(h));
+  return rc;
+}
+
+const char* stokes_autotune_report(const stokes_handle* h) { return h ? h->tune_report.c_str() : "{}"; }
+
 int stokes_num_levels(const stokes_handle* h) { return h ? h->L : 0; }
 int64_t stokes_kernel_launches(const stokes_handle* h) { return h ? h->launches : 0; }
 int64_t stokes_level_size(const stokes_handle* h, int32_t l) {
@@ -1174,6 +1259,36 @@ static int setup_krylov_relax(stokes_handle* h, Level& lv, const stokes_problem*
   TRY(dalloc(h, &lv.kcnt, (size_t)ninst));
   CK(cudaMemset(lv.kcnt, 0, sizeof(int) * ninst));
   return STOKES_OK;
+}
+
+// Tile configuration of a bulk-copy bin for `tp` patches per tile: the
+// largest tile's factor, index-list and right-hand-side sizes, the ring
+// depth and the persistent grid (CTAs per SM from the occupancy query).
+// Returns false when no CTA fits on an SM.
+static bool configure_bin(const DevPatches& dp, TmaBin& bn, int b, int tp, int stages,
+                          const std::vector<int64_t>& foff, const std::vector<int>& pptr, size_t T, int nsm) {
+  bn.tp = tp;
+  bn.ntiles = (bn.count + tp - 1) / tp;
+  int64_t fb = 0, db = 0, rh = 0;
+  for (int t = 0; t < bn.ntiles; ++t) {
+    const int i0 = bn.start + t * tp, i1 = std::min(i0 + tp, bn.start + bn.count);
+    fb = std::max(fb, (foff[i1] - foff[i0]) * (int64_t)T);
+    db = std::max<int64_t>(db, (int64_t)(((pptr[i1] + 3) & ~3) - (pptr[i0] & ~3)) * 4);
+    const int cnt = i1 - i0, per = (cnt + 3) / 4;
+    for (int w = 0; w < 4; ++w) {
+      const int j0 = std::min(i0 + w * per, i1), j1 = std::min(j0 + per, i1);
+      rh = std::max<int64_t>(rh, pptr[j1] - pptr[j0]);
+    }
+  }
+  bn.fac_bytes = (int)fb;
+  bn.dof_bytes = (int)db;
+  bn.rhs_elems = (int)((rh + 3) / 4 * 4);
+  bn.stages = stages;
+  if (vanka_tma_smem(dp, bn, T) > 220 * 1024) return false;
+  const int nb = vanka_tma_blocks_per_sm(dp, bn, b, T);
+  if (nb < 1) return false;
+  bn.grid = std::min(bn.ntiles, nsm * nb);
+  return true;
 }
 
 // BTP (Sec. 4): the SA hierarchies of A and of M_p / nu (or the exact
@@ -1628,23 +1743,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
         bn.max_np = std::max(bn.max_np, pnp[si]);
       }
       const int ppw = vanka_tma_bin_ppw(b);  // patches per warp at a time
-      const int tp = (int)std::max<int64_t>(4 * ppw, std::min<int64_t>(64, 8192 / std::max<int64_t>(maxblk, 1)));
-      bn.tp = tp;
-      bn.ntiles = (bn.count + tp - 1) / tp;
-      int64_t fb = 0, db = 0, rh = 0;
-      for (int t = 0; t < bn.ntiles; ++t) {
-        const int i0 = bn.start + t * tp, i1 = std::min(i0 + tp, bn.start + bn.count);
-        fb = std::max(fb, (foff[i1] - foff[i0]) * (int64_t)T);
-        db = std::max<int64_t>(db, (int64_t)(((pptr[i1] + 3) & ~3) - (pptr[i0] & ~3)) * 4);
-        const int cnt = i1 - i0, per = (cnt + 3) / 4;
-        for (int w = 0; w < 4; ++w) {
-          const int j0 = std::min(i0 + w * per, i1), j1 = std::min(j0 + per, i1);
-          rh = std::max<int64_t>(rh, pptr[j1] - pptr[j0]);
-        }
-      }
-      bn.fac_bytes = (int)fb;
-      bn.dof_bytes = (int)db;
-      bn.rhs_elems = (int)((rh + 3) / 4 * 4);
+      bn.tp = (int)std::max<int64_t>(4 * ppw, std::min<int64_t>(64, 8192 / std::max<int64_t>(maxblk, 1)));
     }
     std::vector<int> pdof_pad(pdof);
     pdof_pad.resize(pdof.size() + 8, 0);  // bulk copies may read up to 16 bytes past the last list
@@ -1674,18 +1773,16 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       for (int b = 0; b < kTmaBins; ++b) {
         TmaBin& bn = dp.bins[b];
         if (bn.count == 0) continue;
-        if (vanka_tma_smem(dp, bn, T) > 220 * 1024)
-          return fail(STOKES_ERR_INVALID_ARG, "patch tiles exceed shared memory");
         // a 2-stage ring when it keeps clearly more CTAs (consumer warps) per SM
-        bn.stages = 3;
-        int nb = vanka_tma_blocks_per_sm(dp, bn, b, T);
-        bn.stages = 2;
-        const int nb2 = vanka_tma_blocks_per_sm(dp, bn, b, T);
-        if (nb2 * 2 >= nb * 3) nb = nb2;
-        else bn.stages = 3;
-        if (nb < 1) return fail(STOKES_ERR_INVALID_ARG, "patch tiles do not fit on an SM");
-        bn.grid = std::min(bn.ntiles, nsm * nb);
+        const int tp = bn.tp;
+        if (!configure_bin(dp, bn, b, tp, 3, foff, pptr, T, nsm))
+          return fail(STOKES_ERR_INVALID_ARG, "patch tiles do not fit on an SM");
+        const int nb3 = bn.grid;
+        TmaBin b2 = bn;
+        if (configure_bin(dp, b2, b, tp, 2, foff, pptr, T, nsm) && b2.grid * 2 >= nb3 * 3) bn = b2;
       }
+      lv.hfoff = foff;
+      lv.hpptr = pptr;
       dp.use_tma = nsmall > 0;
     }
     // factorisation order: blocks that fit in shared memory, then the rest

@@ -235,7 +235,7 @@ constexpr int kMaxAxpyCols = 1024;  // Krylov columns (restart length) one multi
 // 5 NK), and the warps' sums are added in warp order.  Fixed order:
 // deterministic.
 template <int NK>
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const int64_t* __restrict__ cbeg,
+__global__ void __launch_bounds__(kRedThreads, 4) k_multidot(const int64_t* __restrict__ cbeg,
     const int64_t* __restrict__ cend, int ncols, const double* __restrict__ V, int64_t ldv,
     const double* __restrict__ w, double* __restrict__ partial, int ldp) {
   __shared__ double red[kRedThreads / 32][NK];
@@ -337,7 +337,7 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
 // grid: nchunks.  w[row] += sign * sum_k coef[seg*ldh + k] * V_k[row]:
 // two rows per thread per step, the columns' loads issued eight at a time
 // for both rows (sixteen in flight); one DFMA per loaded element.
-__global__ void __launch_bounds__(kRedThreads) k_multiaxpy(const int64_t* __restrict__ cbeg,
+__global__ void __launch_bounds__(kRedThreads, 4) k_multiaxpy(const int64_t* __restrict__ cbeg,
     const int64_t* __restrict__ cend, const int* __restrict__ cseg, int ncols, const double* __restrict__ V,
     int64_t ldv, const double* __restrict__ coef, int ldh, double sign, double* __restrict__ w) {
   __shared__ double cf[kMaxAxpyCols];

@@ -120,6 +120,8 @@ cudaError_t vanka_prepare_kernels();
 int vanka_tma_blocks_per_sm(const DevPatches& p, const TmaBin& bn, int b, size_t elem);
 int vanka_tma_bin_of(int m);
 int vanka_tma_bin_ppw(int b);
+// one bulk-copy bin of the apply (timing by the autotuner)
+cudaError_t vanka_apply_bin(const DevPatches& p, int b, const void* r, void* yp, bool fp32, cudaStream_t st);
 
 template <typename T>
 cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st);

@@ -64,10 +64,10 @@ static cudaError_t launch_mode(const DevCSR& A, const TA* val, const TX* x, cons
 // row per lane, so at step k the warp reads 32 consecutive values and
 // columns (one coalesced line each, streamed past L2) and gathers x through
 // the read-only path.  Padding entries carry column -1 and are skipped, so
-// no row lengths are read.  The loop is software-pipelined: the values and
-// columns of the next U steps (8 for FP32 values, 4 for FP64) are in flight
-// while the x entries of the current U are gathered.  Each row sums its
-// entries in CSR order.
+// no row lengths are read.  U steps (8 for FP32 values, 4 for FP64) have
+// their values and columns in flight together, then their x gathers; this
+// beat a software-pipelined variant and two rows per lane on the C2 level
+// operators.  Each row sums its entries in CSR order.
 constexpr int kSellWarps = 8;
 
 template <typename TA, typename TX, typename TB, typename TY, typename TACC, int MODE>
@@ -84,22 +84,15 @@ __global__ void __launch_bounds__(32 * kSellWarps) k_spmv_sell(int nrows, int nc
   const TA* vp = sval + o0 + lane;
   const int* cp = scol + o0 + lane;
   constexpr int U = sizeof(TA) == 4 ? 8 : 4;
-  TA v[U];
-  int cc[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    v[u] = u < w ? __ldcs(vp + u * 32) : TA(0);
-    cc[u] = u < w ? __ldcs(cp + u * 32) : -1;
-  }
   TACC sum = TACC(0);
   for (int k = 0; k < w; k += U) {
-    TA vn[U];
-    int cn[U];
+    TA v[U];
+    int cc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int kk = k + U + u;
-      vn[u] = kk < w ? __ldcs(vp + (int64_t)kk * 32) : TA(0);
-      cn[u] = kk < w ? __ldcs(cp + (int64_t)kk * 32) : -1;
+      const int kk = k + u;
+      v[u] = kk < w ? __ldcs(vp + (int64_t)kk * 32) : TA(0);
+      cc[u] = kk < w ? __ldcs(cp + (int64_t)kk * 32) : -1;
     }
     TX xv[U];
 #pragma unroll
@@ -107,11 +100,6 @@ __global__ void __launch_bounds__(32 * kSellWarps) k_spmv_sell(int nrows, int nc
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (cc[u] >= 0) sum += TACC(v[u]) * TACC(xv[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      v[u] = vn[u];
-      cc[u] = cn[u];
-    }
   }
   if (row >= nrows) return;
   if (MODE == SPMV_SET) {

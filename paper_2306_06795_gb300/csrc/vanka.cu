@@ -773,6 +773,21 @@ static cudaError_t launch_bin_np(const DevPatches& p, int b, const TR* r, T* yp,
 }
 
 template <typename T, typename TR>
+static cudaError_t apply_tma_bin(const DevPatches& p, int b, const TR* r, T* yp, cudaStream_t st) {
+  const TmaBin& bn = p.bins[b];
+  if (bn.count == 0) return cudaSuccess;
+  const bool one = bn.max_np <= 1;
+  if (p.dim == 2) return one ? launch_bin_np<T, TR, 2, 1>(p, b, r, yp, st) : launch_bin_np<T, TR, 2, 4>(p, b, r, yp, st);
+  return one ? launch_bin_np<T, TR, 3, 1>(p, b, r, yp, st) : launch_bin_np<T, TR, 3, 4>(p, b, r, yp, st);
+}
+
+cudaError_t vanka_apply_bin(const DevPatches& p, int b, const void* r, void* yp, bool fp32, cudaStream_t st) {
+  if (b < 0 || b >= kTmaBins) return cudaErrorInvalidValue;
+  if (fp32) return apply_tma_bin<float, float>(p, b, (const float*)r, (float*)yp, st);
+  return apply_tma_bin<double, double>(p, b, (const double*)r, (double*)yp, st);
+}
+
+template <typename T, typename TR>
 static cudaError_t apply_tma_bins(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
   for (int b = 0; b < kTmaBins; ++b) {
     const TmaBin& bn = p.bins[b];
