@@ -114,8 +114,6 @@ struct stokes_handle {
   // preconditioner: the DC cycle, or the block-triangular BTP (Sec. 4)
   int precond = STOKES_PRECOND_DC;
   std::string tune_report = "{}";  // autotuner choices (JSON)
-  int tail_l0 = -1;                 // first level of the single-CTA coarse tail (-1: none)
-  TailLevel* tail_dev = nullptr;
   int btp_steps = 2;
   std::vector<Level> btpA, btpM;  // SA hierarchies of A and of M_p / nu (TH)
   DevCSR btpB, btpMinv;           // B (pressure rows x velocity columns); SV exact mass inverse
@@ -788,30 +786,12 @@ int relax(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b, in
 // zero initial guess: input lvs[l].b, output lvs[l].x.  Instances whose
 // coarsest level is l take the exact (bordered) solve on their segment.
 template <typename T>
-int vcycle(stokes_handle* h, std::vector<Level>& lvs, int l, bool no_tail = false);
-
-// The single-CTA coarse tail from level l (tail.cu); the ledger counts the
-// level-by-level path's bytes and one launch.
-template <typename T>
-int tail(stokes_handle* h, int l) {
-  if (h->led.count) {
-    const int before = h->led.launches;
-    TRY(vcycle<T>(h, h->lv, l, true));
-    h->led.launches = before + 1;
-    return STOKES_OK;
-  }
-  CK(tail_cycle<T>(h->tail_dev, h->L - l, h->nu1, h->nu2, h->st));
-  return STOKES_OK;
-}
-
-template <typename T>
-int vcycle(stokes_handle* h, std::vector<Level>& lvs, int l, bool no_tail) {
+int vcycle(stokes_handle* h, std::vector<Level>& lvs, int l) {
   Level& L = lvs[l];
   T* x = reinterpret_cast<T*>(L.x);
   T* b = reinterpret_cast<T*>(L.b);
   if (l == (int)lvs.size() - 1) return L_coarse<T>(h, L, b, x);
   const bool main = &lvs == &h->lv;
-  if (main && !no_tail && l == h->tail_l0) return tail<T>(h, l);
   const bool relax_here = (L.has_patches || L.dlsc || L.jacobi) && !(main && h->schedule == STOKES_DC_SKIP1 && l == 1);
   const int nu1 = main ? h->nu1 : h->btp_steps, nu2 = main ? h->nu2 : h->btp_steps;
   if (relax_here) TRY(relax<T>(h, lvs, l, x, b, nu1, true));
@@ -821,7 +801,7 @@ int vcycle(stokes_handle* h, std::vector<Level>& lvs, int l, bool no_tail) {
   Level& C = lvs[l + 1];
   TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
   TRY((L_spmv<T, T, T, T, T>(h, L.R, kval<T>(L.R), r, (const T*)nullptr, reinterpret_cast<T*>(C.b), SPMV_SET)));
-  TRY(vcycle<T>(h, lvs, l + 1, no_tail));
+  TRY(vcycle<T>(h, lvs, l + 1));
   TRY((L_spmv<T, T, T, T, T>(h, L.P, kval<T>(L.P), reinterpret_cast<const T*>(C.x), (const T*)nullptr, x, SPMV_ADD)));
   if (relax_here) TRY(relax<T>(h, lvs, l, x, b, nu2, false));
   return STOKES_OK;
@@ -1452,68 +1432,6 @@ static int setup_btp(stokes_handle* h, const stokes_problem* p, int dim) {
   return STOKES_OK;
 }
 
-// The coarse tail: the first level l0 >= 2 from which every level is tiny
-// (at most 4096 rows), relaxes with stationary Vanka (or not at all) and has
-// patches of at most 128 velocity DoFs per component and 4 seeds.
-static int setup_tail(stokes_handle* h) {
-  int l0 = -1;
-  for (int l = h->L - 1; l >= 2; --l) {
-    const Level& L = h->lv[l];
-    const bool ok = L.n <= 4096 && !L.dlsc && !L.krylov &&
-                    (!L.has_patches || (L.pat.max_m <= 128 && L.pat.max_np <= 4));
-    if (!ok) break;
-    l0 = l;
-  }
-  if (l0 < 0 || l0 == h->L - 1) return STOKES_OK;  // nothing to fuse beyond the coarsest solve
-  std::vector<TailLevel> tv;
-  const bool f32 = h->prec == STOKES_FP32;
-  auto csr = [&](const DevCSR& A) {
-    TailCSR t;
-    t.rowptr = A.rowptr;
-    t.col = A.col;
-    t.val = f32 ? (const void*)A.v32 : (const void*)A.v64;
-    t.nrows = A.nrows;
-    return t;
-  };
-  for (int l = l0; l < h->L; ++l) {
-    const Level& L = h->lv[l];
-    TailLevel t{};
-    t.n = (int)L.n;
-    t.dim = h->dim;
-    t.K = csr(L.K);
-    if (l + 1 < h->L) {
-      t.R = csr(L.R);
-      t.P = csr(L.P);
-    }
-    if (L.has_patches) {
-      t.npatch = L.pat.npatch;
-      t.shared = L.pat.shared;
-      t.ptr = L.pat.ptr;
-      t.dof = L.pat.dof;
-      t.nvel = L.pat.nvel;
-      t.npres = L.pat.npres;
-      t.foff = L.pat.foff;
-      t.fac = L.pat.fac;
-      t.tptr = L.pat.tptr;
-      t.pdst = L.pat.pdst;
-    }
-    t.omega = L.omega;
-    t.nblocks = L.coarse.nblocks;
-    t.boff = L.coarse.boff;
-    t.bn = L.coarse.bn;
-    t.koff = L.coarse.koff;
-    t.Kinv = L.coarse.Kinv;
-    t.x = L.x;
-    t.b = L.b;
-    t.r = L.r;
-    t.yp = L.yp;
-    tv.push_back(t);
-  }
-  TRY(upload(h, &h->tail_dev, tv));
-  h->tail_l0 = l0;
-  return STOKES_OK;
-}
-
 static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int ninst, const stokes_params* prm) {
   const int dim = probs[0]->dim;
   h->dim = dim;
@@ -1927,7 +1845,6 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     if (h->lv[l].relax == STOKES_RELAX_VANKA_KRYLOV) TRY(setup_krylov_relax(h, h->lv[l], probs, ninst, l));
   if (h->disc == STOKES_SV) TRY(setup_sv(h, probs, ninst, dim));
   if (h->precond == STOKES_PRECOND_BTP) TRY(setup_btp(h, probs[0], dim));
-  TRY(setup_tail(h));
   if (h->prec == STOKES_FP32) TRY(dalloc(h, &h->x0_64, (size_t)h->lv[0].n));
   if (!h->d0buf) TRY(dalloc(h, &h->d0buf, (size_t)h->lv[0].n));
   // level-0 row kinds and Dirichlet mask

@@ -194,35 +194,6 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
 cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
                       const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
                       cudaStream_t st);
-// A level of the single-CTA coarse tail (tail.cu): device pointers only.
-struct TailCSR {
-  const int* rowptr;
-  const int* col;
-  const void* val;  // values in the cycle precision
-  int nrows;
-};
-struct TailLevel {
-  int n, dim, shared, npatch;
-  TailCSR K, R, P;
-  const int* ptr;
-  const int* dof;
-  const int* nvel;
-  const int* npres;
-  const int64_t* foff;
-  const void* fac;
-  const int* tptr;
-  const int* pdst;
-  double omega;
-  int nblocks;
-  const int* boff;
-  const int* bn;
-  const int64_t* koff;
-  const double* Kinv;
-  void *x, *b, *r, *yp;
-};
-template <typename T>
-cudaError_t tail_cycle(const TailLevel* lv, int nl, int nu1, int nu2, cudaStream_t st);
-
 // Krylov-wrapped relaxation (krylov.cu).  Rows of a level cut into chunks
 // that never straddle an instance; sbeg/send: chunk range of each instance.
 constexpr int kKrMaxSteps = 4;  // inner FGMRES steps per relaxation call
