@@ -206,10 +206,6 @@ int choose_tpr(int64_t nnz, int nrows) {
   return 32;
 }
 
-// Operators with at least this many rows and no sliced copy use the
-// bulk-copy SpMV.
-constexpr int kTmaRows = 1 << 30;
-constexpr int kTileNnz = 1024, kTileRows = 256;
 // Largest stored/nonzero ratio of a sliced-ELLPACK copy, and the fewest rows
 // for one (smaller operators keep enough warps busy with vector CSR).
 constexpr double kSellMaxPad = 1.25;
@@ -222,13 +218,9 @@ int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
   d.nrows = c.nrows;
   d.ncols = c.ncols;
   d.nnz = (int64_t)c.col.size();
-  // arrays padded so that 16-byte-widened tile copies stay inside them
   std::vector<int> rp(c.rowptr);
-  rp.resize(rp.size() + 8, rp.back());
   std::vector<int> cl(c.col);
-  cl.resize(cl.size() + 8, 0);
   std::vector<double> v(c.val);
-  v.resize(v.size() + 8, 0.0);
   TRY(upload(h, &d.rowptr, rp));
   TRY(upload(h, &d.col, cl));
   TRY(upload(h, &d.v64, v));
@@ -283,39 +275,6 @@ int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
       d.schunks = nch;
       return STOKES_OK;
     }
-  }
-  // tiles for the bulk-copy SpMV
-  if (c.nrows >= kTmaRows && maxrow <= kTileNnz - 8) {
-    std::vector<int> trow{0};
-    int vb = 0, vb32 = 0, cb = 0, pb = 0;
-    int r = 0;
-    while (r < c.nrows) {
-      int r1 = r;
-      while (r1 < c.nrows && r1 - r < kTileRows && c.rowptr[r1 + 1] - c.rowptr[r] <= kTileNnz - 8) ++r1;
-      trow.push_back(r1);
-      const int n0 = c.rowptr[r], n1 = c.rowptr[r1];
-      vb = std::max(vb, ((n1 + 1) / 2 * 2 - n0 / 2 * 2) * 8);
-      vb32 = std::max(vb32, ((n1 + 3) / 4 * 4 - n0 / 4 * 4) * 4);
-      cb = std::max(cb, ((n1 + 3) / 4 * 4 - n0 / 4 * 4) * 4);
-      pb = std::max(pb, ((r1 + 1 + 3) / 4 * 4 - r / 4 * 4) * 4);
-      r = r1;
-    }
-    d.ntiles = (int)trow.size() - 1;
-    d.tile_val_bytes = vb;
-    d.tile_val_bytes32 = vb32;
-    d.tile_col_bytes = cb;
-    d.tile_rp_bytes = pb;
-    TRY(upload(h, &d.trow, trow));
-    TRY(dalloc(h, &d.err, 1));
-    CK(cudaMemset(d.err, 0, sizeof(int)));
-    h->err_flags.push_back(d.err);
-    int nsm = 0, dev = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int b32 = spmv_tma_blocks_per_sm(d, false), b64 = spmv_tma_blocks_per_sm(d, true);
-    if (b32 < 1 || b64 < 1) return fail(STOKES_ERR_INVALID_ARG, "SpMV tiles do not fit on an SM");
-    d.tma_grid32 = std::min(d.ntiles, nsm * b32);
-    d.tma_grid64 = std::min(d.ntiles, nsm * b64);
   }
   return STOKES_OK;
 }
@@ -1921,7 +1880,6 @@ int stokes_setup(const stokes_problem* const* probs, int32_t ninstances, const s
     }
   }
   e = vanka_prepare_kernels();
-  if (e == cudaSuccess) e = spmv_prepare_kernels();
   if (e != cudaSuccess) {
     stokes_destroy(h);
     return fail(STOKES_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));

@@ -19,14 +19,6 @@ struct DevCSR {
   double* v64 = nullptr;
   float* v32 = nullptr;
   int tpr = 4;  // threads per row of the vector-CSR SpMV
-  // bulk-copy tiles (large operators only; ntiles == 0 otherwise)
-  int ntiles = 0;
-  int* trow = nullptr;          // [ntiles+1] first row of each tile
-  int tile_val_bytes = 0;       // FP64 values per stage (16-byte widened)
-  int tile_val_bytes32 = 0;     // FP32 values per stage
-  int tile_col_bytes = 0, tile_rp_bytes = 0;
-  int tma_grid32 = 0, tma_grid64 = 0;
-  int* err = nullptr;
   // row-block tiles of the stream SpMV: {first row, first entry, end row,
   // end entry}, at most kStreamRows rows and kStreamNnz entries each
   int stiles = 0;
@@ -39,12 +31,6 @@ struct DevCSR {
   double* sv64 = nullptr;
   float* sv32 = nullptr;
 };
-
-template <typename TA, typename TX, typename TB, typename TY, typename TACC>
-cudaError_t spmv_tma(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y, int mode, double s0, double s1,
-                     const uint8_t* kind, cudaStream_t st);
-cudaError_t spmv_prepare_kernels();
-int spmv_tma_blocks_per_sm(const DevCSR& A, bool fp64);
 
 // SpMV modes
 enum { SPMV_SET = 0, SPMV_RES = 1, SPMV_ADD = 2, SPMV_SCALED_RES = 3 };

@@ -231,7 +231,6 @@ cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y
   // the sliced copy holds the same values as A.v32 / A.v64
   if (A.schunks > 0 && sell_values<TA>(A) && (const void*)val == (const void*)(sizeof(TA) == 4 ? (const void*)A.v32 : (const void*)A.v64))
     return spmv_sell<TA, TX, TB, TY, TACC>(A, sell_values<TA>(A), x, b, y, mode, s0, s1, kind, st);
-  if (A.ntiles > 0) return spmv_tma<TA, TX, TB, TY, TACC>(A, val, x, b, y, mode, s0, s1, kind, st);
   switch (A.tpr) {
     case 2: return launch_mode<TA, TX, TB, TY, TACC, 2>(A, val, x, b, y, mode, s0, s1, kind, st);
     case 4: return launch_mode<TA, TX, TB, TY, TACC, 4>(A, val, x, b, y, mode, s0, s1, kind, st);
