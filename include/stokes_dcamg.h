@@ -219,6 +219,17 @@ int stokes_fgmres_solve_host(stokes_handle* h, const double* b_host, double* x_h
 int stokes_autotune(stokes_handle* h, int32_t reps);
 const char* stokes_autotune_report(const stokes_handle* h);
 
+/* Device-side Galerkin product of the AMG setup (Alg. 1): C = P^T K P in
+ * FP64 on the GPU (a setup step; the solve path does not call it).  K
+ * (n x n) and P (n x nc) are host CSRs as in stokes_setup; C receives
+ * nc x nc host arrays with sorted columns, allocated by the library and
+ * released with stokes_csr_free.  Deterministic: every entry sums its
+ * partial products in a fixed order.  Runs on cuda_stream (NULL: the
+ * default stream) and returns after the copy back.  STOKES_ERR_INVALID_ARG
+ * when an output row has more than 4096 partial products. */
+int stokes_galerkin(const stokes_csr* K, const stokes_csr* P, void* cuda_stream, stokes_csr* C);
+void stokes_csr_free(stokes_csr* C);
+
 /* Single steps of the cycle on one level, for testing and measurement.
  * All vectors are device FP64 of the sizes stated; the operation runs in
  * the cycle precision unless its name says FP64.

@@ -36,7 +36,7 @@ EXPORTS = ["stokes_setup", "stokes_factor_patches", "stokes_vcycle", "stokes_fgm
            "stokes_fgmres_solve_host", "stokes_level_op", "stokes_num_levels", "stokes_level_size",
            "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_time_kernel",
            "stokes_kernel_launches", "stokes_vanka_noalloc", "stokes_destroy", "stokes_autotune",
-           "stokes_autotune_report",
+           "stokes_autotune_report", "stokes_galerkin", "stokes_csr_free",
            "stokes_status_string", "stokes_last_error"]
 
 
@@ -108,6 +108,9 @@ def _load():
     lib.stokes_kernel_launches.restype = C.c_int64
     lib.stokes_vanka_noalloc.argtypes = [vp, C.c_int32, vp, vp]
     lib.stokes_destroy.argtypes = [vp]
+    lib.stokes_galerkin.argtypes = [C.POINTER(stokes_csr), C.POINTER(stokes_csr), vp, C.POINTER(stokes_csr)]
+    lib.stokes_galerkin.restype = C.c_int
+    lib.stokes_csr_free.argtypes = [C.POINTER(stokes_csr)]
     lib.stokes_autotune.argtypes = [vp, C.c_int32]
     lib.stokes_autotune.restype = C.c_int
     lib.stokes_autotune_report.argtypes = [vp]
@@ -318,6 +321,25 @@ def stokes_fgmres_solve_host(h, b, x, rtol=1e-8, restart=30, maxit=1000):
                                              restart, maxit, info),
                 "stokes_fgmres_solve_host", allow_not_converged=True)
     return rc, [(i.iters, i.status, i.true_relres) for i in info]
+
+
+def stokes_galerkin(K, P, stream=None):
+    """P^T K P on the device (FP64); K, P: scipy sparse matrices; returns a scipy CSR."""
+    import scipy.sparse as sp
+    keep = _Keep()
+    k = _csr(keep, K)
+    p = _csr(keep, P)
+    out = stokes_csr()
+    _check(lib.stokes_galerkin(C.byref(k), C.byref(p), C.c_void_p(stream) if stream else None, C.byref(out)),
+           "stokes_galerkin")
+    try:
+        n, nnz = out.nrows, out.nnz
+        rp = np.ctypeslib.as_array(out.rowptr, shape=(n + 1,)).copy()
+        ci = np.ctypeslib.as_array(out.col, shape=(nnz,)).copy() if nnz else np.zeros(0, np.int32)
+        va = np.ctypeslib.as_array(out.val, shape=(nnz,)).copy() if nnz else np.zeros(0)
+    finally:
+        lib.stokes_csr_free(C.byref(out))
+    return sp.csr_matrix((va, ci, rp), shape=(out.nrows, out.ncols))
 
 
 def stokes_autotune(h, reps=5):

@@ -1069,6 +1069,49 @@ int stokes_autotune(stokes_handle* h, int32_t reps) {
 
 const char* stokes_autotune_report(const stokes_handle* h) { return h ? h->tune_report.c_str() : "{}"; }
 
+int stokes_galerkin(const stokes_csr* K, const stokes_csr* P, void* cuda_stream, stokes_csr* C) {
+  if (!K || !P || !C) return fail(STOKES_ERR_INVALID_ARG, "null argument");
+  TRY(check_csr(K, "galerkin K"));
+  TRY(check_csr(P, "galerkin P"));
+  if (K->nrows != K->ncols || P->nrows != K->nrows)
+    return fail(STOKES_ERR_INVALID_ARG, "galerkin: K must be square and P must have K's rows");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  std::vector<int> kcol(K->col, K->col + K->nnz), pcol(P->col, P->col + P->nnz);
+  int status = 0;
+  int64_t* crp = nullptr;
+  int* ccol = nullptr;
+  double* cval = nullptr;
+  int64_t cnnz = 0;
+  cudaError_t e = galerkin_rap(K->nrows, K->rowptr, kcol.data(), K->val, P->ncols, P->rowptr, pcol.data(), P->val,
+                               st, &status, &crp, &ccol, &cval, &cnnz);
+  if (e != cudaSuccess) {
+    delete[] crp;
+    delete[] ccol;
+    delete[] cval;
+    return fail(e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA,
+                std::string("galerkin: ") + cudaGetErrorString(e));
+  }
+  if (status) return fail(STOKES_ERR_INVALID_ARG, "galerkin: a row has more than 4096 partial products");
+  C->nrows = P->ncols;
+  C->ncols = P->ncols;
+  C->nnz = cnnz;
+  C->rowptr = crp;
+  C->col = ccol;
+  C->val = cval;
+  return STOKES_OK;
+}
+
+void stokes_csr_free(stokes_csr* C) {
+  if (!C) return;
+  delete[] C->rowptr;
+  delete[] C->col;
+  delete[] C->val;
+  C->rowptr = nullptr;
+  C->col = nullptr;
+  C->val = nullptr;
+  C->nnz = 0;
+}
+
 int stokes_num_levels(const stokes_handle* h) { return h ? h->L : 0; }
 int64_t stokes_kernel_launches(const stokes_handle* h) { return h ? h->launches : 0; }
 int64_t stokes_level_size(const stokes_handle* h, int32_t l) {
@@ -1778,7 +1821,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
         dp.fac_scratch = scr;
       }
       const size_t apply_shm = T * (((size_t)max_m_large * (max_m_large + 1) / 2 + 3) / 4 * 4 +
-                                    (size_t)dim * max_m_large + 20) + 16;
+                                    2 * (size_t)dim * max_m_large + 4 + 8 * 4) + 16;
       dp.apply_global_a = apply_shm > (size_t)optin ? 1 : 0;
     }
     char* facp = nullptr;

@@ -180,6 +180,12 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
 cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, int ncols,
                       const double* V, int64_t ldv, const double* coef, int ldh, double sign, double* w,
                       cudaStream_t st);
+// Device Galerkin product Kc = P^T K P (galerkin.cu); host CSR in, host
+// arrays out (new[]); status 1: a row over the per-row product capacity.
+cudaError_t galerkin_rap(int n, const int64_t* krp, const int* kcol, const double* kval, int nc, const int64_t* prp,
+                         const int* pcol, const double* pval, cudaStream_t st, int* status, int64_t** crp,
+                         int** ccol, double** cval, int64_t* cnnz);
+
 // Krylov-wrapped relaxation (krylov.cu).  Rows of a level cut into chunks
 // that never straddle an instance; sbeg/send: chunk range of each instance.
 constexpr int kKrMaxSteps = 4;  // inner FGMRES steps per relaxation call

@@ -46,8 +46,10 @@ __device__ __forceinline__ int bsearch_int(const int* v, int n, int key) {
   return -1;
 }
 
+constexpr int kFacThreads = 256;  // CTA-per-patch factorisation (m > 32)
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_vanka_factor(int nlist, const int* __restrict__ list, int dim, int shared,
+__global__ void __launch_bounds__(kFacThreads) k_vanka_factor(int nlist, const int* __restrict__ list, int dim, int shared,
     const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
     const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing,
@@ -135,11 +137,15 @@ __global__ void __launch_bounds__(128) k_vanka_factor(int nlist, const int* __re
       }
       if (tid == 0 && bad) misc[1] = T(1);
       __syncthreads();
-      for (int e = tid; e < m * m; e += nt) {
-        const int ii = e / m, jj = e - ii * m;
-        if (ii == k) A[e] = rowk[jj];
-        else if (jj == k) A[e] = -colk[ii] * p;
-        else A[e] -= colk[ii] * rowk[jj];
+      // one warp per row, lanes along the row: no index division, conflict-free
+      for (int ii = tid >> 5; ii < m; ii += nt >> 5) {
+        const T ci = colk[ii];
+        T* Ar = A + (size_t)ii * m;
+        for (int jj = tid & 31; jj < m; jj += 32) {
+          if (ii == k) Ar[jj] = rowk[jj];
+          else if (jj == k) Ar[jj] = -ci * p;
+          else Ar[jj] -= ci * rowk[jj];
+        }
       }
       __syncthreads();
     }
@@ -426,7 +432,7 @@ cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, c
   start += p.nfac_warp[2];
   if (p.nfac_smem > 0) {
     const size_t shm = vanka_factor_smem(dm, p.max_m_fac_smem, p.max_np, sizeof(T), false);
-    k_vanka_factor<T><<<p.nfac_smem, 128, shm, st>>>(p.nfac_smem, p.fac_list + start, dm, p.shared, p.ptr, p.dof, p.nvel,
+    k_vanka_factor<T><<<p.nfac_smem, kFacThreads, shm, st>>>(p.nfac_smem, p.fac_list + start, dm, p.shared, p.ptr, p.dof, p.nvel,
                                                      p.npres, p.foff, K.rowptr, K.col, K.v64,
                                                      reinterpret_cast<T*>(p.fac), nsingular, p.max_m_fac_smem,
                                                      p.max_np, (T*)nullptr);
@@ -438,7 +444,7 @@ cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, c
   for (int c0 = 0; c0 < nglob; c0 += p.fac_chunk) {
     const int cnt = std::min(p.fac_chunk, nglob - c0);
     const size_t shm = vanka_factor_smem(dm, p.max_m, p.max_np, sizeof(T), true);
-    k_vanka_factor<T><<<cnt, 128, shm, st>>>(cnt, p.fac_list + start + c0, dm, p.shared, p.ptr, p.dof, p.nvel,
+    k_vanka_factor<T><<<cnt, kFacThreads, shm, st>>>(cnt, p.fac_list + start + c0, dm, p.shared, p.ptr, p.dof, p.nvel,
                                              p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac),
                                              nsingular, p.max_m, p.max_np, reinterpret_cast<T*>(p.fac_scratch));
     cudaError_t e = cudaGetLastError();
@@ -463,15 +469,21 @@ __device__ __forceinline__ void group_copy(T* __restrict__ dst, const T* __restr
   for (int k = nv * V + lane; k < n; k += nl) dst[k] = __ldcs(src + k);
 }
 
-// One CTA of 128 threads per patch for patches with more than 32 velocity
-// DoFs per component (coarse levels, 3D).
+// One CTA of kApplyThreads threads per patch for patches with more than 96
+// velocity DoFs per component (coarse levels, 3D): the patch's right-hand
+// side and (when it fits) its packed block in shared memory; y_u = A^-1 b_u
+// with one warp per matrix row (lanes along the row, a fixed shuffle tree
+// per row), then the Schur step and x_u = y_u - U y_p as in the warp
+// kernels.
+constexpr int kApplyThreads = 256;
+
 template <typename T, typename TR, int DIM>
-__global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* __restrict__ list,
+__global__ void __launch_bounds__(kApplyThreads) k_vanka_apply_cta(int nlist, const int* __restrict__ list,
     const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, int shared, const T* __restrict__ fac,
     const TR* __restrict__ r, T* __restrict__ yp, int max_m, int global_a, const int* __restrict__ pdst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int NT = 128, RPT = 4;  // rows per thread: m <= 512
+  constexpr int NT = kApplyThreads, NW = NT / 32;
   const int bi = blockIdx.x;
   if (bi >= nlist) return;
   const int i = list[bi];
@@ -482,9 +494,9 @@ __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* _
   const int pk = m * (m + 1) / 2;
   T* As = reinterpret_cast<T*>(smem_raw);
   T* b = As + (global_a ? 0 : ((max_m * (max_m + 1) / 2 + 3) & ~3));
-  T* red = b + DIM * max_m + kMaxNp;  // [4 warps][kMaxNp]
+  T* yu = b + DIM * max_m + kMaxNp;     // [DIM * max_m]
+  T* red = yu + DIM * max_m;            // [NW][kMaxNp]
   for (int k = tid; k < mt; k += NT) b[k] = T(r[dof[base + k]]);
-  T yu[DIM][RPT];
   const int nblk = shared ? 1 : DIM;
   for (int cb = 0; cb < nblk; ++cb) {
     const T* A = global_a ? fac + fo + (int64_t)cb * padded_pk<T>(m) : As;
@@ -492,16 +504,24 @@ __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* _
     if (!global_a) group_copy(As, fac + fo + (int64_t)cb * padded_pk<T>(m), pk, tid, NT);
     __syncthreads();
     const int c0 = shared ? 0 : cb, c1 = shared ? DIM : cb + 1;
+    for (int a = warp; a < m; a += NW) {
+      T acc[DIM];
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      const int a = tid + q * NT;
-      if (a >= m) break;
+      for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+      const int ta = a * (a + 1) / 2;
+      for (int bb = lane; bb < m; bb += 32) {
+        const T av = A[bb <= a ? ta + bb : bb * (bb + 1) / 2 + a];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+          if (c >= c0 && c < c1) acc[c] += av * b[c * m + bb];
+      }
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         if (c < c0 || c >= c1) continue;
-        T acc = T(0);
-        for (int bb = 0; bb < m; ++bb) acc += A[packed_index(a, bb)] * b[c * m + bb];
-        yu[c][q] = acc;
+        T v = acc[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) yu[c * m + a] = v;
       }
     }
   }
@@ -518,7 +538,7 @@ __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* _
   __syncthreads();
   for (int k = 0; k < np; ++k) {
     T s = red[k];
-    for (int w = 1; w < NT / 32; ++w) s += red[w * kMaxNp + k];
+    for (int w = 1; w < NW; ++w) s += red[w * kMaxNp + k];
     t[k] = b[mu + k] - s;
   }
   for (int k = 0; k < np; ++k) {
@@ -526,16 +546,10 @@ __global__ void __launch_bounds__(128) k_vanka_apply_cta(int nlist, const int* _
     for (int k2 = 0; k2 < np; ++k2) s += Sinv[k * np + k2] * t[k2];
     ypk[k] = s;
   }
-#pragma unroll
-  for (int q = 0; q < RPT; ++q) {
-    const int a = tid + q * NT;
-    if (a >= m) break;
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      T x = yu[c][q];
-      for (int k = 0; k < np; ++k) x -= U[(int64_t)k * mu + c * m + a] * ypk[k];
-      yp[pdst[base + c * m + a]] = x;
-    }
+  for (int e = tid; e < mu; e += NT) {
+    T x = yu[e];
+    for (int k = 0; k < np; ++k) x -= U[(int64_t)k * mu + e] * ypk[k];
+    yp[pdst[base + e]] = x;
   }
   if (tid < np) yp[pdst[base + mu + tid]] = ypk[tid];
 }
@@ -849,14 +863,15 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
   if (p.nlarge > 0) {
     const int mm = p.max_m_large;
     const int ga = p.apply_global_a;
-    size_t shm = sizeof(T) * ((ga ? 0 : ((size_t)mm * (mm + 1) / 2 + 3) / 4 * 4) + (size_t)p.dim * mm + kMaxNp + 4 * kMaxNp) + 16;
+    size_t shm = sizeof(T) * ((ga ? 0 : ((size_t)mm * (mm + 1) / 2 + 3) / 4 * 4) + 2 * (size_t)p.dim * mm + kMaxNp +
+                              (kApplyThreads / 32) * kMaxNp) + 16;
     cudaError_t e;
     if (p.dim == 2) {
-      k_vanka_apply_cta<T, TR, 2><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
+      k_vanka_apply_cta<T, TR, 2><<<p.nlarge, kApplyThreads, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
                                                              p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga,
                                                              p.pdst);
     } else {
-      k_vanka_apply_cta<T, TR, 3><<<p.nlarge, 128, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
+      k_vanka_apply_cta<T, TR, 3><<<p.nlarge, kApplyThreads, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
                                                              p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga,
                                                              p.pdst);
     }
