@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libstokes_dcamg.so")
-SOURCES = ["spmv.cu", "vanka.cu", "blas.cu", "fgmres.cu", "krylov.cu", "galerkin.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["spmv.cu", "vanka.cu", "vanka_tiles.cu", "blas.cu", "fgmres.cu", "krylov.cu", "galerkin.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

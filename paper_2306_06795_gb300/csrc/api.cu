@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "stokes_dcamg.h"
+#include "tiles.cuh"
 
 using namespace sd;
 
@@ -1681,8 +1682,11 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     }
     bin_start[kTmaBins] = (int)order.size();
     const int nsmall = (int)order.size();
+    // the rest (tiled blocks) by descending m: the persistent apply deals
+    // them round robin to its warps
     for (int i = 0; i < npatch; ++i)
       if (bin_of(onv[i]) < 0) order.push_back(i);
+    std::stable_sort(order.begin() + nsmall, order.end(), [&](int a, int b) { return onv[a] > onv[b]; });
     std::vector<int> pptr{0}, pdof, pnv, pnp, small, large, stor(npatch);
     std::vector<int64_t> foff;
     int64_t fac = 0;
@@ -1697,7 +1701,8 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       pnv.push_back((int)m);
       pnp.push_back((int)np);
       foff.push_back(fac);
-      const int64_t pkp = (m * (m + 1) / 2 + align - 1) / align * align;  // blocks start 16-byte aligned
+      // blocks start 16-byte aligned; bulk-copy bins packed, the rest tiled
+      const int64_t pkp = si < nsmall ? (m * (m + 1) / 2 + align - 1) / align * align : tiled_block_elems((int)m);
       int64_t sz = nblk * pkp + dim * m * np + np * np;
       fac += (sz + align - 1) / align * align;
       (si < nsmall ? small : large).push_back(si);
@@ -1787,17 +1792,27 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       lv.hpptr = pptr;
       dp.use_tma = nsmall > 0;
     }
-    // factorisation order: blocks that fit in shared memory, then the rest
+    // factorisation order: warp bins; then FP32: tensor-core sweep grouped by
+    // tile rows (shared memory), the rest in global scratch; FP64: blocks that
+    // fit in shared memory, then the rest
     {
       int optin = 0, dev = 0;
       CK(cudaGetDevice(&dev));
       CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      std::vector<int> fl, fg, fw[3];
-      int msm = 0;
+      std::vector<int> fl, fg, fw[3], ft[kTcMaxSmemRows + 1];
+      int msm = 0, glob_rows = 0;
       for (int si = 0; si < npatch; ++si) {
         const int wb = vanka_factor_warp_bin(pnv[si]);
+        const int rows = tile_rows(pnv[si]);
         if (wb >= 0) {
           fw[wb].push_back(si);
+        } else if (T == 4) {
+          if (rows <= kTcMaxSmemRows && vanka_factor_tc_smem(dim, rows, max_np, false) <= (size_t)optin) {
+            ft[rows].push_back(si);
+          } else {
+            fg.push_back(si);
+            glob_rows = std::max(glob_rows, rows);
+          }
         } else if (vanka_factor_smem(dim, pnv[si], max_np, T, false) <= (size_t)optin) {
           fl.push_back(si);
           msm = std::max(msm, pnv[si]);
@@ -1805,8 +1820,16 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
           fg.push_back(si);
         }
       }
-      dp.nfac_smem = (int)fl.size();
-      dp.max_m_fac_smem = msm;
+      if (T == 4) {
+        for (int rows = 1; rows <= kTcMaxSmemRows; ++rows) {
+          dp.nfac_tc[rows] = (int)ft[rows].size();
+          fl.insert(fl.end(), ft[rows].begin(), ft[rows].end());
+        }
+        dp.tc_glob_rows = glob_rows;
+      } else {
+        dp.nfac_smem = (int)fl.size();
+        dp.max_m_fac_smem = msm;
+      }
       fl.insert(fl.end(), fg.begin(), fg.end());
       for (int b = 2; b >= 0; --b) {
         dp.nfac_warp[b] = (int)fw[b].size();
@@ -1814,15 +1837,45 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       }
       TRY(upload(h, &dp.fac_list, fl));
       if (!fg.empty()) {
-        if (vanka_factor_smem(dim, max_m, max_np, T, true) > (size_t)optin)
-          return fail(STOKES_ERR_INVALID_ARG, "patch too large for the factorisation kernel");
+        size_t scr_bytes;
+        if (T == 4) {
+          if (vanka_factor_tc_smem(dim, glob_rows, max_np, true) > (size_t)optin)
+            return fail(STOKES_ERR_INVALID_ARG, "patch too large for the factorisation kernel");
+          scr_bytes = (size_t)dp.fac_chunk * ((size_t)glob_rows * (glob_rows + 1) / 2 + glob_rows) * kTileElems * 4;
+        } else {
+          if (vanka_factor_smem(dim, max_m, max_np, T, true) > (size_t)optin)
+            return fail(STOKES_ERR_INVALID_ARG, "patch too large for the factorisation kernel");
+          scr_bytes = (size_t)dp.fac_chunk * max_m * max_m * T;
+        }
         char* scr = nullptr;
-        TRY(dalloc(h, &scr, (size_t)dp.fac_chunk * max_m * max_m * T));
+        TRY(dalloc(h, &scr, scr_bytes));
         dp.fac_scratch = scr;
       }
-      const size_t apply_shm = T * (((size_t)max_m_large * (max_m_large + 1) / 2 + 3) / 4 * 4 +
-                                    2 * (size_t)dim * max_m_large + 4 + 8 * 4) + 16;
-      dp.apply_global_a = apply_shm > (size_t)optin ? 1 : 0;
+      // apply of the tiled patches: per consumer warp a ring that holds U |
+      // S^-1 and the output positions at once, plus two tiles of prefetch
+      if (!large.empty()) {
+        if (dim * max_m_large + max_np + 6 > kTileElems)
+          return fail(STOKES_ERR_INVALID_ARG, "patch too large for the tiled apply");
+        int nus = 0;
+        for (int si : large) {
+          const int64_t L = (int64_t)dim * pnv[si] * pnp[si] + (int64_t)pnp[si] * pnp[si];
+          nus = std::max(nus, (int)((L + kTileElems - 1) / kTileElems));
+        }
+        dp.tiles_nodes = 32 * tile_rows(max_m_large);
+        int nsm = 0;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        int stages = std::max(4, nus + 3);
+        int per_sm = 0;
+        for (; stages >= nus + 1; --stages) {
+          if (vanka_tiles_smem(stages, dp.tiles_nodes, dim, T) > (size_t)optin) continue;
+          per_sm = vanka_tiles_blocks_per_sm(stages, dp.tiles_nodes, dim, max_np, T);
+          if (per_sm > 0) break;
+        }
+        if (per_sm <= 0) return fail(STOKES_ERR_INVALID_ARG, "tiled patches do not fit on an SM");
+        dp.tiles_stages = stages;
+        const int want = (int)((large.size() + 3) / 4);  // four consumer warps per CTA
+        dp.tiles_grid = std::max(1, std::min(want, per_sm * nsm));
+      }
     }
     char* facp = nullptr;
     TRY(dalloc(h, &facp, (size_t)fac * T));

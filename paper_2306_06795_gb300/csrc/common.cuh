@@ -45,6 +45,7 @@ cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y
 // A bin of patches solved by the bulk-copy kernel: storage patches
 // [start, start + count), all with m in the bin's range.
 constexpr int kTmaBins = 5;
+constexpr int kTcMaxSmemRows = 8;  // tensor-core factorisation keeps up to 8 x 8 tile rows on chip
 struct TmaBin {
   int start = 0, count = 0, tp = 0, ntiles = 0, grid = 0, stages = 3;
   int fac_bytes = 0, dof_bytes = 0, rhs_elems = 0, max_np = 0;
@@ -62,9 +63,9 @@ struct DevPatches {
   int64_t fac_elems = 0;
   void* fac = nullptr;    // factors, float or double
   int shared = 1;         // one velocity block shared by all components
-  int* small = nullptr;   // patch ids with m <= 32
+  int* small = nullptr;   // storage ids of the patches in bulk-copy bins (packed blocks)
   int nsmall = 0;
-  int* large = nullptr;   // patch ids with m > 32
+  int* large = nullptr;   // storage ids of the rest (tiled blocks), by descending m
   int nlarge = 0;
   int max_m = 0, max_np = 0, max_m_large = 0;
   int* tptr = nullptr;    // [n+1] DoF j's patch solutions are yp[tptr[j] .. tptr[j+1])
@@ -79,13 +80,23 @@ struct DevPatches {
   // factorisation: patches whose block fits in shared memory first
   int* fac_list = nullptr;
   int nfac_warp[3] = {0, 0, 0};  // warp-per-patch bins m <= 8, 20, 32 (first in fac_list)
+  // FP64: CTA-per-patch Gauss-Jordan, blocks in shared memory, then the rest
   int nfac_smem = 0, max_m_fac_smem = 0, fac_chunk = 256;
-  void* fac_scratch = nullptr;  // fac_chunk * max_m^2 elements, when needed
-  int apply_global_a = 0;       // large-bin apply reads A from global memory
+  // FP32: tensor-core blocked sweep, per tile-row count nT = 1..8 with the
+  // tiles in shared memory, then the rest with the tiles in global scratch
+  int nfac_tc[kTcMaxSmemRows + 1] = {};
+  int tc_glob_rows = 0;         // largest nT of the global-scratch patches
+  void* fac_scratch = nullptr;  // per-chunk scratch of the global-memory variants
+  // apply of the large patches (tiled blocks): ring stages per warp, node
+  // capacity (32 * largest nT) and persistent grid
+  int tiles_stages = 0, tiles_nodes = 0, tiles_grid = 0;
 };
 
 size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool global_a);
+size_t vanka_factor_tc_smem(int dim, int rows, int max_np, bool global_tiles);
 int vanka_factor_warp_bin(int m);  // 0, 1, 2 for m <= 8, 20, 32; -1 above
+size_t vanka_tiles_smem(int stages, int nodes, int dim, size_t elem);
+int vanka_tiles_blocks_per_sm(int stages, int nodes, int dim, int np_max, size_t elem);
 
 }  // namespace sd
 struct stokes_handle;
@@ -111,6 +122,12 @@ cudaError_t vanka_apply_bin(const DevPatches& p, int b, const void* r, void* yp,
 
 template <typename T>
 cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st);
+// FP32 factorisation of the CTA-per-patch patches (m > 32) on tensor cores
+cudaError_t vanka_factor_tc(const DevPatches& p, const DevCSR& K, int start, int* nsingular, cudaStream_t st);
+// patch solves of the large patches (tiled blocks)
+template <typename T, typename TR>
+cudaError_t vanka_apply_tiles(const DevPatches& p, const TR* r, T* yp, cudaStream_t st);
+cudaError_t vanka_tiles_prepare_kernels(int optin);
 
 // Patch solves of Eqs. vanka_fact1/2 for every patch: yp (patch-major) =
 // K_i^-1 V_i r.

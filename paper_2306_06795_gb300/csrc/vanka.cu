@@ -15,11 +15,11 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tiles.cuh"
 #include "tma.cuh"
 
 namespace sd {
 
-constexpr int kMaxNp = 4;     // seeds per patch supported by the apply kernels
 constexpr int kWarpM = 32;    // velocity DoFs per component handled by the warp kernel
 constexpr int kWarpPk = kWarpM * (kWarpM + 1) / 2;
 
@@ -27,25 +27,7 @@ __device__ __forceinline__ int packed_index(int a, int b) {
   return a >= b ? a * (a + 1) / 2 + b : b * (b + 1) / 2 + a;
 }
 
-// Packed block length rounded up to 16 bytes, so every block starts aligned.
-template <typename T>
-__host__ __device__ __forceinline__ int padded_pk(int m) {
-  constexpr int V = 16 / sizeof(T);
-  return (m * (m + 1) / 2 + V - 1) / V * V;
-}
-
 // -------------------------------------------------------------- factorise
-__device__ __forceinline__ int bsearch_int(const int* v, int n, int key) {
-  int lo = 0, hi = n - 1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    const int x = v[mid];
-    if (x == key) return mid;
-    if (x < key) lo = mid + 1; else hi = mid - 1;
-  }
-  return -1;
-}
-
 constexpr int kFacThreads = 256;  // CTA-per-patch factorisation (m > 32)
 
 template <typename T>
@@ -53,7 +35,7 @@ __global__ void __launch_bounds__(kFacThreads) k_vanka_factor(int nlist, const i
     const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
     const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing,
-    int max_m, int max_np, T* __restrict__ gA) {
+    int max_m, int max_np, T* __restrict__ gA, int nsmall) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if ((int)blockIdx.x >= nlist) return;
   const int i = list[blockIdx.x];
@@ -94,7 +76,8 @@ __global__ void __launch_bounds__(kFacThreads) k_vanka_factor(int nlist, const i
     }
   }
   const int nblk = shared ? 1 : dim;
-  const int pkp = padded_pk<T>(m);
+  const bool tiled = i >= nsmall;
+  const int64_t blk = tiled ? tiled_block_elems(m) : (int64_t)padded_pk<T>(m);
   T* out = fac + foff[i];
   for (int cb = 0; cb < nblk; ++cb) {
     __syncthreads();
@@ -149,9 +132,20 @@ __global__ void __launch_bounds__(kFacThreads) k_vanka_factor(int nlist, const i
       }
       __syncthreads();
     }
-    // packed lower triangle of the (symmetrised) inverse
-    for (int a = tid; a < m; a += nt)
-      for (int b = 0; b <= a; ++b) out[cb * pkp + a * (a + 1) / 2 + b] = T(0.5) * (A[a * m + b] + A[b * m + a]);
+    // lower triangle of the (symmetrised) inverse, tiled or packed
+    if (tiled) {
+      for (int64_t e = tid; e < blk; e += nt) {
+        const int q = (int)(e >> 10);
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= q) ++I;
+        const int J = q - I * (I + 1) / 2, r = (int)(e >> 5) & 31, c = ((int)e & 31) ^ r;
+        const int a = I * 32 + r, b = J * 32 + c;
+        out[cb * blk + e] = (a < m && b < m) ? T(0.5) * (A[a * m + b] + A[b * m + a]) : T(0);
+      }
+    } else {
+      for (int a = tid; a < m; a += nt)
+        for (int b = 0; b <= a; ++b) out[cb * blk + a * (a + 1) / 2 + b] = T(0.5) * (A[a * m + b] + A[b * m + a]);
+    }
     // U rows of the components this block serves
     const int c0 = shared ? 0 : cb, c1 = shared ? dim : cb + 1;
     for (int c = c0; c < c1; ++c)
@@ -170,7 +164,7 @@ __global__ void __launch_bounds__(kFacThreads) k_vanka_factor(int nlist, const i
     S[k * kMaxNp + k2] = -s;
   }
   __syncthreads();
-  T* Uout = out + nblk * pkp;
+  T* Uout = out + nblk * blk;
   T* Sout = Uout + mu * np;
   for (int idx = tid; idx < mu * np; idx += nt) {
     const int r = idx / np, k = idx - r * np;
@@ -230,7 +224,7 @@ template <typename T, int MAXM>
 __global__ void __launch_bounds__(kFacWarps * 32) k_vanka_factor_warp(int nlist, const int* __restrict__ list,
     int dim, int shared, const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
-    const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing) {
+    const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing, int nsmall) {
   using L = FacWarpSmem<T, MAXM>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -269,7 +263,8 @@ __global__ void __launch_bounds__(kFacWarps * 32) k_vanka_factor_warp(int nlist,
     }
   }
   const int nblk = shared ? 1 : dim;
-  const int pkp = padded_pk<T>(m);
+  const bool tiled = i >= nsmall;  // one 32 x 32 tile
+  const int blk = tiled ? kTileElems : padded_pk<T>(m);
   T* out = fac + foff[i];
   bool sing = false;
   for (int cb = 0; cb < nblk; ++cb) {
@@ -330,9 +325,14 @@ __global__ void __launch_bounds__(kFacWarps * 32) k_vanka_factor_warp(int nlist,
       for (int j = 0; j < MAXM; ++j) Am[lane * L::kStride + j] = row[j];
     }
     __syncwarp();
-    if (lane < m)
+    if (tiled) {
+      for (int c = 0; c < 32; ++c)
+        out[cb * blk + lane * 32 + (c ^ lane)] =
+            lane < m && c < m ? T(0.5) * (Am[lane * L::kStride + c] + Am[c * L::kStride + lane]) : T(0);
+    } else if (lane < m) {
       for (int b = 0; b <= lane; ++b)
-        out[cb * pkp + lane * (lane + 1) / 2 + b] = T(0.5) * (Am[lane * L::kStride + b] + Am[b * L::kStride + lane]);
+        out[cb * blk + lane * (lane + 1) / 2 + b] = T(0.5) * (Am[lane * L::kStride + b] + Am[b * L::kStride + lane]);
+    }
     // U rows of the components this block serves: U = A^-1 B^T
     const int c0 = shared ? 0 : cb, c1 = shared ? dim : cb + 1;
     if (lane < m)
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kFacWarps * 32) k_vanka_factor_warp(int nlist,
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) S[k * kMaxNp + k2] = -s;
   }
-  T* Uout = out + nblk * pkp;
+  T* Uout = out + nblk * blk;
   T* Sout = Uout + mu * np;
   for (int idx = lane; idx < mu * np; idx += 32) {
     const int r = idx / np, k = idx - r * np;
@@ -400,7 +400,7 @@ static cudaError_t launch_factor_warp(const DevPatches& p, const DevCSR& K, int 
   const size_t shm = kFacWarps * FacWarpSmem<T, MAXM>::bytes();
   const unsigned blocks = (unsigned)((count + kFacWarps - 1) / kFacWarps);
   k_vanka_factor_warp<T, MAXM><<<blocks, kFacWarps * 32, shm, st>>>(count, p.fac_list + start, p.dim, p.shared,
-      p.ptr, p.dof, p.nvel, p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac), nsingular);
+      p.ptr, p.dof, p.nvel, p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac), nsingular, p.nsmall);
   return cudaGetLastError();
 }
 
@@ -412,14 +412,15 @@ size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool globa
          sizeof(int) * ((size_t)dim * max_m + max_np) + 16;
 }
 
-// Factorise the patches in `list`: patches whose m x m block fits in shared
-// memory in one launch; the others (coarse 3D levels) in chunks of at most
-// `chunk` patches with the block in the global scratch gA.
+// Factorise all patches: the warp-per-patch bins (m <= 32) lead the list;
+// then, for FP32, the tensor-core blocked sweep, and for FP64 the
+// CTA-per-patch Gauss-Jordan (blocks that fit in shared memory first, the
+// rest in chunks of at most `fac_chunk` patches with the block in the global
+// scratch gA).
 template <typename T>
 cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, cudaStream_t st) {
   if (p.npatch == 0) return cudaSuccess;
   const int dm = p.dim;
-  // warp-per-patch bins (m <= 8, 20, 32) lead the list, then the CTA kernel
   int start = 0;
   cudaError_t e0 = launch_factor_warp<T, 8>(p, K, start, p.nfac_warp[0], nsingular, st);
   if (e0 != cudaSuccess) return e0;
@@ -430,27 +431,32 @@ cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, c
   e0 = launch_factor_warp<T, 32>(p, K, start, p.nfac_warp[2], nsingular, st);
   if (e0 != cudaSuccess) return e0;
   start += p.nfac_warp[2];
-  if (p.nfac_smem > 0) {
-    const size_t shm = vanka_factor_smem(dm, p.max_m_fac_smem, p.max_np, sizeof(T), false);
-    k_vanka_factor<T><<<p.nfac_smem, kFacThreads, shm, st>>>(p.nfac_smem, p.fac_list + start, dm, p.shared, p.ptr, p.dof, p.nvel,
-                                                     p.npres, p.foff, K.rowptr, K.col, K.v64,
-                                                     reinterpret_cast<T*>(p.fac), nsingular, p.max_m_fac_smem,
-                                                     p.max_np, (T*)nullptr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    return vanka_factor_tc(p, K, start, nsingular, st);
+  } else {
+    if (p.nfac_smem > 0) {
+      const size_t shm = vanka_factor_smem(dm, p.max_m_fac_smem, p.max_np, sizeof(T), false);
+      k_vanka_factor<T><<<p.nfac_smem, kFacThreads, shm, st>>>(p.nfac_smem, p.fac_list + start, dm, p.shared, p.ptr,
+                                                               p.dof, p.nvel, p.npres, p.foff, K.rowptr, K.col, K.v64,
+                                                               reinterpret_cast<T*>(p.fac), nsingular,
+                                                               p.max_m_fac_smem, p.max_np, (T*)nullptr, p.nsmall);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    start += p.nfac_smem;
+    const int nglob = p.npatch - start;
+    for (int c0 = 0; c0 < nglob; c0 += p.fac_chunk) {
+      const int cnt = std::min(p.fac_chunk, nglob - c0);
+      const size_t shm = vanka_factor_smem(dm, p.max_m, p.max_np, sizeof(T), true);
+      k_vanka_factor<T><<<cnt, kFacThreads, shm, st>>>(cnt, p.fac_list + start + c0, dm, p.shared, p.ptr, p.dof,
+                                                       p.nvel, p.npres, p.foff, K.rowptr, K.col, K.v64,
+                                                       reinterpret_cast<T*>(p.fac), nsingular, p.max_m, p.max_np,
+                                                       reinterpret_cast<T*>(p.fac_scratch), p.nsmall);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
-  start += p.nfac_smem;
-  const int nglob = p.npatch - start;
-  for (int c0 = 0; c0 < nglob; c0 += p.fac_chunk) {
-    const int cnt = std::min(p.fac_chunk, nglob - c0);
-    const size_t shm = vanka_factor_smem(dm, p.max_m, p.max_np, sizeof(T), true);
-    k_vanka_factor<T><<<cnt, kFacThreads, shm, st>>>(cnt, p.fac_list + start + c0, dm, p.shared, p.ptr, p.dof, p.nvel,
-                                             p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac),
-                                             nsingular, p.max_m, p.max_np, reinterpret_cast<T*>(p.fac_scratch));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
 }
 template cudaError_t vanka_factor<float>(const DevPatches&, const DevCSR&, int*, cudaStream_t);
 template cudaError_t vanka_factor<double>(const DevPatches&, const DevCSR&, int*, cudaStream_t);
@@ -467,91 +473,6 @@ __device__ __forceinline__ void group_copy(T* __restrict__ dst, const T* __restr
   int4* d4 = reinterpret_cast<int4*>(dst);
   for (int k = lane; k < nv; k += nl) d4[k] = __ldcs(s4 + k);
   for (int k = nv * V + lane; k < n; k += nl) dst[k] = __ldcs(src + k);
-}
-
-// One CTA of kApplyThreads threads per patch for patches with more than 96
-// velocity DoFs per component (coarse levels, 3D): the patch's right-hand
-// side and (when it fits) its packed block in shared memory; y_u = A^-1 b_u
-// with one warp per matrix row (lanes along the row, a fixed shuffle tree
-// per row), then the Schur step and x_u = y_u - U y_p as in the warp
-// kernels.
-constexpr int kApplyThreads = 256;
-
-template <typename T, typename TR, int DIM>
-__global__ void __launch_bounds__(kApplyThreads) k_vanka_apply_cta(int nlist, const int* __restrict__ list,
-    const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
-    const int* __restrict__ npres, const int64_t* __restrict__ foff, int shared, const T* __restrict__ fac,
-    const TR* __restrict__ r, T* __restrict__ yp, int max_m, int global_a, const int* __restrict__ pdst) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int NT = kApplyThreads, NW = NT / 32;
-  const int bi = blockIdx.x;
-  if (bi >= nlist) return;
-  const int i = list[bi];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int base = ptr[i], m = nvel[i], np = npres[i];
-  const int mu = DIM * m, mt = mu + np;
-  const int64_t fo = foff[i];
-  const int pk = m * (m + 1) / 2;
-  T* As = reinterpret_cast<T*>(smem_raw);
-  T* b = As + (global_a ? 0 : ((max_m * (max_m + 1) / 2 + 3) & ~3));
-  T* yu = b + DIM * max_m + kMaxNp;     // [DIM * max_m]
-  T* red = yu + DIM * max_m;            // [NW][kMaxNp]
-  for (int k = tid; k < mt; k += NT) b[k] = T(r[dof[base + k]]);
-  const int nblk = shared ? 1 : DIM;
-  for (int cb = 0; cb < nblk; ++cb) {
-    const T* A = global_a ? fac + fo + (int64_t)cb * padded_pk<T>(m) : As;
-    __syncthreads();
-    if (!global_a) group_copy(As, fac + fo + (int64_t)cb * padded_pk<T>(m), pk, tid, NT);
-    __syncthreads();
-    const int c0 = shared ? 0 : cb, c1 = shared ? DIM : cb + 1;
-    for (int a = warp; a < m; a += NW) {
-      T acc[DIM];
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-      const int ta = a * (a + 1) / 2;
-      for (int bb = lane; bb < m; bb += 32) {
-        const T av = A[bb <= a ? ta + bb : bb * (bb + 1) / 2 + a];
-#pragma unroll
-        for (int c = 0; c < DIM; ++c)
-          if (c >= c0 && c < c1) acc[c] += av * b[c * m + bb];
-      }
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        if (c < c0 || c >= c1) continue;
-        T v = acc[c];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) yu[c * m + a] = v;
-      }
-    }
-  }
-  const T* U = fac + fo + (int64_t)nblk * padded_pk<T>(m);
-  const T* Sinv = U + (int64_t)mu * np;
-  T t[kMaxNp], ypk[kMaxNp];
-  for (int k = 0; k < np; ++k) {
-    T part = T(0);
-    for (int rr = tid; rr < mu; rr += NT) part += U[(int64_t)k * mu + rr] * b[rr];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    if (lane == 0) red[warp * kMaxNp + k] = part;
-  }
-  __syncthreads();
-  for (int k = 0; k < np; ++k) {
-    T s = red[k];
-    for (int w = 1; w < NW; ++w) s += red[w * kMaxNp + k];
-    t[k] = b[mu + k] - s;
-  }
-  for (int k = 0; k < np; ++k) {
-    T s = T(0);
-    for (int k2 = 0; k2 < np; ++k2) s += Sinv[k * np + k2] * t[k2];
-    ypk[k] = s;
-  }
-  for (int e = tid; e < mu; e += NT) {
-    T x = yu[e];
-    for (int k = 0; k < np; ++k) x -= U[(int64_t)k * mu + e] * ypk[k];
-    yp[pdst[base + e]] = x;
-  }
-  if (tid < np) yp[pdst[base + mu + tid]] = ypk[tid];
 }
 
 // Persistent, warp-specialised patch solves.  Patches are stored bin by bin
@@ -860,24 +781,7 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
     cudaError_t e = apply_tma_bins<T, TR>(p, r, yp, st);
     if (e != cudaSuccess) return e;
   }
-  if (p.nlarge > 0) {
-    const int mm = p.max_m_large;
-    const int ga = p.apply_global_a;
-    size_t shm = sizeof(T) * ((ga ? 0 : ((size_t)mm * (mm + 1) / 2 + 3) / 4 * 4) + 2 * (size_t)p.dim * mm + kMaxNp +
-                              (kApplyThreads / 32) * kMaxNp) + 16;
-    cudaError_t e;
-    if (p.dim == 2) {
-      k_vanka_apply_cta<T, TR, 2><<<p.nlarge, kApplyThreads, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga,
-                                                             p.pdst);
-    } else {
-      k_vanka_apply_cta<T, TR, 3><<<p.nlarge, kApplyThreads, shm, st>>>(p.nlarge, p.large, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                             p.shared, reinterpret_cast<const T*>(p.fac), r, yp, mm, ga,
-                                                             p.pdst);
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  if (p.nlarge > 0) return vanka_apply_tiles<T, TR>(p, r, yp, st);
   return cudaSuccess;
 }
 template cudaError_t vanka_apply<float, float>(const DevPatches&, const float*, float*, cudaStream_t);
@@ -893,8 +797,6 @@ cudaError_t vanka_prepare_kernels() {
   if (e != cudaSuccess) return e;
   std::vector<const void*> ks = {
       (const void*)k_vanka_factor<float>, (const void*)k_vanka_factor<double>,
-      (const void*)k_vanka_apply_cta<float, float, 2>, (const void*)k_vanka_apply_cta<float, float, 3>,
-      (const void*)k_vanka_apply_cta<double, double, 2>, (const void*)k_vanka_apply_cta<double, double, 3>,
       (const void*)k_vanka_factor_warp<float, 8>, (const void*)k_vanka_factor_warp<float, 20>,
       (const void*)k_vanka_factor_warp<float, 32>, (const void*)k_vanka_factor_warp<double, 8>,
       (const void*)k_vanka_factor_warp<double, 20>, (const void*)k_vanka_factor_warp<double, 32>};
@@ -906,7 +808,7 @@ cudaError_t vanka_prepare_kernels() {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  return vanka_tiles_prepare_kernels(optin);
 }
 
 // -------------------------------------------------------------- scatter
