@@ -487,6 +487,81 @@ def run_gpu_c5(args):
         dist.destroy_process_group()
 
 
+def run_gpu_configs(args):
+    """One JSON line per config (C1, C2, C3 with Vanka and with DLSC on the
+    coarse levels, C4): FP32- and FP64-preconditioned solves to 1e-8 from
+    x0 = 0 (factorisation + FGMRES per step), iterations, true residuals,
+    the FP32 solution's error against the FP64 one, and the FP32 V-cycle
+    time.  Context for the C2 headline; rank 0 only."""
+    import torch
+
+    import paper_2306_06795_gb300 as sd
+    from problems import configs
+
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    cases = [("C1 TH2D 16^2 lid", configs.c1, lambda pr: configs.TH2D_VANKA),
+             ("C2 TH2D 256^2 manufactured", configs.c2, lambda pr: configs.TH2D_VANKA),
+             ("C3 SV2D 128^2 Vanka", configs.c3, lambda pr: configs.SV2D_VANKA),
+             ("C3 SV2D 128^2 Vanka + DLSC", configs.c3, lambda pr: configs.sv_vanka_dlsc(pr.nlevels)),
+             ("C4 TH3D 32^3 lid", configs.c4, lambda pr: configs.TH3D_VANKA)]
+    built = {}
+    for name, make, params in cases:
+        key = make.__name__
+        if key not in built:
+            built[key] = make()
+        pr = built[key]
+        prm = params(pr)
+        n = pr.b.size
+        b = torch.tensor(pr.b, dtype=torch.float64, device=dev)
+        res = {}
+        xs = {}
+        with torch.cuda.stream(stream):
+            for prec in (sd.STOKES_FP32, sd.STOKES_FP64):
+                h = sd.stokes_setup(pr, dict(prm, precision=prec), stream=stream.cuda_stream)
+                x = torch.zeros_like(b)
+
+                def step():
+                    sd.stokes_factor_patches(h)
+                    x.zero_()
+                    rc, info = sd.stokes_fgmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=600)
+                    return rc, info[0]
+
+                for _ in range(2):
+                    rc, info = step()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                reps = 3
+                e0.record(stream)
+                for _ in range(reps):
+                    rc, info = step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                z = torch.empty_like(b)
+                for _ in range(3):
+                    sd.stokes_vcycle(h, b, z)
+                e0.record(stream)
+                for _ in range(10):
+                    sd.stokes_vcycle(h, b, z)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res[prec] = dict(status=int(rc), iters=int(info[0]), true_relres=float(info[2]), ms_per_solve=ms,
+                                 vcycle_ms=e0.elapsed_time(e1) / 10, cycle_bytes=sd.stokes_cycle_bytes(h))
+                xs[prec] = x.cpu().numpy()
+                sd.stokes_destroy(h)
+        err = float(np.linalg.norm(xs[sd.STOKES_FP32] - xs[sd.STOKES_FP64]) / np.linalg.norm(xs[sd.STOKES_FP64]))
+        r32, r64 = res[sd.STOKES_FP32], res[sd.STOKES_FP64]
+        print(json.dumps({"config": name, "dofs": int(n), "levels": int(pr.nlevels),
+                          "fp32": r32, "fp64": r64, "fp32_vs_fp64_solution_relerr": err,
+                          "fp32_vcycle_GBps": r32["cycle_bytes"] / r32["vcycle_ms"] / 1e6}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,8 +575,9 @@ def main():
                     help="profiling driver: set up, factorise and run one FP32-preconditioned solve")
     ap.add_argument("--ref-iters", type=int, default=34,
                     help="iterations a full oracle solve takes (scales the reference sample)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
-                    help="c2: the single 256^2 problem (default); c5: the 64-instance batch")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5", "configs"],
+                    help="c2: the single 256^2 problem (default); c5: the 64-instance batch; "
+                         "configs: one line per config C1-C4")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -509,6 +585,8 @@ def main():
         run_profile(args)
     elif args.workload == "c5":
         run_gpu_c5(args)
+    elif args.workload == "configs":
+        run_gpu_configs(args)
     else:
         run_gpu(args)
 

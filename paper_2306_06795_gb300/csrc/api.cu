@@ -124,6 +124,7 @@ struct stokes_handle {
   cudaStream_t st = nullptr;
   bool own_stream = false;     // created here: joined with the legacy default stream per call
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  ForkJoin fj;                 // side streams for independent launches of one step
   std::vector<Level> lv;
   std::vector<int> inst_levels;
   uint8_t* kind0 = nullptr;  // level 0: 0 velocity, 1 pressure, 2 Dirichlet
@@ -232,8 +233,9 @@ int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
   d.tpr = choose_tpr(d.nnz, d.nrows);
   int maxrow = 0;
   for (int i = 0; i < c.nrows; ++i) maxrow = std::max(maxrow, c.rowptr[i + 1] - c.rowptr[i]);
-  // row-block tiles for the stream SpMV (mid-size operators)
-  if (c.nrows >= kStreamMinRows && c.nrows < kSellRows && maxrow <= kStreamNnz) {
+  // row-block tiles for the stream SpMV: mid-size operators, and large ones
+  // whose row lengths vary too much for a sliced-ELLPACK copy
+  auto stream_tiles = [&]() -> int {
     std::vector<int4> td;
     int r = 0;
     while (r < c.nrows) {
@@ -245,7 +247,8 @@ int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
     d.stiles = (int)td.size();
     TRY(upload(h, &d.tdesc, td));
     return STOKES_OK;
-  }
+  };
+  if (c.nrows >= kStreamMinRows && c.nrows < kSellRows && maxrow <= kStreamNnz) return stream_tiles();
   // sliced ELLPACK copy when the padding to the longest row of each chunk
   // of 32 rows stays small
   if (c.nrows >= kSellRows) {
@@ -276,6 +279,7 @@ int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
       d.schunks = nch;
       return STOKES_OK;
     }
+    if (maxrow <= kStreamNnz) return stream_tiles();
   }
   return STOKES_OK;
 }
@@ -455,7 +459,7 @@ int L_apply(stokes_handle* h, const Level& lv, const TR* r, T* yp) {
     h->led.launches += p.nlarge > 0;
     return STOKES_OK;
   }
-  CK((vanka_apply<T, TR>(p, r, yp, h->st)));
+  CK((vanka_apply<T, TR>(p, r, yp, h->st, &h->fj)));
   return STOKES_OK;
 }
 
@@ -984,6 +988,11 @@ void stokes_destroy(stokes_handle* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  for (int k = 0; k < kForkMax; ++k) {
+    if (h->fj.side[k]) cudaStreamDestroy(h->fj.side[k]);
+    if (h->fj.join[k]) cudaEventDestroy(h->fj.join[k]);
+  }
+  if (h->fj.fork) cudaEventDestroy(h->fj.fork);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
 }
@@ -1007,6 +1016,13 @@ int stokes_autotune(stokes_handle* h, int32_t reps) {
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const size_t T = esz(h);
   const bool f32 = h->prec == STOKES_FP32;
+  // every timed launch starts with a cold L2, as inside a cycle (whose
+  // working set is far larger than L2): back-to-back launches would find
+  // part of the factors still cached and favour the wrong configuration
+  if (!h->flush) {
+    h->flush_bytes = size_t(256) << 20;
+    TRY(dalloc(h, reinterpret_cast<char**>(&h->flush), h->flush_bytes));
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1032,12 +1048,17 @@ int stokes_autotune(stokes_handle* h, int32_t reps) {
           if (!configure_bin(dp, cand, b, tp, stages, lv.hfoff, lv.hpptr, T, nsm)) continue;
           bn = cand;
           CK(vanka_apply_bin(dp, b, lv.r, lv.yp, f32, h->st));
-          CK(cudaEventRecord(e0, h->st));
-          for (int q = 0; q < reps; ++q) CK(vanka_apply_bin(dp, b, lv.r, lv.yp, f32, h->st));
-          CK(cudaEventRecord(e1, h->st));
-          CK(cudaEventSynchronize(e1));
           float ms = 0.f;
-          CK(cudaEventElapsedTime(&ms, e0, e1));
+          for (int q = 0; q < reps; ++q) {
+            CK(l2_flush(h->flush, h->flush_bytes, h->st));
+            CK(cudaEventRecord(e0, h->st));
+            CK(vanka_apply_bin(dp, b, lv.r, lv.yp, f32, h->st));
+            CK(cudaEventRecord(e1, h->st));
+            CK(cudaEventSynchronize(e1));
+            float one = 0.f;
+            CK(cudaEventElapsedTime(&one, e0, e1));
+            ms += one;
+          }
           ms /= reps;
           if (best_ms < 0.f || ms < best_ms) {
             best_ms = ms;
@@ -1975,6 +1996,15 @@ int stokes_setup(const stokes_problem* const* probs, int32_t ninstances, const s
       return fail(STOKES_ERR_CUDA, "cudaEventCreate failed");
     }
   }
+  e = cudaEventCreateWithFlags(&h->fj.fork, cudaEventDisableTiming);
+  for (int k = 0; k < kForkMax && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&h->fj.side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fj.join[k], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    stokes_destroy(h);
+    return fail(STOKES_ERR_CUDA, std::string("side streams: ") + cudaGetErrorString(e));
+  }
   e = vanka_prepare_kernels();
   if (e != cudaSuccess) {
     stokes_destroy(h);
@@ -2379,10 +2409,10 @@ static int level_op_impl(stokes_handle* h, int32_t op, int32_t l, const double* 
       if (op == STOKES_OP_VANKA) {
         TRY(in_cast(lv.n, x, lv.ta));
         if (f32) {
-          CK((vanka_apply<float, float>(lv.pat, (float*)lv.ta, (float*)lv.yp, h->st)));
+          CK((vanka_apply<float, float>(lv.pat, (float*)lv.ta, (float*)lv.yp, h->st, &h->fj)));
           CK(vanka_scatter<float>(lv.pat, lv.n, (float*)lv.yp, (float*)lv.tb, 1.0, 0, nullptr, nullptr, nullptr, h->st));
         } else {
-          CK((vanka_apply<double, double>(lv.pat, (double*)lv.ta, (double*)lv.yp, h->st)));
+          CK((vanka_apply<double, double>(lv.pat, (double*)lv.ta, (double*)lv.yp, h->st, &h->fj)));
           CK(vanka_scatter<double>(lv.pat, lv.n, (double*)lv.yp, (double*)lv.tb, 1.0, 0, nullptr, nullptr, nullptr, h->st));
         }
         return out_cast(lv.n, lv.tb, y);

@@ -42,6 +42,15 @@ template <typename TA, typename TX, typename TB, typename TY, typename TACC>
 cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y, int mode,
                  double s0, double s1, const uint8_t* kind, cudaStream_t st);
 
+// Side streams and events that let independent launches of one step run
+// side by side: fork on the main stream, launch on the sides, join back.
+constexpr int kForkMax = 6;
+struct ForkJoin {
+  cudaStream_t side[kForkMax] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kForkMax] = {};
+};
+
 // A bin of patches solved by the bulk-copy kernel: storage patches
 // [start, start + count), all with m in the bin's range.
 constexpr int kTmaBins = 5;
@@ -132,7 +141,7 @@ cudaError_t vanka_tiles_prepare_kernels(int optin);
 // Patch solves of Eqs. vanka_fact1/2 for every patch: yp (patch-major) =
 // K_i^-1 V_i r.
 template <typename T, typename TR>
-cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st);
+cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st, const ForkJoin* fj = nullptr);
 
 // Weighted scatter of Eq. vanka: s_j = sum over the patch slots of DoF j in
 // ascending patch order; mode 0: x_j = omega s_j / cnt_j; mode 1: x_j +=

@@ -488,7 +488,7 @@ __device__ __forceinline__ void group_copy(T* __restrict__ dst, const T* __restr
 constexpr int kNCW = 4;
 
 template <typename T, typename TR, int DIM, int NPM, int LP, int R>
-__global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
+__global__ void __launch_bounds__(32 * (kNCW + 1), sizeof(T) == 4 ? 7 : 4) k_vanka_apply_tma(
     int pstart, int pcount, int ntiles, int tp, int stages, int fac_bytes, int dof_bytes, int rhs_elems, int shared,
     const int4* __restrict__ meta, const int* __restrict__ pptr, const int64_t* __restrict__ foff,
     const int* __restrict__ dof, const int* __restrict__ pdst, const T* __restrict__ fac, const TR* __restrict__ r,
@@ -722,20 +722,6 @@ cudaError_t vanka_apply_bin(const DevPatches& p, int b, const void* r, void* yp,
   return apply_tma_bin<double, double>(p, b, (const double*)r, (double*)yp, st);
 }
 
-template <typename T, typename TR>
-static cudaError_t apply_tma_bins(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
-  for (int b = 0; b < kTmaBins; ++b) {
-    const TmaBin& bn = p.bins[b];
-    if (bn.count == 0) continue;
-    const bool one = bn.max_np <= 1;
-    cudaError_t e;
-    if (p.dim == 2) e = one ? launch_bin_np<T, TR, 2, 1>(p, b, r, yp, st) : launch_bin_np<T, TR, 2, 4>(p, b, r, yp, st);
-    else e = one ? launch_bin_np<T, TR, 3, 1>(p, b, r, yp, st) : launch_bin_np<T, TR, 3, 4>(p, b, r, yp, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
 // Shared-memory bytes of a TMA bin's tile configuration.
 size_t vanka_tma_smem(const DevPatches& p, const TmaBin& bn, size_t elem) {
   (void)p;
@@ -775,17 +761,38 @@ int vanka_tma_bin_of(int m) {
 }
 int vanka_tma_bin_ppw(int b) { return b == 0 ? 5 : (b == 1 ? 3 : (b == 2 ? 2 : 1)); }
 
+// The bins and the tiled patches are independent launches (disjoint patches
+// and outputs).  With side streams they are forked off the main stream and
+// joined back, so the small bins of a coarse level run side by side instead
+// of one tail after another; captured into a graph they become parallel
+// branches.
 template <typename T, typename TR>
-cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st) {
-  if (p.nsmall > 0) {
-    cudaError_t e = apply_tma_bins<T, TR>(p, r, yp, st);
-    if (e != cudaSuccess) return e;
+cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st, const ForkJoin* fj) {
+  int parts[kTmaBins + 1], np = 0;
+  if (p.nsmall > 0)
+    for (int b = 0; b < kTmaBins; ++b)
+      if (p.bins[b].count > 0) parts[np++] = b;
+  if (p.nlarge > 0) parts[np++] = kTmaBins;
+  const bool fork = fj != nullptr && np > 1 && np - 1 <= kForkMax;
+  cudaError_t e = cudaSuccess;
+  if (fork) e = cudaEventRecord(fj->fork, st);
+  for (int k = 0; k < np && e == cudaSuccess; ++k) {
+    cudaStream_t s = st;
+    if (fork && k > 0) {
+      s = fj->side[k - 1];
+      e = cudaStreamWaitEvent(s, fj->fork, 0);
+      if (e != cudaSuccess) break;
+    }
+    e = parts[k] == kTmaBins ? vanka_apply_tiles<T, TR>(p, r, yp, s) : apply_tma_bin<T, TR>(p, parts[k], r, yp, s);
+    if (e == cudaSuccess && fork && k > 0) e = cudaEventRecord(fj->join[k - 1], s);
   }
-  if (p.nlarge > 0) return vanka_apply_tiles<T, TR>(p, r, yp, st);
-  return cudaSuccess;
+  if (fork)
+    for (int k = 1; k < np && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(st, fj->join[k - 1], 0);
+  return e;
 }
-template cudaError_t vanka_apply<float, float>(const DevPatches&, const float*, float*, cudaStream_t);
-template cudaError_t vanka_apply<double, double>(const DevPatches&, const double*, double*, cudaStream_t);
+template cudaError_t vanka_apply<float, float>(const DevPatches&, const float*, float*, cudaStream_t, const ForkJoin*);
+template cudaError_t vanka_apply<double, double>(const DevPatches&, const double*, double*, cudaStream_t,
+                                                 const ForkJoin*);
 
 // Allow every kernel with large dynamic shared memory the device's opt-in
 // maximum once, so launches inside graph capture never need the attribute.
