@@ -393,15 +393,23 @@ def run_gpu(args):
 
 
 def run_profile(args):
-    """Kernel launches for ncu: factorisation, then DC cycles (graph replays)."""
+    """Kernel launches for ncu: factorisation, then DC cycles (graph replays),
+    on C2 (default), C4, or the 3D Taylor-Hood lid-driven cavity on an N^3
+    cube (`cubeN`, a small case of the C4 kernels)."""
     import torch
 
     import paper_2306_06795_gb300 as sd
-    from problems import configs
+    from problems import configs, mesh, stokes
 
-    pr = configs.c2()
+    name = args.profile_problem or "c2"
+    if name == "c2":
+        pr, prm = configs.c2(), configs.TH2D_VANKA
+    elif name == "c4":
+        pr, prm = configs.c4(), configs.TH3D_VANKA
+    else:
+        pr, prm = stokes.build_th(mesh.unit_cube(int(name[4:])), bc="lid"), configs.TH3D_VANKA
     stream = torch.cuda.Stream()
-    h = sd.stokes_setup(pr, dict(configs.TH2D_VANKA, precision=sd.STOKES_FP32), stream=stream.cuda_stream)
+    h = sd.stokes_setup(pr, dict(prm, precision=sd.STOKES_FP32), stream=stream.cuda_stream)
     sd.stokes_factor_patches(h)
     r = torch.tensor(pr.b, dtype=torch.float64, device="cuda")
     z = torch.empty_like(r)
@@ -571,6 +579,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--profile-cycles", type=int, default=0,
                     help="profiling driver: set up, factorise and run this many DC cycles, print nothing")
+    ap.add_argument("--profile-problem", default=None,
+                    help="profiling driver problem: c2 (default), c4, or cubeN (3D lid-driven cavity on an N^3 cube)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling driver: set up, factorise and run one FP32-preconditioned solve")
     ap.add_argument("--ref-iters", type=int, default=34,
@@ -581,7 +591,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.profile_cycles or args.profile_solve:
+    elif args.profile_cycles or args.profile_solve or args.profile_problem:
         run_profile(args)
     elif args.workload == "c5":
         run_gpu_c5(args)

@@ -3,10 +3,11 @@
 // and the deterministic weighted scatter (a7).
 //
 // Patch factor layout (elements of T, block start 16-byte aligned):
-//   nblk packed lower triangles of A_c^-1 (nblk = 1 when all velocity
-//   components share one block, else dim), each m(m+1)/2 entries, row by
-//   row; then U = A^-1 B^T stored seed-major (np columns of dim*m); then
-//   S^-1 (np x np, row-major) with S = -B A^-1 B^T.
+//   nblk blocks A_c^-1 (nblk = 1 when all velocity components share one
+//   block, else dim): for the patches of the bulk-copy bins a packed lower
+//   triangle, m(m+1)/2 entries row by row; for the rest the tiled lower
+//   triangle of tiles.cuh; then U = A^-1 B^T stored seed-major (np columns
+//   of dim*m); then S^-1 (np x np, row-major) with S = -B A^-1 B^T.
 // The patch solve computes, for b = V_i r (Eqs. vanka_fact1/2),
 //   y_u = A^-1 b_u,  y_p = S^-1 (b_p - U^T b_u),  x_u = y_u - U y_p,
 // which is [I U^; 0 I][A^-1 0; B^ S^-1] b with U^ = -U and
