@@ -489,7 +489,7 @@ __device__ __forceinline__ void group_copy(T* __restrict__ dst, const T* __restr
 constexpr int kNCW = 4;
 
 template <typename T, typename TR, int DIM, int NPM, int LP, int R>
-__global__ void __launch_bounds__(32 * (kNCW + 1), sizeof(T) == 4 ? 7 : 4) k_vanka_apply_tma(
+__global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     int pstart, int pcount, int ntiles, int tp, int stages, int fac_bytes, int dof_bytes, int rhs_elems, int shared,
     const int4* __restrict__ meta, const int* __restrict__ pptr, const int64_t* __restrict__ foff,
     const int* __restrict__ dof, const int* __restrict__ pdst, const T* __restrict__ fac, const TR* __restrict__ r,
