@@ -230,6 +230,50 @@ const char* stokes_autotune_report(const stokes_handle* h);
 int stokes_galerkin(const stokes_csr* K, const stokes_csr* P, void* cuda_stream, stokes_csr* C);
 void stokes_csr_free(stokes_csr* C);
 
+/* Further device steps of the smoothed-aggregation setup of Alg. 1 (setup
+ * steps; the solve path does not call them).  Host arrays in; outputs are
+ * host arrays allocated by the library (stokes_csr_free,
+ * stokes_patch_lists_free).  All run on cuda_stream (NULL: the default
+ * stream), return after the copy back, and are deterministic.
+ *
+ * stokes_sa_strength: strength-of-connection pattern S of a square A (Sec.
+ *   3.2): off-diagonal j is strong for row i when |a_ij| > theta
+ *   sqrt(|a_ii| |a_jj|), theta >= 0; values 1, columns sorted.
+ * stokes_sa_tentative: tentative prolongator of aggregates agg[n] (-1 for
+ *   a node outside every aggregate, otherwise 0 .. naggregates-1, every
+ *   aggregate non-empty) with near-null vector B[n]: T (n x naggregates)
+ *   holds B_i / ||B on the aggregate||_2 in column agg_i; Bc[naggregates]
+ *   (caller-allocated) receives the norms, so that T Bc = B on aggregated
+ *   rows.  Norms sum the squares in node order.
+ * stokes_sa_smooth: Jacobi-smoothed prolongator P = T - omega D^-1 A T
+ *   (D the diagonal of A; rows without a nonzero off-diagonal entry get
+ *   D^-1 = 0), each entry t - omega (d_i^-1 (A T)_ij), exact zeros dropped.
+ *   omega is the caller's (4/3 over the spectral radius of D^-1 A in the
+ *   host setup).  STOKES_ERR_INVALID_ARG when a row of A T has more than
+ *   4096 partial products.
+ * stokes_vanka_patches: Vanka patch lists of a Galerkin level (Sec. 3.3.1)
+ *   of K with field offsets field_off[dim + 2] (velocity components of
+ *   equal size, then pressure): patch s holds every velocity node j linked
+ *   to pressure DoF s by max over components |b_sj| > rel_tol times the
+ *   largest of the row, with all dim components (nodes ascending), then
+ *   the seed; layout as stokes_patches, one seed per patch.
+ *   STOKES_ERR_INVALID_ARG when a pressure row has more than 4096
+ *   velocity entries. */
+typedef struct {
+  int32_t npatch;
+  int64_t* ptr;   /* [npatch + 1] */
+  int32_t* dof;   /* [ptr[npatch]] */
+  int32_t* nvel;  /* [npatch * dim] */
+  int32_t* npres; /* [npatch] */
+} stokes_patch_lists;
+int stokes_sa_strength(const stokes_csr* A, double theta, void* cuda_stream, stokes_csr* S);
+int stokes_sa_tentative(int32_t n, const int32_t* agg, int32_t naggregates, const double* B, void* cuda_stream,
+                        stokes_csr* T, double* Bc);
+int stokes_sa_smooth(const stokes_csr* A, const stokes_csr* T, double omega, void* cuda_stream, stokes_csr* P);
+int stokes_vanka_patches(const stokes_csr* K, const int64_t* field_off, int32_t dim, double rel_tol, void* cuda_stream,
+                         stokes_patch_lists* out);
+void stokes_patch_lists_free(stokes_patch_lists* p);
+
 /* Single steps of the cycle on one level, for testing and measurement.
  * All vectors are device FP64 of the sizes stated; the operation runs in
  * the cycle precision unless its name says FP64.

@@ -36,7 +36,8 @@ EXPORTS = ["stokes_setup", "stokes_factor_patches", "stokes_vcycle", "stokes_fgm
            "stokes_fgmres_solve_host", "stokes_level_op", "stokes_num_levels", "stokes_level_size",
            "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_time_kernel",
            "stokes_kernel_launches", "stokes_vanka_noalloc", "stokes_destroy", "stokes_autotune",
-           "stokes_autotune_report", "stokes_galerkin", "stokes_csr_free",
+           "stokes_autotune_report", "stokes_galerkin", "stokes_csr_free", "stokes_sa_strength",
+           "stokes_sa_tentative", "stokes_sa_smooth", "stokes_vanka_patches", "stokes_patch_lists_free",
            "stokes_status_string", "stokes_last_error"]
 
 
@@ -111,6 +112,18 @@ def _load():
     lib.stokes_galerkin.argtypes = [C.POINTER(stokes_csr), C.POINTER(stokes_csr), vp, C.POINTER(stokes_csr)]
     lib.stokes_galerkin.restype = C.c_int
     lib.stokes_csr_free.argtypes = [C.POINTER(stokes_csr)]
+    lib.stokes_sa_strength.argtypes = [C.POINTER(stokes_csr), C.c_double, vp, C.POINTER(stokes_csr)]
+    lib.stokes_sa_strength.restype = C.c_int
+    lib.stokes_sa_tentative.argtypes = [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double), vp,
+                                        C.POINTER(stokes_csr), C.POINTER(C.c_double)]
+    lib.stokes_sa_tentative.restype = C.c_int
+    lib.stokes_sa_smooth.argtypes = [C.POINTER(stokes_csr), C.POINTER(stokes_csr), C.c_double, vp,
+                                     C.POINTER(stokes_csr)]
+    lib.stokes_sa_smooth.restype = C.c_int
+    lib.stokes_vanka_patches.argtypes = [C.POINTER(stokes_csr), C.POINTER(C.c_int64), C.c_int32, C.c_double, vp,
+                                         C.POINTER(stokes_patches)]
+    lib.stokes_vanka_patches.restype = C.c_int
+    lib.stokes_patch_lists_free.argtypes = [C.POINTER(stokes_patches)]
     lib.stokes_autotune.argtypes = [vp, C.c_int32]
     lib.stokes_autotune.restype = C.c_int
     lib.stokes_autotune_report.argtypes = [vp]
@@ -323,15 +336,9 @@ def stokes_fgmres_solve_host(h, b, x, rtol=1e-8, restart=30, maxit=1000):
     return rc, [(i.iters, i.status, i.true_relres) for i in info]
 
 
-def stokes_galerkin(K, P, stream=None):
-    """P^T K P on the device (FP64); K, P: scipy sparse matrices; returns a scipy CSR."""
+def _csr_out(out):
+    """Copy a library-allocated CSR into a scipy CSR and release it."""
     import scipy.sparse as sp
-    keep = _Keep()
-    k = _csr(keep, K)
-    p = _csr(keep, P)
-    out = stokes_csr()
-    _check(lib.stokes_galerkin(C.byref(k), C.byref(p), C.c_void_p(stream) if stream else None, C.byref(out)),
-           "stokes_galerkin")
     try:
         n, nnz = out.nrows, out.nnz
         rp = np.ctypeslib.as_array(out.rowptr, shape=(n + 1,)).copy()
@@ -340,6 +347,75 @@ def stokes_galerkin(K, P, stream=None):
     finally:
         lib.stokes_csr_free(C.byref(out))
     return sp.csr_matrix((va, ci, rp), shape=(out.nrows, out.ncols))
+
+
+def _stream(stream):
+    return C.c_void_p(stream) if stream else None
+
+
+def stokes_galerkin(K, P, stream=None):
+    """P^T K P on the device (FP64); K, P: scipy sparse matrices; returns a scipy CSR."""
+    keep = _Keep()
+    k = _csr(keep, K)
+    p = _csr(keep, P)
+    out = stokes_csr()
+    _check(lib.stokes_galerkin(C.byref(k), C.byref(p), _stream(stream), C.byref(out)), "stokes_galerkin")
+    return _csr_out(out)
+
+
+def stokes_sa_strength(A, theta=0.0, stream=None):
+    """Strength-of-connection pattern of A on the device (scipy CSR, values 1)."""
+    keep = _Keep()
+    a = _csr(keep, A)
+    out = stokes_csr()
+    _check(lib.stokes_sa_strength(C.byref(a), float(theta), _stream(stream), C.byref(out)), "stokes_sa_strength")
+    return _csr_out(out)
+
+
+def stokes_sa_tentative(agg, naggregates, B, stream=None):
+    """Tentative prolongator of the aggregates agg (-1: none) with near-null
+    vector B on the device; returns (T as scipy CSR, aggregate norms Bc)."""
+    agg = np.ascontiguousarray(agg, dtype=np.int32)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    Bc = np.zeros(max(int(naggregates), 1))
+    out = stokes_csr()
+    _check(lib.stokes_sa_tentative(agg.size, agg.ctypes.data_as(C.POINTER(C.c_int32)), int(naggregates),
+                                   B.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream), C.byref(out),
+                                   Bc.ctypes.data_as(C.POINTER(C.c_double))), "stokes_sa_tentative")
+    return _csr_out(out), Bc[: int(naggregates)]
+
+
+def stokes_sa_smooth(A, T, omega, stream=None):
+    """Jacobi-smoothed prolongator T - omega D^-1 A T on the device (scipy CSR)."""
+    keep = _Keep()
+    a = _csr(keep, A)
+    t = _csr(keep, T)
+    out = stokes_csr()
+    _check(lib.stokes_sa_smooth(C.byref(a), C.byref(t), float(omega), _stream(stream), C.byref(out)),
+           "stokes_sa_smooth")
+    return _csr_out(out)
+
+
+def stokes_vanka_patches(K, field_off, dim, rel_tol=1e-14, stream=None):
+    """Vanka patch lists of a Galerkin level on the device; returns
+    (ptr int64, dof int32, nvel int32 (npatch, dim), npres int32)."""
+    keep = _Keep()
+    k = _csr(keep, K)
+    off = np.ascontiguousarray(field_off, dtype=np.int64)
+    out = stokes_patches()
+    _check(lib.stokes_vanka_patches(C.byref(k), off.ctypes.data_as(C.POINTER(C.c_int64)), int(dim), float(rel_tol),
+                                    _stream(stream), C.byref(out)), "stokes_vanka_patches")
+    try:
+        npatch = out.npatch
+        ptr = np.ctypeslib.as_array(out.ptr, shape=(npatch + 1,)).copy()
+        nd = int(ptr[-1])
+        dof = np.ctypeslib.as_array(out.dof, shape=(nd,)).copy() if nd else np.zeros(0, np.int32)
+        nvel = (np.ctypeslib.as_array(out.nvel, shape=(npatch * dim,)).copy().reshape(npatch, dim) if npatch
+                else np.zeros((0, dim), np.int32))
+        npres = np.ctypeslib.as_array(out.npres, shape=(npatch,)).copy() if npatch else np.zeros(0, np.int32)
+    finally:
+        lib.stokes_patch_lists_free(C.byref(out))
+    return ptr, dof, nvel, npres
 
 
 def stokes_autotune(h, reps=5):

@@ -1134,6 +1134,127 @@ void stokes_csr_free(stokes_csr* C) {
   C->nnz = 0;
 }
 
+// shared tail of the setup entry points: a failed CUDA call, or a filled CSR
+static int setup_csr_out(cudaError_t e, const char* what, int32_t nr, int32_t nc, int64_t nnz, int64_t* rp, int* col,
+                         double* val, stokes_csr* out) {
+  if (e != cudaSuccess) {
+    delete[] rp;
+    delete[] col;
+    delete[] val;
+    return fail(e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  out->nrows = nr;
+  out->ncols = nc;
+  out->nnz = nnz;
+  out->rowptr = rp;
+  out->col = col;
+  out->val = val;
+  return STOKES_OK;
+}
+
+int stokes_sa_strength(const stokes_csr* A, double theta, void* cuda_stream, stokes_csr* S) {
+  if (!A || !S) return fail(STOKES_ERR_INVALID_ARG, "null argument");
+  TRY(check_csr(A, "strength A"));
+  if (A->nrows != A->ncols || !(theta >= 0.0)) return fail(STOKES_ERR_INVALID_ARG, "strength: A square, theta >= 0");
+  std::vector<int> col(A->col, A->col + A->nnz);
+  int64_t* rp = nullptr;
+  int* c = nullptr;
+  double* v = nullptr;
+  int64_t nnz = 0;
+  cudaError_t e = sa_strength(A->nrows, A->rowptr, col.data(), A->val, theta,
+                              reinterpret_cast<cudaStream_t>(cuda_stream), &rp, &c, &v, &nnz);
+  return setup_csr_out(e, "strength", A->nrows, A->nrows, nnz, rp, c, v, S);
+}
+
+int stokes_sa_tentative(int32_t n, const int32_t* agg, int32_t naggregates, const double* B, void* cuda_stream,
+                        stokes_csr* T, double* Bc) {
+  if (n < 0 || naggregates < 0 || (n > 0 && (!agg || !B)) || !T || (naggregates > 0 && !Bc))
+    return fail(STOKES_ERR_INVALID_ARG, "tentative: bad arguments");
+  std::vector<int> present(naggregates, 0);
+  for (int i = 0; i < n; ++i) {
+    if (agg[i] < -1 || agg[i] >= naggregates) return fail(STOKES_ERR_INVALID_ARG, "tentative: aggregate out of range");
+    if (agg[i] >= 0) present[agg[i]] = 1;
+  }
+  for (int a = 0; a < naggregates; ++a)
+    if (!present[a]) return fail(STOKES_ERR_INVALID_ARG, "tentative: empty aggregate");
+  int64_t* rp = nullptr;
+  int* c = nullptr;
+  double* v = nullptr;
+  int64_t nnz = 0;
+  cudaError_t e = sa_tentative(n, agg, naggregates, B, reinterpret_cast<cudaStream_t>(cuda_stream), &rp, &c, &v, &nnz,
+                               Bc);
+  return setup_csr_out(e, "tentative", n, naggregates, nnz, rp, c, v, T);
+}
+
+int stokes_sa_smooth(const stokes_csr* A, const stokes_csr* T, double omega, void* cuda_stream, stokes_csr* P) {
+  if (!A || !T || !P) return fail(STOKES_ERR_INVALID_ARG, "null argument");
+  TRY(check_csr(A, "smooth A"));
+  TRY(check_csr(T, "smooth T"));
+  if (A->nrows != A->ncols || T->nrows != A->nrows)
+    return fail(STOKES_ERR_INVALID_ARG, "smooth: A must be square and T must have A's rows");
+  std::vector<int> acol(A->col, A->col + A->nnz), tcol(T->col, T->col + T->nnz);
+  int status = 0;
+  int64_t* rp = nullptr;
+  int* c = nullptr;
+  double* v = nullptr;
+  int64_t nnz = 0;
+  cudaError_t e = sa_smooth(A->nrows, A->rowptr, acol.data(), A->val, T->ncols, T->rowptr, tcol.data(), T->val, omega,
+                            reinterpret_cast<cudaStream_t>(cuda_stream), &status, &rp, &c, &v, &nnz);
+  if (e == cudaSuccess && status) return fail(STOKES_ERR_INVALID_ARG, "smooth: a row has more than 4096 products");
+  return setup_csr_out(e, "smooth", A->nrows, T->ncols, nnz, rp, c, v, P);
+}
+
+int stokes_vanka_patches(const stokes_csr* K, const int64_t* field_off, int32_t dim, double rel_tol, void* cuda_stream,
+                         stokes_patch_lists* out) {
+  if (!K || !field_off || !out || (dim != 2 && dim != 3) || !(rel_tol >= 0.0))
+    return fail(STOKES_ERR_INVALID_ARG, "vanka_patches: bad arguments");
+  TRY(check_csr(K, "vanka_patches K"));
+  if (K->nrows != K->ncols || field_off[0] != 0 || field_off[dim + 1] != K->nrows)
+    return fail(STOKES_ERR_INVALID_ARG, "vanka_patches: field offsets do not span K");
+  for (int c = 0; c <= dim; ++c)
+    if (field_off[c + 1] < field_off[c]) return fail(STOKES_ERR_INVALID_ARG, "vanka_patches: offsets decrease");
+  for (int c = 1; c < dim; ++c)
+    if (field_off[c + 1] - field_off[c] != field_off[1] - field_off[0])
+      return fail(STOKES_ERR_INVALID_ARG, "vanka_patches: velocity components of different sizes");
+  std::vector<int> col(K->col, K->col + K->nnz);
+  int status = 0, np = 0;
+  int64_t* ptr = nullptr;
+  int *dof = nullptr, *nvel = nullptr, *npres = nullptr;
+  cudaError_t e = vanka_patch_lists(K->nrows, K->rowptr, col.data(), K->val, field_off, dim, rel_tol,
+                                    reinterpret_cast<cudaStream_t>(cuda_stream), &status, &np, &ptr, &dof, &nvel,
+                                    &npres);
+  if (e != cudaSuccess || status) {
+    delete[] ptr;
+    delete[] dof;
+    delete[] nvel;
+    delete[] npres;
+    if (e != cudaSuccess)
+      return fail(e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA,
+                  std::string("vanka_patches: ") + cudaGetErrorString(e));
+    return fail(STOKES_ERR_INVALID_ARG, "vanka_patches: a pressure row has more than 4096 velocity entries");
+  }
+  out->npatch = np;
+  out->ptr = ptr;
+  out->dof = dof;
+  out->nvel = nvel;
+  out->npres = npres;
+  return STOKES_OK;
+}
+
+void stokes_patch_lists_free(stokes_patch_lists* p) {
+  if (!p) return;
+  delete[] p->ptr;
+  delete[] p->dof;
+  delete[] p->nvel;
+  delete[] p->npres;
+  p->ptr = nullptr;
+  p->dof = nullptr;
+  p->nvel = nullptr;
+  p->npres = nullptr;
+  p->npatch = 0;
+}
+
 int stokes_num_levels(const stokes_handle* h) { return h ? h->L : 0; }
 int64_t stokes_kernel_launches(const stokes_handle* h) { return h ? h->launches : 0; }
 int64_t stokes_level_size(const stokes_handle* h, int32_t l) {

@@ -211,6 +211,18 @@ cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, con
 cudaError_t galerkin_rap(int n, const int64_t* krp, const int* kcol, const double* kval, int nc, const int64_t* prp,
                          const int* pcol, const double* pval, cudaStream_t st, int* status, int64_t** crp,
                          int** ccol, double** cval, int64_t* cnnz);
+// Further device steps of the AMG setup (Alg. 1): host arrays in, host arrays
+// out (allocated with new[]).
+cudaError_t sa_strength(int n, const int64_t* rp, const int* col, const double* val, double theta, cudaStream_t st,
+                        int64_t** srp, int** scol, double** sval, int64_t* snnz);
+cudaError_t sa_tentative(int n, const int* agg, int na, const double* B, cudaStream_t st, int64_t** trp, int** tcol,
+                         double** tval, int64_t* tnnz, double* Bc);
+cudaError_t sa_smooth(int n, const int64_t* arp, const int* acol, const double* aval, int nc, const int64_t* trp,
+                      const int* tcol, const double* tval, double omega, cudaStream_t st, int* status,
+                      int64_t** prp, int** pcol, double** pval, int64_t* pnnz);
+cudaError_t vanka_patch_lists(int n, const int64_t* rp, const int* col, const double* val, const int64_t* hoff, int dim,
+                              double rel_tol, cudaStream_t st, int* status, int* npatch, int64_t** hptr, int** hdof,
+                              int** hnvel, int** hnpres);
 
 // Krylov-wrapped relaxation (krylov.cu).  Rows of a level cut into chunks
 // that never straddle an instance; sbeg/send: chunk range of each instance.
