@@ -60,10 +60,26 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        self.skip = 0
+        if self.proc is not None:
+            # wait (at most 5 s) until sampling runs, then count only the
+            # samples taken from here on, i.e. inside the timed region
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self._lines() == 0 and self.proc.poll() is None:
+                time.sleep(0.02)
+            self.skip = self._lines()
+
+    def _lines(self):
+        try:
+            self.f.flush()
+            with open(self.path) as g:
+                return sum(1 for _ in g)
+        except Exception:
+            return 0
 
     def stop(self):
         if self.proc is None:
@@ -76,7 +92,9 @@ class ClockSampler:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for k_line, line in enumerate(open(self.path)):
+            if k_line < self.skip:
+                continue
             p = [x.strip() for x in line.split(",")]
             if len(p) < 8:
                 continue
@@ -573,7 +591,7 @@ def run_gpu_configs(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
