@@ -16,6 +16,11 @@ sharing no code with the CUDA path:
   Galerkin V-cycle on the P1isoP2/P1 hierarchy (Eq. TG-operator), with an
   exact bordered solve on the coarsest level;
 * ``krylov`` - restarted flexible GMRES with right preconditioning (Sec. 4);
+  ``cycle.krylov_relax`` wraps a relaxation in a few such steps (Sec. 3.3.1);
+* ``btp``    - the block-triangular comparison preconditioner (Sec. 4): SA
+  V-cycles on A and on the scaled pressure mass matrix (or its exact
+  block-diagonal inverse);
+* ``search`` - the brute-force search of relaxation weights (Sec. 4);
 * ``direct`` - sparse direct solves of the full Stokes system, used by the
   pins of the discretisation.
 
