@@ -1,0 +1,46 @@
+"""Host logic of bench.py that needs no GPU: the clock record counts only
+the nvidia-smi samples taken inside the timed region and reports every
+throttle reason seen there."""
+import os
+
+import bench
+
+
+class _Proc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _sampler(path, lines, skip):
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    c = bench.ClockSampler.__new__(bench.ClockSampler)
+    c.path = str(path)
+    c.f = open(os.devnull, "w")
+    c.proc = _Proc()
+    c.skip = skip
+    return c
+
+
+def test_samples_before_the_timed_region_are_skipped(tmp_path):
+    idle = "345, 2070, 120.5, 0x1, Not Active, Not Active, Not Active, Not Active"
+    busy = "2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    capped = "1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active"
+    rec = _sampler(tmp_path / "c.csv", [idle, busy, busy, capped], skip=1).stop()
+    assert rec["samples"] == 3
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"]
+
+
+def test_thermal_slowdown_is_reported(tmp_path):
+    hot = "1500, 2070, 1000.0, 0x40, Not Active, Active, Not Active, Not Active"
+    rec = _sampler(tmp_path / "c.csv", [hot, hot], skip=0).stop()
+    assert rec["reasons"] == ["hw_thermal_slowdown"] and rec["samples"] == 2
+
+
+def test_no_samples(tmp_path):
+    rec = _sampler(tmp_path / "c.csv", ["garbage"], skip=0).stop()
+    assert rec["reasons"] == ["no samples"]
