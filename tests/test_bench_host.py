@@ -44,3 +44,13 @@ def test_thermal_slowdown_is_reported(tmp_path):
 def test_no_samples(tmp_path):
     rec = _sampler(tmp_path / "c.csv", ["garbage"], skip=0).stop()
     assert rec["reasons"] == ["no samples"]
+
+
+def test_sampler_without_nvidia_smi_reports_unavailable():
+    """Constructing the sampler never fails; without nvidia-smi (this
+    container) the record says so."""
+    import shutil
+    c = bench.ClockSampler(0)
+    rec = c.stop()
+    if shutil.which("nvidia-smi") is None:
+        assert rec["reasons"] == ["nvidia-smi unavailable"]
