@@ -51,3 +51,25 @@ def test_setup_without_gpu_fails_loudly(sd):
     with pytest.raises(sd.StokesError) as ei:
         sd.stokes_setup(pr, dict(precision=sd.STOKES_FP64), stream=0)
     assert ei.value.code == sd.STOKES_ERR_CUDA
+
+
+def test_setup_steps_validate_arguments_on_the_host(sd):
+    """The device setup steps reject bad arguments before any device work,
+    so these calls fail with STOKES_ERR_INVALID_ARG with or without a GPU."""
+    import numpy as np
+    import scipy.sparse as sp
+    A = sp.identity(4, format="csr")
+    cases = [
+        lambda: sd.stokes_sa_strength(A, -1.0),                                  # theta < 0
+        lambda: sd.stokes_sa_strength(sp.csr_matrix(np.ones((3, 4))), 0.0),      # not square
+        lambda: sd.stokes_sa_tentative(np.array([0, 0, 2, -1]), 2, np.ones(4)),  # aggregate out of range
+        lambda: sd.stokes_sa_tentative(np.array([0, 0, 0, -1]), 2, np.ones(4)),  # empty aggregate
+        lambda: sd.stokes_sa_smooth(A, sp.csr_matrix(np.ones((3, 2))), 0.5),     # T has other rows
+        lambda: sd.stokes_vanka_patches(A, np.array([0, 1, 2, 5]), 2),           # offsets do not span K
+        lambda: sd.stokes_vanka_patches(A, np.array([0, 1, 3, 4]), 2),           # unequal components
+        lambda: sd.stokes_vanka_patches(A, np.array([0, 1, 2, 3, 4]), 4),        # dim not 2 or 3
+    ]
+    for k, call in enumerate(cases):
+        with pytest.raises(sd.StokesError) as ei:
+            call()
+        assert ei.value.code == sd.STOKES_ERR_INVALID_ARG, k
