@@ -32,6 +32,10 @@ STOKES_KERNEL_VANKA_APPLY, STOKES_KERNEL_SCATTER, STOKES_KERNEL_SPMV, STOKES_KER
 (STOKES_OP_SPMV, STOKES_OP_SPMV_F64, STOKES_OP_RESIDUAL, STOKES_OP_RESTRICT,
  STOKES_OP_PROLONG, STOKES_OP_VANKA, STOKES_OP_RELAX, STOKES_OP_COARSE) = range(8)
 
+# Chebyshev degrees of the DLSC stages (momentum, continuity, pressure
+# correction) by dimension, Table lsd_dgs_config
+DLSC_DEGREES = {2: (3, 3, 6), 3: (4, 4, 16)}
+
 EXPORTS = ["stokes_setup", "stokes_factor_patches", "stokes_vcycle", "stokes_fgmres_solve",
            "stokes_fgmres_solve_host", "stokes_level_op", "stokes_num_levels", "stokes_level_size",
            "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_time_kernel",
@@ -242,10 +246,11 @@ def _problem(keep, pr):
     return p
 
 
-def _params(keep, prm, nlevels):
+def _params(keep, prm, nlevels, dim=2):
     """prm: dict with schedule, nu1, nu2, eta_u, eta_p, omega (scalar or per
-    level; omega0 overrides level 0), relax (list or None), cheb_deg,
-    dlsc_sweeps, mcg_deg, precision."""
+    level; omega0 overrides level 0), relax (list or None), cheb_deg (default:
+    the DLSC degrees of the paper's table for the dimension, (3, 3, 6) in 2D
+    and (4, 4, 16) in 3D), dlsc_sweeps, mcg_deg, precision."""
     s = stokes_params()
     s.schedule = int(prm.get("schedule", 0))
     s.nu1 = int(prm.get("nu1", 1))
@@ -262,7 +267,7 @@ def _params(keep, prm, nlevels):
     if prm.get("relax") is not None:
         rl = keep.arr(prm["relax"], np.int32)
         s.relax = _p(rl, C.c_int32)
-    cd = prm.get("cheb_deg", (3, 3, 6))
+    cd = prm.get("cheb_deg", DLSC_DEGREES[dim])
     s.cheb_deg[0], s.cheb_deg[1], s.cheb_deg[2] = (int(v) for v in cd)
     s.dlsc_sweeps = int(prm.get("dlsc_sweeps", 2))
     s.mcg_deg = int(prm.get("mcg_deg", 32))
@@ -300,7 +305,7 @@ def stokes_setup(problems, params, stream=None):
     cps = [_problem(keep, pr) for pr in problems]
     arr = (C.POINTER(stokes_problem) * len(cps))(*[C.pointer(p) for p in cps])
     nl = max(len(pr.K) for pr in problems)
-    prm = _params(keep, params, nl)
+    prm = _params(keep, params, nl, problems[0].dim)
     out = C.c_void_p()
     if stream is None:
         import torch

@@ -12,7 +12,8 @@ def oracle_params(pr, prm):
         omega[0] = prm["omega0"]
     return cycle.Params(schedule=prm.get("schedule", 0), nu1=prm.get("nu1", 1), nu2=prm.get("nu2", 1),
                         eta_u=prm.get("eta_u", 1.0), eta_p=prm.get("eta_p", 1.0), omega=omega,
-                        relax=prm.get("relax"), cheb_deg=prm.get("cheb_deg", (3, 3, 6)),
+                        relax=prm.get("relax"),
+                        cheb_deg=prm.get("cheb_deg", (3, 3, 6) if pr.dim == 2 else (4, 4, 16)),
                         mcg_deg=prm.get("mcg_deg", 32), dlsc_sweeps=prm.get("dlsc_sweeps", 2))
 
 
