@@ -188,6 +188,38 @@ def test_stationary_dc_iteration_contracts(c1):
     assert factor < 0.9, factor
 
 
+def test_fgmres_minimises_over_the_preconditioned_vectors():
+    """Flexible GMRES (Sec. 4): with a preconditioner that changes at every
+    step, the m-step iterate is x0 + Z y with Z the preconditioner's outputs,
+    and its residual is the least-squares minimum of ||b - K (x0 + Z y)||
+    over all y (computed here independently of the Arnoldi recurrences)."""
+    rng = np.random.default_rng(41)
+    n, m = 40, 7
+    A = rng.standard_normal((n, n)) + 6 * np.eye(n)
+    b = rng.standard_normal(n)
+    x0 = rng.standard_normal(n)
+    Z = []
+
+    def precond(v):
+        # a different, fixed-seed linear map per call: z = (I + 0.3 R_k) v
+        R = np.random.default_rng(100 + len(Z)).standard_normal((n, n)) / np.sqrt(n)
+        z = v + 0.3 * (R @ v)
+        Z.append(z)
+        return z
+
+    x, its, rr = krylov.fgmres(A, b, precond, x0=x0, rtol=1e-30, restart=m + 5, maxit=m)
+    assert its == m and len(Z) == m
+    Zm = np.array(Z).T
+    y, *_ = np.linalg.lstsq(A @ Zm, b - A @ x0, rcond=None)
+    best = np.linalg.norm(b - A @ (x0 + Zm @ y))
+    assert abs(np.linalg.norm(b - A @ x) - best) <= 1e-10 * np.linalg.norm(b)
+    # the correction lies in span(Z)
+    c, *_ = np.linalg.lstsq(Zm, x - x0, rcond=None)
+    assert np.linalg.norm(Zm @ c - (x - x0)) <= 1e-10 * np.linalg.norm(x - x0)
+    # a flipped sign in the update (x0 - Z y) would not minimise
+    assert np.linalg.norm(b - A @ (x0 - Zm @ y)) > 1.5 * best
+
+
 def test_fgmres_dc_solves_c1_to_tolerance(c1):
     par = cycle.Params(**{k: v for k, v in configs.TH2D_VANKA.items() if k != "omega"},
                        omega=[configs.TH2D_VANKA["omega"]] * (c1.nlevels - 1))
