@@ -66,6 +66,21 @@ def test_block_factorisation_equals_dense_lu(c1):
     assert worst < 1e-12
 
 
+def test_sampled_vanka_equals_the_full_application(c1):
+    """The sampled Vanka application used for full-size checks (only the
+    patches holding the sampled DoFs) gives the full Eq. vanka application
+    at those DoFs, on every level."""
+    o = cycle.Oracle(c1, cycle.Params(omega=[1.0] * (c1.nlevels - 1)))
+    rng = np.random.default_rng(17)
+    for l in range(c1.nlevels - 1):
+        n = c1.K[l].shape[0]
+        r = rng.standard_normal(n)
+        full = o.vanka[l].apply(r)
+        dofs = np.sort(rng.choice(n, size=min(40, n), replace=False))
+        ref = vanka.sampled_apply(c1.K[l], c1.patches[l], r, dofs)
+        assert np.abs(ref - full[dofs]).max() <= 1e-12 * np.abs(full).max()
+
+
 def test_single_patch_is_a_direct_solve(c1):
     """One patch holding every free DoF except one pressure DoF (which fixes
     the pressure constant): Vanka with W = 1 is an exact solve."""
