@@ -81,6 +81,21 @@ def test_sampled_vanka_equals_the_full_application(c1):
         assert np.abs(ref - full[dofs]).max() <= 1e-12 * np.abs(full).max()
 
 
+def test_bordered_coarsest_solve(c1):
+    """The coarsest solve of the bordered system [K_L n; n^T 0] (n the coarse
+    pressure null vector, K_L n = 0): x solves K_L x = b - (n.b / n.n) n, the
+    projection of b on the range, and is orthogonal to n."""
+    o = cycle.Oracle(c1, cycle.Params(omega=[1.0] * (c1.nlevels - 1)))
+    KL = c1.K[-1].toarray()
+    n = c1.coarse_null
+    assert np.abs(KL @ n).max() <= 1e-10 * np.abs(KL).max() * np.abs(n).max()
+    b = np.random.default_rng(23).standard_normal(KL.shape[0])
+    x = o.coarse_solve(b)
+    proj = b - (n @ b) / (n @ n) * n
+    assert np.linalg.norm(KL @ x - proj) <= 1e-10 * np.linalg.norm(b)
+    assert abs(n @ x) <= 1e-10 * np.linalg.norm(x) * np.linalg.norm(n)
+
+
 def test_single_patch_is_a_direct_solve(c1):
     """One patch holding every free DoF except one pressure DoF (which fixes
     the pressure constant): Vanka with W = 1 is an exact solve."""
