@@ -1,9 +1,12 @@
 """Pins of the FP64 oracle against facts fixed by the paper and by linear
 algebra: the partition of unity of Eq. vanka, the block factorisation of
 Eqs. vanka_fact1/2 against dense LU on every patch, a single all-covering
-patch against a direct solve, the two-level form of Eq. TG-operator-full as
-a dense operator product, the Chebyshev closed form, FGMRES special cases,
-and convergence of the stationary DC iteration."""
+patch against a direct solve, the sampled Vanka application against the full
+one, the bordered coarsest solve against its projection property, the
+two-level form of Eq. TG-operator-full as a dense operator product, the
+Chebyshev closed form, FGMRES special cases and its minimisation over the
+preconditioned vectors, Krylov-wrapped relaxation, DLSC, and convergence of
+the stationary DC iteration."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
