@@ -35,9 +35,22 @@ WORKLOAD = ("2D Taylor-Hood P2/P1 Stokes, unit square 256x256 squares split by t
             "manufactured u = curl(sin^2(pi x) sin^2(pi y)), p = cos(pi x) cos(pi y); FP32 DC-all V(1,1) "
             "additive-Vanka cycle on the P1isoP2/P1 SA hierarchy, FGMRES(30) to 1e-8 true relative residual")
 METRIC = "Stokes solves/s to 1e-8 rel-res (FP32 DC-AMG preconditioned FGMRES)"
-# dram__bytes_read.sum + dram__bytes_write.sum of one level-0 FP32 apply launch, from the ncu
-# capture summarised in profiles/vanka_apply_tma_c2_level0.md (set to None when the kernel changes)
-APPLY_L0_DRAM_BYTES = 87.55e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one level-0 FP32 apply launch from an ncu capture,
+# keyed by the SHA-256 of the kernel's sources at capture time: when the sources differ the figure
+# no longer describes the kernel and the bench line reports traffic as null
+APPLY_L0_TRAFFIC = {"dram_bytes": 87.55e6, "sources": ["vanka.cu", "tma.cuh", "common.cuh"],
+                    "sha256": None}
+
+
+def apply_traffic():
+    """The recorded DRAM bytes of the roofline kernel if its sources are
+    unchanged since the capture, else None."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in APPLY_L0_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2306_06795_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return APPLY_L0_TRAFFIC["dram_bytes"] if hsh.hexdigest() == APPLY_L0_TRAFFIC["sha256"] else None
 
 
 def dist_env():
@@ -386,7 +399,7 @@ def run_gpu(args):
                    "fp32_frac_of_measured_hbm": vc[sd.STOKES_FP32][1] / vc[sd.STOKES_FP32][0] / 1e6 / peak},
         "roofline": {"kernel": "k_vanka_apply_tma (level 0, FP32, 66,049 patches)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_kind, "traffic": APPLY_L0_DRAM_BYTES,
+                     "peak_source": peak_kind, "traffic": apply_traffic(),
                      "bytes_per_launch": kbytes, "avg_launch_ms": kms},
         "krylov_relax": {"relax": "Krylov-wrapped Vanka (Sec. 3.3.1): 2 FGMRES steps x 1 undamped sweep per level, "
                                   "eta 1, FP32 cycle",

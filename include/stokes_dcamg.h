@@ -345,8 +345,20 @@ int64_t stokes_kernel_launches(const stokes_handle* h);
  * part must start at zero; calls that overlap on the GPU (from several
  * threads or streams) race on it.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Queued on the handle's stream, asynchronous. */
+ * before any stream capture.  The work is queued on the handle's stream;
+ * before returning, the call waits for it and reads the level's bulk-copy
+ * error flag: a pipeline wait that ran out (the patch solutions are then
+ * incomplete) returns STOKES_ERR_CUDA, and y must not be used. */
 int stokes_vanka_noalloc(stokes_handle* h, int32_t level, const double* x_dev, double* y_dev);
+
+/* Test support for the error path (the paper has no counterpart): sets the
+ * device error flag of level l's bulk-copy Vanka apply as a bounded wait
+ * that ran out would, without running any kernel.  Every later call that
+ * checks the flags (stokes_level_op, stokes_fgmres_solve,
+ * stokes_vanka_noalloc) then returns STOKES_ERR_CUDA.  The flag is never
+ * cleared: use a handle made for the test.  Synchronises the handle's
+ * stream.  STOKES_ERR_INVALID_ARG for a level without patches. */
+int stokes_inject_pipeline_error(stokes_handle* h, int32_t level);
 
 /* Release all device memory of the handle (NULL is allowed). */
 void stokes_destroy(stokes_handle* h);

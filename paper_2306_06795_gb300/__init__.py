@@ -39,8 +39,8 @@ DLSC_DEGREES = {2: (3, 3, 6), 3: (4, 4, 16)}
 EXPORTS = ["stokes_setup", "stokes_factor_patches", "stokes_vcycle", "stokes_fgmres_solve",
            "stokes_fgmres_solve_host", "stokes_level_op", "stokes_num_levels", "stokes_level_size",
            "stokes_cycle_bytes", "stokes_sweep_factor_bytes", "stokes_time_kernel",
-           "stokes_kernel_launches", "stokes_vanka_noalloc", "stokes_destroy", "stokes_autotune",
-           "stokes_autotune_report", "stokes_galerkin", "stokes_csr_free", "stokes_sa_strength",
+           "stokes_kernel_launches", "stokes_vanka_noalloc", "stokes_inject_pipeline_error", "stokes_destroy",
+           "stokes_autotune", "stokes_autotune_report", "stokes_galerkin", "stokes_csr_free", "stokes_sa_strength",
            "stokes_sa_tentative", "stokes_sa_smooth", "stokes_vanka_patches", "stokes_patch_lists_free",
            "stokes_status_string", "stokes_last_error"]
 
@@ -112,6 +112,7 @@ def _load():
     lib.stokes_kernel_launches.argtypes = [vp]
     lib.stokes_kernel_launches.restype = C.c_int64
     lib.stokes_vanka_noalloc.argtypes = [vp, C.c_int32, vp, vp]
+    lib.stokes_inject_pipeline_error.argtypes = [vp, C.c_int32]
     lib.stokes_destroy.argtypes = [vp]
     lib.stokes_galerkin.argtypes = [C.POINTER(stokes_csr), C.POINTER(stokes_csr), vp, C.POINTER(stokes_csr)]
     lib.stokes_galerkin.restype = C.c_int
@@ -278,10 +279,21 @@ def _params(keep, prm, nlevels, dim=2):
 
 
 # ---------------------------------------------------------------- API
-def _dptr(t):
+def _dptr(t, n=None, what="vector"):
+    """Device address of a contiguous FP64 CUDA tensor of n entries (n=None:
+    any size).  Raises instead of passing the library a pointer it would read
+    or write out of bounds."""
     if t is None:
         return None
-    assert t.is_cuda and t.is_contiguous(), "device FP64 contiguous tensor expected"
+    if not getattr(t, "is_cuda", False):
+        raise TypeError(f"{what}: a CUDA tensor is expected")
+    import torch
+    if t.dtype != torch.float64:
+        raise TypeError(f"{what}: FP64 expected, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: a contiguous tensor is expected")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what}: {n} entries expected, got {t.numel()}")
     return C.c_void_p(t.data_ptr())
 
 
@@ -321,19 +333,24 @@ def stokes_factor_patches(h):
 
 
 def stokes_vcycle(h, r, z):
-    _check(lib.stokes_vcycle(h.ptr, _dptr(r), _dptr(z)), "stokes_vcycle")
+    n = stokes_level_size(h, 0)
+    _check(lib.stokes_vcycle(h.ptr, _dptr(r, n, "r"), _dptr(z, n, "z")), "stokes_vcycle")
 
 
 def stokes_fgmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=1000):
     info = (stokes_solve_info * h.ninst)()
-    rc = _check(lib.stokes_fgmres_solve(h.ptr, _dptr(b), _dptr(x), rtol, restart, maxit, info),
+    n = stokes_level_size(h, 0)
+    rc = _check(lib.stokes_fgmres_solve(h.ptr, _dptr(b, n, "b"), _dptr(x, n, "x"), rtol, restart, maxit, info),
                 "stokes_fgmres_solve", allow_not_converged=True)
     return rc, [(i.iters, i.status, i.true_relres) for i in info]
 
 
 def stokes_fgmres_solve_host(h, b, x, rtol=1e-8, restart=30, maxit=1000):
     """b, x: numpy FP64 arrays in host memory (x: initial guess in, solution out)."""
-    assert b.dtype == np.float64 and x.dtype == np.float64 and x.flags.c_contiguous
+    n = stokes_level_size(h, 0)
+    for nm, a in (("b", b), ("x", x)):
+        if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+            raise ValueError(f"{nm}: a contiguous FP64 numpy array of {n} entries is expected")
     info = (stokes_solve_info * h.ninst)()
     rc = _check(lib.stokes_fgmres_solve_host(h.ptr, C.c_void_p(b.ctypes.data), C.c_void_p(x.ctypes.data), rtol,
                                              restart, maxit, info),
@@ -432,7 +449,18 @@ def stokes_autotune_report(h):
 
 
 def stokes_level_op(h, op, level, x, b, y):
-    _check(lib.stokes_level_op(h.ptr, op, level, _dptr(x), _dptr(b), _dptr(y)), "stokes_level_op")
+    L = stokes_num_levels(h)
+    if not 0 <= level < L:
+        raise ValueError(f"level {level} outside 0..{L - 1}")
+    n = stokes_level_size(h, level)
+    nx = ny = n
+    if op in (STOKES_OP_RESTRICT, STOKES_OP_PROLONG):
+        if level + 1 >= L:
+            raise ValueError("no coarser level")
+        nc = stokes_level_size(h, level + 1)
+        nx, ny = (n, nc) if op == STOKES_OP_RESTRICT else (nc, n)
+    _check(lib.stokes_level_op(h.ptr, op, level, _dptr(x, nx, "x"), _dptr(b, n, "b"), _dptr(y, ny, "y")),
+           "stokes_level_op")
 
 
 def stokes_num_levels(h):
@@ -467,7 +495,17 @@ def stokes_kernel_launches(h):
 def stokes_vanka_noalloc(h, level, x, y):
     """y = M_level^-1 x with the library's fixed scratch (no device
     allocation during the call); see include/stokes_dcamg.h."""
-    _check(lib.stokes_vanka_noalloc(h.ptr, level, _dptr(x), _dptr(y)), "stokes_vanka_noalloc")
+    L = stokes_num_levels(h)
+    if not 0 <= level < L:
+        raise ValueError(f"level {level} outside 0..{L - 1}")
+    n = stokes_level_size(h, level)
+    _check(lib.stokes_vanka_noalloc(h.ptr, level, _dptr(x, n, "x"), _dptr(y, n, "y")), "stokes_vanka_noalloc")
+
+
+def stokes_inject_pipeline_error(h, level):
+    """Set level's bulk-copy error flag as a timed-out wait would (test
+    support; every later checked call on the handle fails)."""
+    _check(lib.stokes_inject_pipeline_error(h.ptr, level), "stokes_inject_pipeline_error")
 
 
 def stokes_destroy(h):

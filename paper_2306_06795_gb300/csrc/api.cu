@@ -2476,6 +2476,14 @@ extern "C" int stokes_time_kernel(stokes_handle* h, int32_t which, int32_t l, in
   return join_out(h);
 }
 
+extern "C" int stokes_inject_pipeline_error(stokes_handle* h, int32_t l) {
+  if (!h || l < 0 || l >= h->L || !h->lv[l].has_patches) return fail(STOKES_ERR_INVALID_ARG, "level has no patches");
+  const int v = 8;  // a flag value no pipeline sets (1, 2, 4 mark its own waits)
+  CK(cudaMemcpyAsync(h->lv[l].pat.err, &v, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return STOKES_OK;
+}
+
 extern "C" int stokes_level_op(stokes_handle* h, int32_t op, int32_t l, const double* x, const double* b, double* y) {
   if (!h || l < 0 || l >= h->L || !y) return fail(STOKES_ERR_INVALID_ARG, "level_op arguments");
   TRY(join_in(h));

@@ -83,7 +83,11 @@ __global__ void __launch_bounds__(64) k_fg_update(int ninst, int m, int j, FgSta
       col[i] = t;
     }
     const double den = hypot(col[j], col[j + 1]);
-    const double c = col[j] / den, sj = col[j + 1] / den;
+    // den == 0: the rotated column vanishes (K0 z_j lies in span V_{j-1}
+    // and adds nothing); column j is left out of the least-squares solve
+    // and the instance stops as at a breakdown
+    const bool degenerate = !(den > 0.0);
+    const double c = degenerate ? 1.0 : col[j] / den, sj = degenerate ? 0.0 : col[j + 1] / den;
     cs[j] = c;
     sn[j] = sj;
     col[j] = den;
@@ -92,10 +96,10 @@ __global__ void __launch_bounds__(64) k_fg_update(int ninst, int m, int j, FgSta
     g[j + 1] = -sj * gj;
     g[j] = c * gj;
     st.its[s] += 1;
-    st.kcol[s] = j + 1;
+    st.kcol[s] = degenerate ? j : j + 1;
     if (!isfinite(g[j + 1])) atomicOr(st.err, 1);
-    const bool run = !(fabs(g[j + 1]) <= rtol * st.bnorm[s]) && !breakdown && st.its[s] < maxit && j + 1 < m &&
-                     isfinite(g[j + 1]);
+    const bool run = !(fabs(g[j + 1]) <= rtol * st.bnorm[s]) && !breakdown && !degenerate && st.its[s] < maxit &&
+                     j + 1 < m && isfinite(g[j + 1]);
     st.run[s] = run;
     st.scale[s] = run ? 1.0 / hn : 0.0;
     if (run) atomicOr(st.stat + j, 1);

@@ -78,5 +78,18 @@ extern "C" int stokes_vanka_noalloc(stokes_handle* h, int32_t level, const doubl
   rc = v.fp32 ? run<float>(v, static_cast<unsigned char*>(scratch), x_dev, y_dev)
               : run<double>(v, static_cast<unsigned char*>(scratch), x_dev, y_dev);
   if (rc != STOKES_OK) return rc;
+  // a bounded wait of the bulk-copy apply that ran out leaves part of the
+  // patch solutions unwritten; the scatter then read what an earlier call
+  // left in the shared scratch, so y is unusable: read the level's flag
+  // (this waits for the call's work on the handle's stream)
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, v.pat->err, sizeof(int), cudaMemcpyDeviceToHost, v.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(v.st);
+  if (e != cudaSuccess) return sd::set_error(STOKES_ERR_CUDA, cudaGetErrorString(e));
+  if (flag)
+    return sd::set_error(STOKES_ERR_CUDA, ("stokes_vanka_noalloc: a bulk-copy pipeline wait of level " +
+                                           std::to_string(level) + " timed out (flag " + std::to_string(flag) +
+                                           "); the output is unusable")
+                                              .c_str());
   return sd::stream_join_out(h);
 }

@@ -54,3 +54,16 @@ def test_sampler_without_nvidia_smi_reports_unavailable():
     rec = c.stop()
     if shutil.which("nvidia-smi") is None:
         assert rec["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_roofline_traffic_is_null_unless_the_kernel_sources_match(monkeypatch):
+    import hashlib
+    h = hashlib.sha256()
+    for f in bench.APPLY_L0_TRAFFIC["sources"]:
+        with open(os.path.join(bench.ROOT, "paper_2306_06795_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    rec = dict(bench.APPLY_L0_TRAFFIC)
+    monkeypatch.setattr(bench, "APPLY_L0_TRAFFIC", dict(rec, sha256=h.hexdigest()))
+    assert bench.apply_traffic() == rec["dram_bytes"]
+    monkeypatch.setattr(bench, "APPLY_L0_TRAFFIC", dict(rec, sha256="0" * 64))
+    assert bench.apply_traffic() is None
