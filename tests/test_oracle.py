@@ -3,7 +3,9 @@ algebra: the partition of unity of Eq. vanka, the block factorisation of
 Eqs. vanka_fact1/2 against dense LU on every patch, a single all-covering
 patch against a direct solve, the sampled Vanka application against the full
 one, the bordered coarsest solve against its projection property, the
-two-level form of Eq. TG-operator-full as a dense operator product, the
+Scott-Vogelius restriction R0 against its projection identity and a direct
+mass solve, the two-level form of Eq. TG-operator-full as a dense operator
+product for Taylor-Hood and for Scott-Vogelius, the
 Chebyshev closed form, FGMRES special cases and its minimisation over the
 preconditioned vectors, Krylov-wrapped relaxation, DLSC, and convergence of
 the stationary DC iteration."""
@@ -160,6 +162,67 @@ def test_two_level_cycle_is_eq_tg_operator_full():
     lhs = (e - z)[free]
     rhs = (G @ e)[free]
     assert np.linalg.norm(lhs - rhs) < 1e-11 * np.linalg.norm(e)
+
+
+def test_sv_restrict0_returns_a_continuous_pressure_and_the_velocity():
+    """Scott-Vogelius R0 (Eq. interp and the pressure transfers of Sec. 3.1):
+    velocity injection, and R0^p = Mcg^-1 Pi^T M_dg on the pressure.  Since
+    Pi^T M_dg Pi = Mcg, R0 maps (d_u, Pi g) to (d_u, g) for every continuous
+    g, up to the degree-32 Chebyshev error of the mass solve; on a general
+    discontinuous d_p it is the L2 projection Mcg^-1 (Pi^T M_dg d_p), checked
+    against a sparse direct solve."""
+    import scipy.sparse.linalg as spla
+    pr = stokes.build_sv(4)
+    o = cycle.Oracle(pr, cycle.Params(eta_u=1.0, eta_p=2.68, omega=[0.78] + [0.55] * (pr.nlevels - 2)))
+    off0, off1 = pr.field_off[0], pr.field_off[1]
+    d = pr.dim
+    Pi = pr.info["Pi"]
+    rng = np.random.default_rng(31)
+    du = rng.standard_normal(off0[d])
+    g = rng.standard_normal(Pi.shape[1])
+    out = o.restrict0(np.concatenate([du, Pi @ g]))
+    assert out.size == pr.K[1].shape[0]
+    assert off1[d] == off0[d] and np.array_equal(out[: off1[d]], du)
+    assert np.linalg.norm(out[off1[d]:] - g) <= 1e-13 * np.linalg.norm(g)
+    dp = rng.standard_normal(off0[d + 1] - off0[d])
+    out = o.restrict0(np.concatenate([du, dp]))
+    ref = spla.spsolve(pr.Mcg.tocsc(), pr.info["Pi"].T @ (pr.info["Mdg"] @ dp))
+    assert np.linalg.norm(out[off1[d]:] - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_sv_two_level_cycle_is_eq_tg_operator_full():
+    """The Scott-Vogelius twin of the two-level identity: with K1 coarsest,
+    G = S (I - P0 K1^-1 eta R0 K0) S, S = I - w0 M0^-1 K0 with the 3-seed
+    cell patches, P0 = blockdiag(I, Pi), R0 = blockdiag(I, Mcg^-1 Pi^T M_dg)
+    formed densely from the definitions (exact mass inverse)."""
+    pr = stokes.build_sv(4, max_levels=2)
+    assert pr.nlevels == 2
+    w0, eu, ep = 0.78, 1.0, 2.68
+    o = cycle.Oracle(pr, cycle.Params(eta_u=eu, eta_p=ep, omega=[w0]))
+    K0 = pr.K[0].toarray()
+    K1 = pr.K[1].toarray()
+    n0, n1 = K0.shape[0], K1.shape[0]
+    d = pr.dim
+    off0 = pr.field_off[0]
+    nv = off0[d]
+    S = np.eye(n0) - w0 * _dense_vanka(pr.K[0], pr.patches[0]) @ K0
+    nvec = pr.coarse_null
+    Bd = np.block([[K1, nvec[:, None]], [nvec[None, :], np.zeros((1, 1))]])
+    K1inv = np.linalg.inv(Bd)[:n1, :n1]
+    Pi = pr.info["Pi"].toarray()
+    R0 = np.zeros((n1, n0))
+    R0[:nv, :nv] = np.eye(nv)
+    R0[nv:, nv:] = np.linalg.solve(pr.Mcg.toarray(), Pi.T @ pr.info["Mdg"].toarray())
+    P0 = pr.P[0].toarray()
+    assert np.array_equal(P0[nv:, nv:], Pi)
+    eta = np.diag(np.concatenate([np.full(nv, eu), np.full(n0 - nv, ep)]))
+    G = S @ (np.eye(n0) - P0 @ K1inv @ R0 @ eta @ K0) @ S
+    rng = np.random.default_rng(32)
+    e = rng.standard_normal(n0)
+    e[pr.dirichlet] = 0.0
+    z = o.apply(K0 @ e)
+    free = ~pr.dirichlet
+    assert np.linalg.norm((e - z)[free] - (G @ e)[free]) < 1e-11 * np.linalg.norm(e)
 
 
 def test_dropping_eta_is_detected():
