@@ -1,7 +1,8 @@
 """DLSC relaxation, FP64 (Sec. 3.3.2, Alg. 2).
 
 One sweep for [A B^T; B 0] [u; p] = [f; g] with the velocity mass matrix
-replaced by Mu (identity on the P1isoP2 hierarchy, Sec. 3.3.2):
+replaced by Mu: its diagonal on the P2/P1 grid (level 0, K0), the identity
+on the P1isoP2 hierarchy (levels >= 1), as Sec. 3.3.2 prescribes:
 
     v* ~ A^-1 (f - A u - B^T p)                   (momentum)
     q  ~ (B Mu^-1 B^T)^-1 (g - B (u + v*))         (continuity)
@@ -41,6 +42,10 @@ def chebyshev(op, b, lo, hi, degree, dinv=None):
 
 
 class DLSCLevel:
+    """DLSC data of level l.  Mu^-1 is 1 / prob.Mu_diag on level 0 (the
+    high-order P2 grid) and the identity on levels >= 1 (P1isoP2 grids);
+    lambda_S[l] is the largest-eigenvalue estimate of B Mu^-1 B^T."""
+
     def __init__(self, prob, l, params):
         K = prob.K[l].tocsr()
         off = prob.field_off[l]
@@ -51,6 +56,13 @@ class DLSCLevel:
         self.A = K[:nv, :nv].tocsr()
         self.B = K[nv:, :nv].tocsr()
         self.BT = K[:nv, nv:].tocsr()
+        if l == 0:
+            if getattr(prob, "Mu_diag", None) is None:
+                raise ValueError("DLSC on level 0 needs the velocity mass diagonal Mu_diag")
+            self.mu_inv = 1.0 / np.asarray(prob.Mu_diag, dtype=np.float64)
+            assert self.mu_inv.size == nv
+        else:
+            self.mu_inv = np.ones(nv)
         self.dim = d
         self.lamA = float(prob.lambda_A[l])
         self.lamS = float(prob.lambda_S[l])
@@ -59,15 +71,17 @@ class DLSCLevel:
 
     def one(self, x, rhs):
         nv = self.nv
+        mi = self.mu_inv
         u, p = x[:nv], x[nv:]
         f, g = rhs[:nv], rhs[nv:]
         sA = (0.5 ** self.dim * self.lamA, 1.1 * self.lamA)
         sS = (0.5 ** self.dim * self.lamS, 1.1 * self.lamS)
-        S = lambda y: self.B @ (self.BT @ y)
+        S = lambda y: self.B @ (mi * (self.BT @ y))
+        # momentum, continuity, pressure correction, velocity correction
         v = chebyshev(lambda y: self.A @ y, f - self.A @ u - self.BT @ p, sA[0], sA[1], self.deg[0])
         q = chebyshev(S, g - self.B @ (u + v), sS[0], sS[1], self.deg[1])
-        dp = chebyshev(S, -(self.B @ (self.A @ (self.BT @ q))), sS[0], sS[1], self.deg[2])
-        du = v + self.BT @ q
+        dp = chebyshev(S, -(self.B @ (mi * (self.A @ (mi * (self.BT @ q))))), sS[0], sS[1], self.deg[2])
+        du = v + mi * (self.BT @ q)
         return np.concatenate([u + du, p + dp])
 
     def sweep(self, x, b):

@@ -17,6 +17,17 @@ SV2D_VANKA = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=2.68, omega0=0.78, 
 SV2D_VANKA_DLSC = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=2.96, omega0=0.87, omega=1.0)
 
 FGMRES = dict(rtol=1e-8, restart=30, maxit=600)
+# the paper's own solver setting (Sec. 4): FGMRES(20), residual reduced by 1e10
+FGMRES_PAPER = dict(rtol=1e-10, restart=20, maxit=600)
+
+
+def th2d_dlsc(nlevels):
+    """DLSC-AMG for Taylor-Hood (Sec. 3.3.2, Sec. 4.1): DLSC relaxation on
+    every level, Mu = diag(velocity mass) on K0 and I on the P1isoP2
+    hierarchy, eta = 1.00 (Table p2p1_taus, DLSC, DC-all, 2D structured),
+    two sweeps per relaxation call with the Table lsd_dgs_config degrees."""
+    return dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=1.0, omega=1.0, relax=[1] * (nlevels - 1),
+                dlsc_sweeps=2)
 
 
 def c1():

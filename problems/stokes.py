@@ -53,7 +53,7 @@ class Problem:
     mcg_bounds: tuple = (0.5, 2.0)  # Wathen interval of D^-1 Mcg
     lambda_A: np.ndarray = None    # per level, DLSC Chebyshev bounds
     lambda_S: np.ndarray = None
-    Mu_diag: np.ndarray = None     # level-0 lumped velocity mass (DLSC)
+    Mu_diag: np.ndarray = None     # diagonal of the level-0 velocity mass matrix (DLSC on K0)
     exact: dict = field(default_factory=dict)
     info: dict = field(default_factory=dict)
 
@@ -283,10 +283,11 @@ def make_patches(K, off, d, seeds=None, rel_tol=1e-14, exclude=None, Bpattern=No
                    np.array(nv, dtype=np.int32), np.array(npr, dtype=np.int32))
 
 
-def dlsc_bounds(K, field_off, d, steps=20, seed=4242):
-    """Largest-eigenvalue estimates of the velocity block A and of B B^T
-    (Mu = I) on every level, by seeded Lanczos (the Chebyshev intervals of
-    the DLSC stages, Table lsd_dgs_config)."""
+def dlsc_bounds(K, field_off, d, steps=20, seed=4242, mu_diag0=None):
+    """Largest-eigenvalue estimates of the velocity block A and of
+    B Mu^-1 B^T on every level, by seeded Lanczos (the Chebyshev intervals
+    of the DLSC stages, Table lsd_dgs_config).  Mu is diag(mu_diag0) on
+    level 0 when given (the P2/P1 grid, Sec. 3.3.2), the identity elsewhere."""
     lamA, lamS = [], []
     for l, Kl in enumerate(K):
         off = field_off[l]
@@ -294,7 +295,11 @@ def dlsc_bounds(K, field_off, d, steps=20, seed=4242):
         A = Kl[:nv, :nv].tocsr()
         B = Kl[nv:, :nv].tocsr()
         lamA.append(sa.lanczos_max(A, steps=steps, seed=seed + l))
-        lamS.append(sa.lanczos_max((B @ B.T).tocsr(), steps=steps, seed=seed + 100 + l))
+        if l == 0 and mu_diag0 is not None:
+            S = (B @ sp.diags(1.0 / mu_diag0) @ B.T).tocsr()
+        else:
+            S = (B @ B.T).tocsr()
+        lamS.append(sa.lanczos_max(S, steps=steps, seed=seed + 100 + l))
     return np.array(lamA), np.array(lamS)
 
 
@@ -394,7 +399,9 @@ def build_th(mesh, nu=1.0, bc="lid", rhs="zero", seed=None, max_levels=10,
                    patches=patches, b=b, coarse_null=cn,
                    dirichlet=np.concatenate([bnd] * d + [np.zeros(npres, bool)]),
                    Mp=k0["Mp"], exact=exact)
-    prob.lambda_A, prob.lambda_S = dlsc_bounds(K, field_off, d)
+    # diagonal of the P2 velocity mass matrix on every component (DLSC on K0)
+    prob.Mu_diag = np.tile(k0["Mu"].diagonal(), d)
+    prob.lambda_A, prob.lambda_S = dlsc_bounds(K, field_off, d, mu_diag0=prob.Mu_diag)
     prob.info = dict(mesh=mesh, V=V, n2=n2, npres=npres, Mu=k0["Mu"])
     return prob
 

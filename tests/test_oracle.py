@@ -327,43 +327,94 @@ def test_fgmres_dc_solves_c1_to_tolerance(c1):
     assert np.linalg.norm(xz - xd) < 1e-6 * np.linalg.norm(xd)
 
 
-def test_dlsc_sweep_is_the_factorised_update():
-    """With exact inner solves, one DLSC sweep (Alg. 2) from x adds
-    [I B^T; 0 -Ap^][A 0; B S]^-1 r, S = B B^T, Ap^ = S^+ (B A B^T), the
-    approximate factorisation of Sec. 3.3.2 with the derivation's sign."""
+def test_fgmres_dlsc_amg_solves_c1_to_tolerance(c1):
+    """DLSC on every level (Mu = diagonal mass on K0): FGMRES reaches the
+    direct solution of C1."""
+    from tests.helpers import make_oracle
+    o = make_oracle(c1, configs.th2d_dlsc(c1.nlevels))
+    x, its, rr = krylov.fgmres(c1.K[0], c1.b, o.apply, rtol=1e-8, restart=30, maxit=100)
+    assert rr <= 1e-8 and its <= 20
+    xd = direct.solve_stokes(c1.K[0], c1.b, c1.field_off[0], 2, Mp=c1.Mp)
+    xz = direct.zero_mean_pressure(x, c1.field_off[0], 2, c1.Mp)
+    assert np.linalg.norm(xz - xd) < 1e-6 * np.linalg.norm(xd)
+
+
+def _exact_dlsc(dl, x, rhs, Ai, Sp):
+    """One DLSC sweep of dl with exact inner solves (A^-1, and S^+ for the
+    Schur operator), by substituting the oracle's Chebyshev routine."""
     from oracle import dlsc
-    pr = stokes.build_th(M.unit_square(4), bc="lid", max_levels=3)
-    l = 1
-    par = cycle.Params(cheb_deg=(3, 3, 6), dlsc_sweeps=1)
-    dl = dlsc.DLSCLevel(pr, l, par)
-    A, B, BT = dl.A.toarray(), dl.B.toarray(), dl.BT.toarray()
-    S = B @ BT
-    Sp = np.linalg.pinv(S)
-    Ai = np.linalg.inv(A)
-    exact = {id(None): None}
 
     def solve(op, b, lo, hi, degree, dinv=None):
-        # exact solve: A when the size matches the velocity block, else S^+
-        return Ai @ b if b.size == A.shape[0] else Sp @ b
+        return Ai @ b if b.size == Ai.shape[0] else Sp @ b
 
     orig = dlsc.chebyshev
     dlsc.chebyshev = solve
     try:
-        rng = np.random.default_rng(5)
-        n = pr.K[l].shape[0]
-        x = rng.standard_normal(n)
-        rhs = rng.standard_normal(n)
-        xn = dl.one(x, rhs)
+        return dl.one(x, rhs)
     finally:
         dlsc.chebyshev = orig
+
+
+@pytest.mark.parametrize("l", [1, 0])
+def test_dlsc_sweep_is_the_factorised_update(l):
+    """With exact inner solves, one DLSC sweep (Alg. 2) from x adds
+    [I Mu^-1 B^T; 0 -Ap^][A 0; B S]^-1 r, S = B Mu^-1 B^T,
+    Ap^ = S^+ (B Mu^-1 A Mu^-1 B^T), the approximate factorisation of
+    Sec. 3.3.2 with the derivation's sign; Mu = I on the P1isoP2 level 1 and
+    the diagonal of the P2 velocity mass matrix on level 0."""
+    from oracle import dlsc
+    pr = stokes.build_th(M.unit_square(4), bc="lid", max_levels=3)
+    par = cycle.Params(cheb_deg=(3, 3, 6), dlsc_sweeps=1)
+    dl = dlsc.DLSCLevel(pr, l, par)
+    mi = dl.mu_inv
+    assert (l == 0) == (np.ptp(mi) > 0)
+    A, B, BT = dl.A.toarray(), dl.B.toarray(), dl.BT.toarray()
+    S = B @ (mi[:, None] * BT)
+    Sp = np.linalg.pinv(S)
+    Ai = np.linalg.inv(A)
+    rng = np.random.default_rng(5)
+    n = pr.K[l].shape[0]
+    x = rng.standard_normal(n)
+    rhs = rng.standard_normal(n)
+    xn = _exact_dlsc(dl, x, rhs, Ai, Sp)
     r = rhs - pr.K[l] @ x
     nv = dl.nv
     ru, rp = r[:nv], r[nv:]
     v = Ai @ ru
     q = Sp @ (rp - B @ v)
-    Ap = Sp @ (B @ A @ BT)
-    upd = np.concatenate([v + BT @ q, -Ap @ q])
+    Ap = Sp @ (B @ (mi[:, None] * (A @ (mi[:, None] * BT))))
+    upd = np.concatenate([v + mi * (BT @ q), -Ap @ q])
     assert np.linalg.norm((xn - x) - upd) < 1e-10 * np.linalg.norm(upd)
+
+
+def test_dlsc_exact_sweep_meets_continuity_and_the_least_squares_commutator():
+    """A property of the method, not of its formula: with exact inner solves
+    one DLSC sweep on K0 (Mu = diagonal of the P2 velocity mass matrix) for a
+    consistent right-hand side leaves (i) a zero continuity residual (the
+    velocity correction makes B u = g) and (ii) a momentum residual r_u with
+    B Mu^-1 r_u = 0: Ap^ is the least-squares commutator of Sec. 3.3.2,
+    whose error A Mu^-1 B^T - B^T Ap^ is Mu^-1-orthogonal to range(B^T).
+    Dropping Mu^-1 anywhere, or the plus sign of Eq. fulldlsc, breaks (ii)."""
+    from oracle import dlsc
+    pr = stokes.build_th(M.unit_square(4), bc="lid", max_levels=3)
+    dl = dlsc.DLSCLevel(pr, 0, cycle.Params(cheb_deg=(3, 3, 6), dlsc_sweeps=1))
+    mi = dl.mu_inv
+    A, B, BT = dl.A.toarray(), dl.B.toarray(), dl.BT.toarray()
+    Sp = np.linalg.pinv(B @ (mi[:, None] * BT))
+    Ai = np.linalg.inv(A)
+    K = pr.K[0]
+    rng = np.random.default_rng(7)
+    n = K.shape[0]
+    rhs = K @ rng.standard_normal(n)          # consistent: b in range(K)
+    x = rng.standard_normal(n)
+    xn = _exact_dlsc(dl, x, rhs, Ai, Sp)
+    res = rhs - K @ xn
+    nv = dl.nv
+    scale = np.linalg.norm(rhs - K @ x)
+    assert np.linalg.norm(res[nv:]) < 1e-10 * scale
+    comm = B @ (mi * res[:nv])
+    assert np.linalg.norm(comm) < 1e-10 * np.linalg.norm(B @ (mi * (rhs - K @ x)[:nv]))
+    assert np.linalg.norm(res[:nv]) > 1e-6 * scale  # not an exact solve: (ii) is a real condition
 
 
 def test_dlsc_relaxation_reduces_the_error():

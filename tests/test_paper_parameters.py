@@ -1,7 +1,7 @@
 """The workload configurations and the DLSC defaults use the parameters the
 paper prints (tests/golden/paper_tables.json, each entry with its table):
 Chebyshev degrees and interval of DLSC (Table lsd_dgs_config), the optimal
-eta of the Taylor-Hood DC-all Vanka preconditioner (Table p2p1_taus) and the
+eta of the Taylor-Hood DC-all Vanka and DLSC preconditioners (Table p2p1_taus) and the
 optimal (omega_0, eta_p) of the Scott-Vogelius ones (Table p2p1disc_params)."""
 import json
 import os
@@ -22,6 +22,13 @@ def test_taylor_hood_eta_is_the_dc_all_optimum():
     assert configs.TH2D_VANKA["schedule"] == 0  # DC-all
     assert configs.TH2D_VANKA["eta_u"] == configs.TH2D_VANKA["eta_p"] == t["vanka_dc_all_2d"]
     assert configs.TH3D_VANKA["eta_u"] == configs.TH3D_VANKA["eta_p"] == t["vanka_dc_all_3d"]
+
+
+def test_taylor_hood_dlsc_eta_is_the_dc_all_optimum():
+    t = tables()["taylor_hood_eta_opt_dlsc"]
+    v = configs.th2d_dlsc(6)
+    assert v["schedule"] == 0 and v["eta_u"] == v["eta_p"] == t["dlsc_dc_all_2d"]
+    assert v["relax"] == [1] * 5 and v["dlsc_sweeps"] == 2  # DLSC on every level, two sweeps
 
 
 def test_scott_vogelius_parameters_are_the_structured_optimum():
@@ -62,6 +69,7 @@ def test_oracle_dlsc_uses_the_chebyshev_interval(monkeypatch):
         field_off = [np.array([0, 1, 2, 3, 5])]
         lambda_A = [2.0]
         lambda_S = [8.0]
+        Mu_diag = np.ones(3)
 
     class Par:
         cheb_deg = (4, 4, 16)
