@@ -12,7 +12,7 @@
  * Alg. 1 hierarchy K1, K2, ... with an exact coarsest solve, prolongation
  * and relaxation on K0.  Relaxation is additive Vanka (Sec. 3.3.1,
  * Eq. vanka) with block-factorised patch solves (Eqs. vanka_fact1/2), or
- * DLSC (Sec. 3.3.2, Alg. 2) on levels >= 1.
+ * DLSC (Sec. 3.3.2, Alg. 2) on any level.
  *
  * Conventions
  *  - Every function returns STOKES_OK (0), a positive status
@@ -56,8 +56,9 @@ enum {
 enum { STOKES_TH = 0, STOKES_SV = 1 };                       /* K0 element pair */
 enum { STOKES_DC_ALL = 0, STOKES_DC_SKIP1 = 1, STOKES_DC_SKIP0 = 2 };  /* Sec. 4 schedules */
 /* Relaxation per level.  VANKA: nu damped additive Vanka sweeps
- * x += omega M^-1 (b - K x) (Eq. vanka).  DLSC: the Chebyshev LSC-DGS sweep
- * of Alg. 2 (levels >= 1).  VANKA_KRYLOV: the Krylov-wrapped relaxation of
+ * x += omega M^-1 (b - K x) (Eq. vanka).  DLSC: dlsc_sweeps Chebyshev LSC-DGS
+ * sweeps of Alg. 2 per relaxation call (Mu = diag(Mu_diag) on level 0, I on
+ * levels >= 1; omega unused).  VANKA_KRYLOV: the Krylov-wrapped relaxation of
  * Sec. 3.3.1, nu steps of flexible GMRES on K e = b - K x, each
  * right-preconditioned by one undamped Vanka sweep, then x += Z y with y
  * the least-squares minimiser (nu <= 4; omega unused). */
@@ -140,6 +141,12 @@ typedef struct {
   /* BTP (Sec. 4), used when stokes_params.preconditioner is
    * STOKES_PRECOND_BTP (single-instance handles); may be NULL otherwise */
   const stokes_btp* btp;
+  /* DLSC on level 0 (Sec. 3.3.2: on the P2 grid Mu is the diagonal of the
+   * velocity mass matrix; the P1isoP2 levels use Mu = I): the diagonal,
+   * [velocity DoFs of level 0], all entries > 0.  Needed only when level 0
+   * relaxes with DLSC (lambda_S[0] is then the estimate for B Mu^-1 B^T);
+   * may be NULL otherwise. */
+  const double* Mu_diag;
 } stokes_problem;
 
 /* Parameters of the defect-correction cycle (Table param_ref). */

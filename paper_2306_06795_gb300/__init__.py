@@ -71,7 +71,7 @@ class stokes_problem(C.Structure):
                 ("R0p", C.POINTER(stokes_csr)), ("Mcg", C.POINTER(stokes_csr)),
                 ("mcg_lo", C.c_double), ("mcg_hi", C.c_double),
                 ("lambda_A", C.POINTER(C.c_double)), ("lambda_S", C.POINTER(C.c_double)),
-                ("btp", C.POINTER(stokes_btp))]
+                ("btp", C.POINTER(stokes_btp)), ("Mu_diag", C.POINTER(C.c_double))]
 
 
 class stokes_params(C.Structure):
@@ -220,6 +220,9 @@ def _problem(keep, pr):
         ls = keep.arr(pr.lambda_S, np.float64)
         p.lambda_A = _p(la, C.c_double)
         p.lambda_S = _p(ls, C.c_double)
+    if getattr(pr, "Mu_diag", None) is not None:
+        md = keep.arr(pr.Mu_diag, np.float64)
+        p.Mu_diag = _p(md, C.c_double)
     bt = getattr(pr, "btp", None)
     if bt is not None:
         q = stokes_btp()

@@ -57,13 +57,17 @@ struct CoarseSet {
   int64_t kinv_elems = 0;
 };
 
-// DLSC relaxation data of one level (Sec. 3.3.2, Alg. 2, Mu = I): the
-// velocity block A, B and B^T as level-sized CSRs (rows outside the block
-// are empty), the row kinds and the Chebyshev bounds.
+// DLSC relaxation data of one level (Sec. 3.3.2, Alg. 2): the velocity
+// block A, B and Mu^-1 B^T as level-sized CSRs (rows outside the block are
+// empty), the row kinds and the Chebyshev bounds.  Mu = I on levels >= 1;
+// on level 0 Mu = diag(Mu_diag): BT holds the rows of B^T scaled by 1/Mu
+// and muinv (velocity rows 1/Mu, pressure rows 0) scales A's product in the
+// pressure-correction right-hand side.
 struct DLSCData {
   DevCSR A, B, BT;
   uint8_t* kind = nullptr;  // 0 velocity, 1 pressure, 2 rows not relaxed here
   double lamA = 0, lamS = 0;
+  void* muinv = nullptr;    // level vector in the cycle precision, or nullptr (Mu = I)
   void* v[9] = {nullptr};   // res, v, q, dp, t1, t2, r, d0, d1
 };
 
@@ -621,8 +625,9 @@ int check_pipeline_errors(stokes_handle* h);
 // ------------------------------------------------------------- the cycle
 namespace {
 
-// One DLSC sweep (Alg. 2) on level l with Mu = I: momentum, continuity and
-// pressure-correction Chebyshev solves, then the velocity correction.
+// One DLSC sweep (Alg. 2) on level l: momentum, continuity and
+// pressure-correction Chebyshev solves, then the velocity correction (D.BT
+// already carries Mu^-1, so B D.BT = B Mu^-1 B^T and D.BT q = Mu^-1 B^T q).
 template <typename T>
 int dlsc_sweep(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b) {
   Level& L = lvs[l];
@@ -636,17 +641,23 @@ int dlsc_sweep(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* 
   // v* ~ A^-1 (f - A u - B^T p)
   TRY(cheb_run<T>(h, D.A, kval<T>(D.A), nullptr, nullptr, nullptr, nullptr, res, D.kind, 0, 1.0, fa * D.lamA,
                   1.1 * D.lamA, h->cheb_deg[0], vs, cr, c0, c1, n));
-  // q ~ S^-1 (g - B (u + v*)),  S = B B^T
+  // q ~ S^-1 (g - B (u + v*)),  S = B Mu^-1 B^T
   TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), vs, res, t1, SPMV_RES)));
   TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), t2, nullptr, t1, D.kind, 1, 1.0, fa * D.lamS,
                   1.1 * D.lamS, h->cheb_deg[1], q, cr, c0, c1, n));
-  // dp ~ S^-1 ( -(B A B^T) q )
+  // dp ~ S^-1 ( -(B Mu^-1 A Mu^-1 B^T) q )
   TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), q, (const T*)nullptr, t1, SPMV_SET)));
   TRY((L_spmv<T, T, T, T, T>(h, D.A, kval<T>(D.A), t1, (const T*)nullptr, t2, SPMV_SET)));
-  TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), t2, (const T*)nullptr, t1, SPMV_SET)));
-  TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), t2, nullptr, t1, D.kind, 1, -1.0, fa * D.lamS,
+  T* ta = t2;  // A Mu^-1 B^T q
+  T* tb = t1;
+  if (D.muinv) {
+    TRY(L_diag_scale<T>(h, n, reinterpret_cast<const T*>(D.muinv), t2, t1));
+    std::swap(ta, tb);
+  }
+  TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), ta, (const T*)nullptr, tb, SPMV_SET)));
+  TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), ta, nullptr, tb, D.kind, 1, -1.0, fa * D.lamS,
                   1.1 * D.lamS, h->cheb_deg[2], dp, cr, c0, c1, n));
-  // u += v* + B^T q ;  p += dp
+  // u += v* + Mu^-1 B^T q ;  p += dp
   TRY((L_axpy<T, T>(h, n, 1.0, vs, x)));
   TRY((L_axpy<T, T>(h, n, 1.0, dp, x)));
   TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), q, (const T*)nullptr, x, SPMV_ADD)));
@@ -725,6 +736,9 @@ int relax(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b, in
   if (L.dlsc) {
     if (zero_guess) TRY(L_zero<T>(h, L.n, x));
     for (int s = 0; s < nsweeps * h->dlsc_sweeps; ++s) TRY(dlsc_sweep<T>(h, lvs, l, x, b));
+    // level 0: the cycle output (Dirichlet rows take r) or the FP64 copy of x
+    if (out64) TRY(L_finalize<T>(h, L.n, x, r64, out64));
+    else if (x64) TRY((L_cast<T, double>(h, L.n, x, x64)));
     return STOKES_OK;
   }
   T* r = reinterpret_cast<T*>(L.r);
@@ -808,7 +822,7 @@ int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
     TRY((L_cast<double, T>(h, L0.n, r64, reinterpret_cast<T*>(L0.b))));
     r0 = reinterpret_cast<const T*>(L0.b);
   }
-  const bool skip0 = h->schedule == STOKES_DC_SKIP0 || !L0.has_patches;
+  const bool skip0 = h->schedule == STOKES_DC_SKIP0 || !(L0.has_patches || L0.dlsc);
   // an FP32 cycle also keeps x in FP64 for the FP64 residual of the DC step,
   // so that residual converts each entry once instead of once per nonzero
   double* x0d = sizeof(T) == 8 ? reinterpret_cast<double*>(x0) : h->x0_64;
@@ -1267,6 +1281,9 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
   HostCSR A, B, BT;
   A.nrows = B.nrows = BT.nrows = A.ncols = B.ncols = BT.ncols = (int)lv.n;
   std::vector<uint8_t> kind(lv.n, 2);
+  // level 0 (the P2 grid): Mu = diag(Mu_diag); levels >= 1: Mu = I
+  const bool mass = l == 0;
+  std::vector<double> muinv(mass ? lv.n : 0, 0.0);
   for (int k = 0; k < ninst; ++k) {
     const stokes_problem* p = probs[k];
     if (p->nlevels <= l) continue;
@@ -1274,6 +1291,12 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
     const int64_t* off = p->field_off + (size_t)l * (dim + 2);
     const int64_t o = lv.seg_off[k];
     const bool relaxes = p->nlevels - 1 > l;
+    if (mass && relaxes)
+      for (int64_t i = 0; i < off[dim]; ++i) {
+        const double m = p->Mu_diag[i];
+        if (!(m > 0) || !std::isfinite(m)) return fail(STOKES_ERR_INVALID_ARG, "Mu_diag entries must be positive");
+        muinv[o + i] = 1.0 / m;
+      }
     for (int i = 0; i < K->nrows; ++i) {
       const bool vel = i < off[dim];
       if (relaxes) kind[o + i] = vel ? 0 : 1;
@@ -1283,7 +1306,8 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
         HostCSR& dst = vel ? (cvel ? A : BT) : (cvel ? B : A);
         if (!vel && !cvel) continue;  // zero block
         dst.col.push_back((int)(o + c));
-        dst.val.push_back(K->val[e]);
+        // B^T rows carry Mu^-1 (velocity row i of B^T scaled by 1/Mu_i)
+        dst.val.push_back(mass && vel && !cvel ? K->val[e] * muinv[o + i] : K->val[e]);
       }
       A.rowptr.push_back((int)A.col.size());
       B.rowptr.push_back((int)B.col.size());
@@ -1294,6 +1318,18 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
   TRY(upload_csr(h, lv.dl.B, B));
   TRY(upload_csr(h, lv.dl.BT, BT));
   TRY(upload(h, &lv.dl.kind, kind));
+  if (mass) {
+    if (h->prec == STOKES_FP32) {
+      std::vector<float> m32(muinv.begin(), muinv.end());
+      float* d = nullptr;
+      TRY(upload(h, &d, m32));
+      lv.dl.muinv = d;
+    } else {
+      double* d = nullptr;
+      TRY(upload(h, &d, muinv));
+      lv.dl.muinv = d;
+    }
+  }
   for (int k = 0; k < ninst; ++k)
     if (probs[k]->nlevels - 1 > l) {
       lv.dl.lamA = probs[k]->lambda_A[l];
@@ -1652,11 +1688,12 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     if (relaxk[l] == STOKES_RELAX_VANKA_KRYLOV && std::max(prm->nu1, prm->nu2) > kKrMaxSteps)
       return fail(STOKES_ERR_INVALID_ARG, "Krylov-wrapped relaxation: at most 4 inner steps (nu1, nu2)");
     if (relaxk[l] == STOKES_RELAX_DLSC) {
-      if (l == 0) return fail(STOKES_ERR_INVALID_ARG, "DLSC is available on levels >= 1 (Mu = I)");
       for (int k = 0; k < ninst; ++k) {
         if (probs[k]->nlevels - 1 <= l) continue;
         if (!probs[k]->lambda_A || !probs[k]->lambda_S)
           return fail(STOKES_ERR_INVALID_ARG, "DLSC needs lambda_A and lambda_S");
+        if (l == 0 && !probs[k]->Mu_diag)
+          return fail(STOKES_ERR_INVALID_ARG, "DLSC on level 0 needs Mu_diag (diagonal of the velocity mass matrix)");
         if (probs[k]->lambda_A[l] != probs[0]->lambda_A[l] || probs[k]->lambda_S[l] != probs[0]->lambda_S[l])
           return fail(STOKES_ERR_INVALID_ARG, "DLSC instances must share their Chebyshev bounds");
       }

@@ -22,4 +22,17 @@ def make_oracle(pr, prm):
 
 
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    """Relative difference of a against the reference b, the larger of the
+    2-norm ratio ||a - b|| / ||b|| and the worst-element ratio
+    max|a - b| / max|b|: a wrong value confined to a few entries cannot hide
+    under a whole-vector norm."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.shape != b.shape:
+        raise ValueError(f"shapes differ: {a.shape} vs {b.shape}")
+    if a.size == 0:
+        return 0.0
+    d = a - b
+    two = np.linalg.norm(d) / max(np.linalg.norm(b), 1e-300)
+    worst = np.max(np.abs(d)) / max(np.max(np.abs(b)), 1e-300)
+    return float(max(two, worst))
