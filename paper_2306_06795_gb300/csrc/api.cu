@@ -167,6 +167,8 @@ struct stokes_handle {
   int64_t* dend = nullptr;
   int* sd_beg = nullptr;
   int* sd_end = nullptr;
+  KrChunks arch;              // the dot-product chunks with their instances (fused Arnoldi passes)
+  int* arcnt = nullptr;       // per-instance completion counters of the fused passes (0 between launches)
   void* flush = nullptr;
   size_t flush_bytes = 0;
   int64_t launches = 0;       // kernels launched so far
@@ -2124,6 +2126,14 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       TRY(upload(h, &h->dend, ce));
       TRY(upload(h, &h->sd_beg, sb));
       TRY(upload(h, &h->sd_end, se));
+      h->arch.n = h->ndchunks;
+      h->arch.beg = h->dbeg;
+      h->arch.end = h->dend;
+      h->arch.sbeg = h->sd_beg;
+      h->arch.send = h->sd_end;
+      TRY(upload(h, &h->arch.seg, cs));
+      std::vector<int> zero(ninst, 0);
+      TRY(upload(h, &h->arcnt, zero));
     }
   }
   return STOKES_OK;
@@ -2304,6 +2314,16 @@ int arnoldi_step(stokes_handle* h, int j, double rtol, int maxit) {
   // w -= V h2, then ||w||^2 (a second pass is needed at nearly every step:
   // with a good preconditioner w = K0 z_j lies mostly in span V)
   const int nc = j + 1;
+  if (nc <= kArMaxCols) {
+    // fused passes: h1 -> hd, h2 -> yd, then the Givens update
+    CK(ar_dots(h->arch, nc, h->V, n, h->w, h->partial, h->ldp, h->arcnt, h->hd, h->ldh, h->fg.stat + j, h->st));
+    CK(ar_axpy_dots(h->arch, nc, h->V, n, h->hd, h->ldh, h->w, h->partial, h->ldp, h->arcnt, h->yd, h->st));
+    CK(ar_axpy_norm_update(h->arch, nc, h->V, n, h->hd, h->yd, h->ldh, h->w, h->partial, h->ldp, h->arcnt,
+                           h->krylov_m, j, h->fg, rtol, maxit, h->st));
+    CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st));
+    CK(cudaMemcpyAsync(h->hstat + j, h->fg.stat + j, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    return STOKES_OK;
+  }
   TRY(seg_dots(h, h->V, n, nc, h->w, 0));
   CK(multiaxpy(h->nchunks, h->cbeg, h->cend, h->cseg, nc, h->V, n, h->hd, h->ldh, -1.0, h->w, h->st));
   CK(cudaMemcpyAsync(h->yd, h->hd, sizeof(double) * ni * h->ldh, cudaMemcpyDeviceToDevice, h->st));
@@ -2393,7 +2413,7 @@ extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x,
       cudaGraphExec_t ge;
       TRY(iter_graph(h, j, rtol, maxit, &ge));
       CK(cudaGraphLaunch(ge, h->st));
-      h->launches += h->cycle_launches + 14;
+      h->launches += h->cycle_launches + (j + 1 <= kArMaxCols ? 5 : 11);
       CK(cudaEventRecord(h->ev_iter[j], h->st));
       last = j;
       if (j > 0) {

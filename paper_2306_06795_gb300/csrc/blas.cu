@@ -9,13 +9,14 @@ namespace sd {
 
 template <typename TI, typename TO>
 __global__ void k_cast(int64_t n, const TI* __restrict__ in, TO* __restrict__ out) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) out[j] = TO(in[j]);
 }
 template <typename TI, typename TO>
 cudaError_t cast_copy(int64_t n, const TI* in, TO* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_cast<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, out);
+  SD_LAUNCH((k_cast<TI, TO>), (unsigned)((n + 255) / 256), 256, 0, st, n, in, out);
   return cudaGetLastError();
 }
 template cudaError_t cast_copy<double, float>(int64_t, const double*, float*, cudaStream_t);
@@ -25,13 +26,14 @@ template cudaError_t cast_copy<float, float>(int64_t, const float*, float*, cuda
 
 template <typename T, typename TI>
 __global__ void k_axpy(int64_t n, T a, const TI* __restrict__ x, T* __restrict__ y) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) y[j] += a * T(x[j]);
 }
 template <typename T, typename TI>
 cudaError_t axpy_into(int64_t n, double a, const TI* x, T* y, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, T(a), x, y);
+  SD_LAUNCH((k_axpy<T, TI>), (unsigned)((n + 255) / 256), 256, 0, st, n, T(a), x, y);
   return cudaGetLastError();
 }
 template cudaError_t axpy_into<float, float>(int64_t, double, const float*, float*, cudaStream_t);
@@ -40,13 +42,14 @@ template cudaError_t axpy_into<double, float>(int64_t, double, const float*, dou
 
 template <typename T>
 __global__ void k_zero(int64_t n, T* __restrict__ y) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) y[j] = T(0);
 }
 template <typename T>
 cudaError_t fill_zero(int64_t n, T* y, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_zero<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, y);
+  SD_LAUNCH(k_zero<T>, (unsigned)((n + 255) / 256), 256, 0, st, n, y);
   return cudaGetLastError();
 }
 template cudaError_t fill_zero<float>(int64_t, float*, cudaStream_t);
@@ -55,13 +58,14 @@ template cudaError_t fill_zero<double>(int64_t, double*, cudaStream_t);
 // z = d .* u (the Jacobi step inside a Krylov-wrapped relaxation)
 template <typename T>
 __global__ void k_diag_scale(int64_t n, const T* __restrict__ d, const T* __restrict__ u, T* __restrict__ z) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) z[j] = d[j] * u[j];
 }
 template <typename T>
 cudaError_t diag_scale(int64_t n, const T* d, const T* u, T* z, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_diag_scale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d, u, z);
+  SD_LAUNCH(k_diag_scale<T>, (unsigned)((n + 255) / 256), 256, 0, st, n, d, u, z);
   return cudaGetLastError();
 }
 template cudaError_t diag_scale<float>(int64_t, const float*, const float*, float*, cudaStream_t);
@@ -72,6 +76,7 @@ template cudaError_t diag_scale<double>(int64_t, const double*, const double*, d
 template <typename T>
 __global__ void k_btp_out(int64_t nu, int64_t np, const T* __restrict__ du, const T* __restrict__ dp, double sp,
                           const uint8_t* __restrict__ dir, const double* __restrict__ r64, double* __restrict__ z) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < nu) z[j] = dir[j] ? r64[j] : (double)du[j];
   else if (j < nu + np) z[j] = sp * (double)dp[j - nu];
@@ -80,7 +85,7 @@ template <typename T>
 cudaError_t btp_out(int64_t nu, int64_t np, const T* du, const T* dp, double sp, const uint8_t* dir,
                     const double* r64, double* z, cudaStream_t st) {
   if (nu + np == 0) return cudaSuccess;
-  k_btp_out<<<(unsigned)((nu + np + 255) / 256), 256, 0, st>>>(nu, np, du, dp, sp, dir, r64, z);
+  SD_LAUNCH(k_btp_out<T>, (unsigned)((nu + np + 255) / 256), 256, 0, st, nu, np, du, dp, sp, dir, r64, z);
   return cudaGetLastError();
 }
 template cudaError_t btp_out<float>(int64_t, int64_t, const float*, const float*, double, const uint8_t*,
@@ -91,13 +96,14 @@ template cudaError_t btp_out<double>(int64_t, int64_t, const double*, const doub
 template <typename T>
 __global__ void k_finalize(int64_t n, const T* __restrict__ x, const uint8_t* __restrict__ dir,
                            const double* __restrict__ r64, double* __restrict__ out) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) out[j] = dir[j] ? r64[j] : double(x[j]);
 }
 template <typename T>
 cudaError_t finalize_out(int64_t n, const T* x, const uint8_t* dir, const double* r64, double* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, dir, r64, out);
+  SD_LAUNCH(k_finalize<T>, (unsigned)((n + 255) / 256), 256, 0, st, n, x, dir, r64, out);
   return cudaGetLastError();
 }
 template cudaError_t finalize_out<float>(int64_t, const float*, const uint8_t*, const double*, double*, cudaStream_t);
@@ -117,6 +123,7 @@ template <typename T>
 __global__ void k_cheb_init(int64_t n, const T* __restrict__ b, const T* __restrict__ dinv,
                             const uint8_t* __restrict__ mask, uint8_t want, T s, T inv_theta, T* __restrict__ r,
                             T* __restrict__ d, T* __restrict__ x) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   T v = (!mask || mask[j] == want) ? s * b[j] : T(0);
@@ -129,7 +136,7 @@ template <typename T>
 cudaError_t cheb_init(int64_t n, const T* b, const T* dinv, const uint8_t* mask, uint8_t want, double s, double theta,
                       T* r, T* d, T* x, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_cheb_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, b, dinv, mask, want, T(s), T(1.0 / theta), r, d, x);
+  SD_LAUNCH(k_cheb_init<T>, (unsigned)((n + 255) / 256), 256, 0, st, n, b, dinv, mask, want, T(s), T(1.0 / theta), r, d, x);
   return cudaGetLastError();
 }
 template cudaError_t cheb_init<float>(int64_t, const float*, const float*, const uint8_t*, uint8_t, double, double,
@@ -143,6 +150,7 @@ __global__ void __launch_bounds__(256) k_cheb_step(int nrows, const int* __restr
                                                    const T* __restrict__ w, const T* __restrict__ dinv,
                                                    T* __restrict__ x, T* __restrict__ r, const T* __restrict__ din,
                                                    T* __restrict__ dout, T alpha, T beta) {
+  pdl_enter();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = tid / TPR;
   const int lane = (int)(tid % TPR);
@@ -166,7 +174,7 @@ cudaError_t cheb_step(const DevCSR& M, const T* val, const T* w, const T* dinv, 
   if (M.nrows == 0) return cudaSuccess;
   const int64_t total = (int64_t)M.nrows * 8;
   const unsigned blocks = (unsigned)((total + 255) / 256);
-  k_cheb_step<T, 8><<<blocks, 256, 0, st>>>(M.nrows, M.rowptr, M.col, val, w, dinv, x, r, d_in, d_out, T(alpha), T(beta));
+  SD_LAUNCH((k_cheb_step<T, 8>), blocks, 256, 0, st, M.nrows, M.rowptr, M.col, val, w, dinv, x, r, d_in, d_out, T(alpha), T(beta));
   return cudaGetLastError();
 }
 template cudaError_t cheb_step<float>(const DevCSR&, const float*, const float*, const float*, float*, float*,
@@ -176,13 +184,14 @@ template cudaError_t cheb_step<double>(const DevCSR&, const double*, const doubl
 
 template <typename TI, typename TO>
 __global__ void k_scatter_rows(int64_t n, const TI* __restrict__ in, const int* __restrict__ rows, TO* __restrict__ out) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) out[rows[j]] = TO(in[j]);
 }
 template <typename TI, typename TO>
 cudaError_t scatter_rows(int64_t n, const TI* in, const int* rows, TO* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_scatter_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, rows, out);
+  SD_LAUNCH((k_scatter_rows<TI, TO>), (unsigned)((n + 255) / 256), 256, 0, st, n, in, rows, out);
   return cudaGetLastError();
 }
 template cudaError_t scatter_rows<double, float>(int64_t, const double*, const int*, float*, cudaStream_t);
@@ -194,6 +203,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_coarse(const int* __restrict__ boff, const int* __restrict__ bn,
                                                 const int64_t* __restrict__ koff, const double* __restrict__ Kinv,
                                                 const T* __restrict__ b, T* __restrict__ y) {
+  pdl_enter();
   const int kb = blockIdx.y;
   const int n = bn[kb];
   const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -212,7 +222,7 @@ cudaError_t coarse_solve(int nblocks, const int* boff, const int* bn, const int6
                          int max_n, const T* b, T* y, cudaStream_t st) {
   if (nblocks == 0) return cudaSuccess;
   dim3 grid((unsigned)((max_n + 3) / 4), (unsigned)nblocks);
-  k_coarse<T><<<grid, 128, 0, st>>>(boff, bn, koff, Kinv, b, y);
+  SD_LAUNCH((k_coarse<T>), grid, 128, 0, st, boff, bn, koff, Kinv, b, y);
   return cudaGetLastError();
 }
 template cudaError_t coarse_solve<float>(int, const int*, const int*, const int64_t*, const double*, int,
@@ -238,6 +248,7 @@ template <int NK>
 __global__ void __launch_bounds__(kRedThreads, 4) k_multidot(const int64_t* __restrict__ cbeg,
     const int64_t* __restrict__ cend, int ncols, const double* __restrict__ V, int64_t ldv,
     const double* __restrict__ w, double* __restrict__ partial, int ldp) {
+  pdl_enter();
   __shared__ double red[kRedThreads / 32][NK];
   const int c = blockIdx.x, k0 = blockIdx.y * NK;
   const int nk = min(NK, ncols - k0);
@@ -299,10 +310,10 @@ cudaError_t multidot_partial(int nchunks, const int64_t* cbeg, const int64_t* ce
   const int nk = ncols >= 8 ? 8 : ncols > 4 ? 8 : ncols > 2 ? 4 : ncols;
   const dim3 grid((unsigned)nchunks, (unsigned)((ncols + nk - 1) / nk));
   switch (nk) {
-    case 1: k_multidot<1><<<grid, kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
-    case 2: k_multidot<2><<<grid, kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
-    case 4: k_multidot<4><<<grid, kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
-    default: k_multidot<8><<<grid, kRedThreads, 0, st>>>(cbeg, cend, ncols, V, ldv, w, partial, ldp);
+    case 1: SD_LAUNCH((k_multidot<1>), grid, kRedThreads, 0, st, cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
+    case 2: SD_LAUNCH((k_multidot<2>), grid, kRedThreads, 0, st, cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
+    case 4: SD_LAUNCH((k_multidot<4>), grid, kRedThreads, 0, st, cbeg, cend, ncols, V, ldv, w, partial, ldp); break;
+    default: SD_LAUNCH((k_multidot<8>), grid, kRedThreads, 0, st, cbeg, cend, ncols, V, ldv, w, partial, ldp);
   }
   return cudaGetLastError();
 }
@@ -313,6 +324,7 @@ __global__ void __launch_bounds__(128) k_multidot_finish(int nseg, const int* __
                                                          const int* __restrict__ sc_end, int ncols,
                                                          const double* __restrict__ partial, int ldp,
                                                          double* __restrict__ h, int ldh, int accumulate) {
+  pdl_enter();
   const int idx = blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (idx >= nseg * ncols) return;
@@ -330,7 +342,7 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
                             int ldp, double* h, int ldh, int accumulate, cudaStream_t st) {
   const int tot = nseg * ncols;
   if (tot == 0) return cudaSuccess;
-  k_multidot_finish<<<(tot + 3) / 4, 128, 0, st>>>(nseg, sc_beg, sc_end, ncols, partial, ldp, h, ldh, accumulate);
+  SD_LAUNCH(k_multidot_finish, (tot + 3) / 4, 128, 0, st, nseg, sc_beg, sc_end, ncols, partial, ldp, h, ldh, accumulate);
   return cudaGetLastError();
 }
 
@@ -340,6 +352,7 @@ cudaError_t multidot_finish(int nseg, const int* sc_beg, const int* sc_end, int 
 __global__ void __launch_bounds__(kRedThreads, 4) k_multiaxpy(const int64_t* __restrict__ cbeg,
     const int64_t* __restrict__ cend, const int* __restrict__ cseg, int ncols, const double* __restrict__ V,
     int64_t ldv, const double* __restrict__ coef, int ldh, double sign, double* __restrict__ w) {
+  pdl_enter();
   __shared__ double cf[kMaxAxpyCols];
   const int c = blockIdx.x;
   for (int k = threadIdx.x; k < ncols; k += kRedThreads) cf[k] = coef[cseg[c] * ldh + k];
@@ -372,7 +385,7 @@ cudaError_t multiaxpy(int nchunks, const int64_t* cbeg, const int64_t* cend, con
                       cudaStream_t st) {
   if (nchunks == 0 || ncols == 0) return cudaSuccess;
   if (ncols > kMaxAxpyCols) return cudaErrorInvalidValue;
-  k_multiaxpy<<<(unsigned)nchunks, kRedThreads, 0, st>>>(cbeg, cend, cseg, ncols, V, ldv, coef, ldh, sign, w);
+  SD_LAUNCH(k_multiaxpy, (unsigned)nchunks, kRedThreads, 0, st, cbeg, cend, cseg, ncols, V, ldv, coef, ldh, sign, w);
   return cudaGetLastError();
 }
 
@@ -380,6 +393,7 @@ __global__ void __launch_bounds__(kRedThreads) k_seg_scale(const int64_t* __rest
     const int64_t* __restrict__ cend, const int* __restrict__ cseg, const double* __restrict__ in,
     double* __restrict__ out, const double* __restrict__ den, int ldd, int kd, const int* __restrict__ active,
     int sqrt_den) {
+  pdl_enter();
   const int c = blockIdx.x;
   const int s = cseg[c];
   double d = den[s * ldd + kd];
@@ -391,7 +405,7 @@ cudaError_t seg_scale(int nchunks, const int64_t* cbeg, const int64_t* cend, con
                       double* out, const double* den, int ldd, int kd, const int* active, int sqrt_den,
                       cudaStream_t st) {
   if (nchunks == 0) return cudaSuccess;
-  k_seg_scale<<<nchunks, kRedThreads, 0, st>>>(cbeg, cend, cseg, in, out, den, ldd, kd, active, sqrt_den);
+  SD_LAUNCH(k_seg_scale, nchunks, kRedThreads, 0, st, cbeg, cend, cseg, in, out, den, ldd, kd, active, sqrt_den);
   return cudaGetLastError();
 }
 

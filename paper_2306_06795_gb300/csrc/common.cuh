@@ -7,6 +7,46 @@
 
 namespace sd {
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be
+// scheduled while the previous kernel of its stream is still finishing;
+// pdl_enter(), the first statement of every kernel of the solve path, waits
+// until that previous grid has completed and its writes are visible
+// (griddepcontrol.wait) and then lets the next kernel of the stream be
+// scheduled (griddepcontrol.launch_dependents), so the semantics stay
+// those of plain stream order while the launch latency overlaps the
+// previous kernel's tail.  Without a programmatic dependency both
+// instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { pdl_enter(); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
+// Launches kernel<<<grid, block, smem, st>>>(args...) with programmatic
+// dependent launch from a function returning cudaError_t; returns the launch
+// error.  A templated kernel name goes in parentheses.
+#define SD_LAUNCH(kernel, grid, block, smem, st, ...)                                                   \
+  do {                                                                                                  \
+    cudaError_t e_launch_ = ::sd::launch_pdl(kernel, dim3(grid), dim3(block), (size_t)(smem), st, __VA_ARGS__); \
+    if (e_launch_ != cudaSuccess) return e_launch_;                                                     \
+  } while (0)
+
 // CSR matrix on the device: int32 row pointers and columns (nnz < 2^31),
 // FP64 values and, for an FP32 cycle, an FP32 copy of the values.
 constexpr int kStreamNnz = 2048, kStreamRows = 256;
@@ -276,6 +316,21 @@ cudaError_t fg_start(int ninst, int m, const FgState& st, const double* h, int l
 cudaError_t fg_update(int ninst, int m, int j, const FgState& st, const double* h1, const double* h2, int ldh,
                       double rtol, int maxit, cudaStream_t s);
 cudaError_t fg_solve(int ninst, int m, const FgState& st, int ldh, cudaStream_t s);
+// Fused classical Gram-Schmidt passes of Arnoldi step j = nc - 1 for
+// nc <= kArMaxCols columns over the chunks ch (fgmres.cu):
+//   ar_dots:             h[s*ldh + k] = V_k . w per instance s (zero_flag, when
+//                        given, is set to 0 first)
+//   ar_axpy_dots:        w -= V coef_s, then h = V^T w
+//   ar_axpy_norm_update: w -= V h2_s, then the Givens update of column j from
+//                        h1, h2 and ||w||^2 (stat[j] collects the running flags)
+constexpr int kArMaxCols = 32;
+cudaError_t ar_dots(const KrChunks& ch, int nc, const double* V, int64_t ldv, const double* w, double* partial,
+                    int ldp, int* cnt, double* h, int ldh, int* zero_flag, cudaStream_t s);
+cudaError_t ar_axpy_dots(const KrChunks& ch, int nc, const double* V, int64_t ldv, const double* coef, int ldh,
+                         double* w, double* partial, int ldp, int* cnt, double* h, cudaStream_t s);
+cudaError_t ar_axpy_norm_update(const KrChunks& ch, int nc, const double* V, int64_t ldv, const double* h1,
+                                const double* h2, int ldh, double* w, double* partial, int ldp, int* cnt, int m, int j,
+                                const FgState& st, double rtol, int maxit, cudaStream_t s);
 // out[row] = in[row] * f[seg(row)] (0 when f is 0)
 cudaError_t seg_mul(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, const double* in,
                     double* out, const double* f, cudaStream_t s);

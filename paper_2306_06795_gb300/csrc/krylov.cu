@@ -95,6 +95,7 @@ template <typename T, int NV>
 __global__ void __launch_bounds__(kKrThreads) k_kdot(KrChunks ch, int nv, const T* __restrict__ A, int64_t lda,
     const T* __restrict__ B, T* __restrict__ copy, double* __restrict__ partial, int ldp, int* __restrict__ cnt,
     double* __restrict__ S, int lds, KrCols cols) {
+  pdl_enter();
   const int c = blockIdx.x;
   T acc[NV];
 #pragma unroll
@@ -155,6 +156,7 @@ template <typename T>
 __global__ void __launch_bounds__(kKrThreads) k_kaxpy_norm(KrChunks ch, int j, int k, const T* __restrict__ U,
     int64_t ldu, T* __restrict__ W, double* __restrict__ partial, int ldp, int* __restrict__ cnt,
     double* __restrict__ S, int lds) {
+  pdl_enter();
   __shared__ T cf[kKrMaxSteps];
   const int c = blockIdx.x;
   const double* q = S + (int64_t)ch.seg[c] * lds;
@@ -193,6 +195,7 @@ template <typename T>
 __global__ void __launch_bounds__(kKrThreads) k_kupdate(KrChunks ch, int k, const T* __restrict__ Z, int64_t ldz,
     const double* __restrict__ S, int lds, T* __restrict__ x, int set, double* __restrict__ x64,
     const uint8_t* __restrict__ dir, const double* __restrict__ r64, double* __restrict__ out64) {
+  pdl_enter();
   __shared__ T y[kKrMaxSteps];
   const int c = blockIdx.x;
   if (threadIdx.x < k) y[threadIdx.x] = T(S[(int64_t)ch.seg[c] * lds + 1 + k * (k + 1) + threadIdx.x]);
@@ -213,7 +216,7 @@ cudaError_t kr_norm0(const KrChunks& ch, const T* r, T* u0, double* partial, int
   if (ch.n == 0) return cudaSuccess;
   KrCols cols;
   cols.c[0] = 0;
-  k_kdot<T, 1><<<ch.n, kKrThreads, 0, st>>>(ch, 1, r, 0, r, u0 == r ? nullptr : u0, partial, ldp, cnt, S, lds, cols);
+  SD_LAUNCH((k_kdot<T, 1>), ch.n, kKrThreads, 0, st, ch, 1, r, 0, r, u0 == r ? nullptr : u0, partial, ldp, cnt, S, lds, cols);
   return cudaGetLastError();
 }
 
@@ -224,7 +227,7 @@ cudaError_t kr_project(const KrChunks& ch, int j, int k, const T* U, int64_t ldu
   if (j >= kKrMaxSteps || k > kKrMaxSteps) return cudaErrorInvalidValue;
   KrCols cols;
   for (int i = 0; i <= j; ++i) cols.c[i] = 1 + j * (k + 1) + i;
-  k_kdot<T, kKrMaxSteps><<<ch.n, kKrThreads, 0, st>>>(ch, j + 1, U, ldu, w, (T*)nullptr, partial, ldp, cnt, S, lds,
+  SD_LAUNCH((k_kdot<T, kKrMaxSteps>), ch.n, kKrThreads, 0, st, ch, j + 1, U, ldu, w, (T*)nullptr, partial, ldp, cnt, S, lds,
                                                       cols);
   return cudaGetLastError();
 }
@@ -234,7 +237,7 @@ cudaError_t kr_orthogonalise(const KrChunks& ch, int j, int k, const T* U, int64
                              int ldp, int* cnt, double* S, int lds, cudaStream_t st) {
   if (ch.n == 0) return cudaSuccess;
   if (j >= kKrMaxSteps || k > kKrMaxSteps) return cudaErrorInvalidValue;
-  k_kaxpy_norm<T><<<ch.n, kKrThreads, 0, st>>>(ch, j, k, U, ldu, w, partial, ldp, cnt, S, lds);
+  SD_LAUNCH((k_kaxpy_norm<T>), ch.n, kKrThreads, 0, st, ch, j, k, U, ldu, w, partial, ldp, cnt, S, lds);
   return cudaGetLastError();
 }
 
@@ -243,7 +246,7 @@ cudaError_t kr_update(const KrChunks& ch, int k, const T* Z, int64_t ldz, const 
                       double* x64, const uint8_t* dir, const double* r64, double* out64, cudaStream_t st) {
   if (ch.n == 0) return cudaSuccess;
   if (k > kKrMaxSteps) return cudaErrorInvalidValue;
-  k_kupdate<T><<<ch.n, kKrThreads, 0, st>>>(ch, k, Z, ldz, S, lds, x, set, x64, dir, r64, out64);
+  SD_LAUNCH((k_kupdate<T>), ch.n, kKrThreads, 0, st, ch, k, Z, ldz, S, lds, x, set, x64, dir, r64, out64);
   return cudaGetLastError();
 }
 

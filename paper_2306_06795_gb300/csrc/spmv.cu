@@ -12,6 +12,7 @@ __global__ void __launch_bounds__(256) k_spmv(int nrows, const int* __restrict__
                                               const TX* __restrict__ x, const TB* __restrict__ b,
                                               TY* __restrict__ y, double s0, double s1,
                                               const uint8_t* __restrict__ kind) {
+  pdl_enter();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = tid / TPR;
   const int lane = (int)(tid % TPR);
@@ -46,16 +47,16 @@ static cudaError_t launch_mode(const DevCSR& A, const TA* val, const TX* x, cons
   const unsigned blocks = (unsigned)((total + threads - 1) / threads);
   switch (mode) {
     case SPMV_SET:
-      k_spmv<TA, TX, TB, TY, TACC, TPR, SPMV_SET><<<blocks, threads, 0, st>>>(A.nrows, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv<TA, TX, TB, TY, TACC, TPR, SPMV_SET>), blocks, threads, 0, st, A.nrows, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
       break;
     case SPMV_RES:
-      k_spmv<TA, TX, TB, TY, TACC, TPR, SPMV_RES><<<blocks, threads, 0, st>>>(A.nrows, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv<TA, TX, TB, TY, TACC, TPR, SPMV_RES>), blocks, threads, 0, st, A.nrows, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
       break;
     case SPMV_ADD:
-      k_spmv<TA, TX, TB, TY, TACC, TPR, SPMV_ADD><<<blocks, threads, 0, st>>>(A.nrows, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv<TA, TX, TB, TY, TACC, TPR, SPMV_ADD>), blocks, threads, 0, st, A.nrows, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
       break;
     default:
-      k_spmv<TA, TX, TB, TY, TACC, TPR, SPMV_SCALED_RES><<<blocks, threads, 0, st>>>(A.nrows, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv<TA, TX, TB, TY, TACC, TPR, SPMV_SCALED_RES>), blocks, threads, 0, st, A.nrows, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
   }
   return cudaGetLastError();
 }
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(32 * kSellWarps) k_spmv_sell(int nrows, int nc
     const int64_t* __restrict__ soff, const int* __restrict__ scol, const TA* __restrict__ sval,
     const TX* __restrict__ x, const TB* __restrict__ b, TY* __restrict__ y, double s0, double s1,
     const uint8_t* __restrict__ kind) {
+  pdl_enter();
   const int c = blockIdx.x * kSellWarps + (threadIdx.x >> 5);
   if (c >= nchunks) return;
   const int lane = threadIdx.x & 31;
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_spmv_stream(const int4* __re
     const int* __restrict__ rowptr, const int* __restrict__ col, const TA* __restrict__ val,
     const TX* __restrict__ x, const TB* __restrict__ b, TY* __restrict__ y, double s0, double s1,
     const uint8_t* __restrict__ kind) {
+  pdl_enter();
   constexpr int PER = kStreamNnz / kStreamThreads;
   __shared__ TA sv[kStreamNnz];
   __shared__ TX sx[kStreamNnz];
@@ -185,16 +188,16 @@ static cudaError_t spmv_stream(const DevCSR& A, const TA* val, const TX* x, cons
   const unsigned blocks = (unsigned)A.stiles;
   switch (mode) {
     case SPMV_SET:
-      k_spmv_stream<TA, TX, TB, TY, TACC, SPMV_SET><<<blocks, kStreamThreads, 0, st>>>(A.tdesc, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv_stream<TA, TX, TB, TY, TACC, SPMV_SET>), blocks, kStreamThreads, 0, st, A.tdesc, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
       break;
     case SPMV_RES:
-      k_spmv_stream<TA, TX, TB, TY, TACC, SPMV_RES><<<blocks, kStreamThreads, 0, st>>>(A.tdesc, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv_stream<TA, TX, TB, TY, TACC, SPMV_RES>), blocks, kStreamThreads, 0, st, A.tdesc, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
       break;
     case SPMV_ADD:
-      k_spmv_stream<TA, TX, TB, TY, TACC, SPMV_ADD><<<blocks, kStreamThreads, 0, st>>>(A.tdesc, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv_stream<TA, TX, TB, TY, TACC, SPMV_ADD>), blocks, kStreamThreads, 0, st, A.tdesc, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
       break;
     default:
-      k_spmv_stream<TA, TX, TB, TY, TACC, SPMV_SCALED_RES><<<blocks, kStreamThreads, 0, st>>>(A.tdesc, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv_stream<TA, TX, TB, TY, TACC, SPMV_SCALED_RES>), blocks, kStreamThreads, 0, st, A.tdesc, A.rowptr, A.col, val, x, b, y, s0, s1, kind);
   }
   return cudaGetLastError();
 }
@@ -210,16 +213,16 @@ static cudaError_t spmv_sell(const DevCSR& A, const TA* sval, const TX* x, const
   const int threads = 32 * kSellWarps;
   switch (mode) {
     case SPMV_SET:
-      k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_SET><<<blocks, threads, 0, st>>>(A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_SET>), blocks, threads, 0, st, A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
       break;
     case SPMV_RES:
-      k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_RES><<<blocks, threads, 0, st>>>(A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_RES>), blocks, threads, 0, st, A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
       break;
     case SPMV_ADD:
-      k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_ADD><<<blocks, threads, 0, st>>>(A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_ADD>), blocks, threads, 0, st, A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
       break;
     default:
-      k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_SCALED_RES><<<blocks, threads, 0, st>>>(A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
+      SD_LAUNCH((k_spmv_sell<TA, TX, TB, TY, TACC, SPMV_SCALED_RES>), blocks, threads, 0, st, A.nrows, A.schunks, A.soff, A.scol, sval, x, b, y, s0, s1, kind);
   }
   return cudaGetLastError();
 }

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kFacThreads) k_vanka_factor(int nlist, const i
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
     const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing,
     int max_m, int max_np, T* __restrict__ gA, int nsmall) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if ((int)blockIdx.x >= nlist) return;
   const int i = list[blockIdx.x];
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(kFacWarps * 32) k_vanka_factor_warp(int nlist,
     int dim, int shared, const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
     const int* __restrict__ col, const double* __restrict__ Kval, T* __restrict__ fac, int* nsing, int nsmall) {
+  pdl_enter();
   using L = FacWarpSmem<T, MAXM>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -400,7 +402,7 @@ static cudaError_t launch_factor_warp(const DevPatches& p, const DevCSR& K, int 
   if (count == 0) return cudaSuccess;
   const size_t shm = kFacWarps * FacWarpSmem<T, MAXM>::bytes();
   const unsigned blocks = (unsigned)((count + kFacWarps - 1) / kFacWarps);
-  k_vanka_factor_warp<T, MAXM><<<blocks, kFacWarps * 32, shm, st>>>(count, p.fac_list + start, p.dim, p.shared,
+  SD_LAUNCH((k_vanka_factor_warp<T, MAXM>), blocks, kFacWarps * 32, shm, st, count, p.fac_list + start, p.dim, p.shared,
       p.ptr, p.dof, p.nvel, p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<T*>(p.fac), nsingular, p.nsmall);
   return cudaGetLastError();
 }
@@ -437,7 +439,7 @@ cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, c
   } else {
     if (p.nfac_smem > 0) {
       const size_t shm = vanka_factor_smem(dm, p.max_m_fac_smem, p.max_np, sizeof(T), false);
-      k_vanka_factor<T><<<p.nfac_smem, kFacThreads, shm, st>>>(p.nfac_smem, p.fac_list + start, dm, p.shared, p.ptr,
+      SD_LAUNCH((k_vanka_factor<T>), p.nfac_smem, kFacThreads, shm, st, p.nfac_smem, p.fac_list + start, dm, p.shared, p.ptr,
                                                                p.dof, p.nvel, p.npres, p.foff, K.rowptr, K.col, K.v64,
                                                                reinterpret_cast<T*>(p.fac), nsingular,
                                                                p.max_m_fac_smem, p.max_np, (T*)nullptr, p.nsmall);
@@ -449,7 +451,7 @@ cudaError_t vanka_factor(const DevPatches& p, const DevCSR& K, int* nsingular, c
     for (int c0 = 0; c0 < nglob; c0 += p.fac_chunk) {
       const int cnt = std::min(p.fac_chunk, nglob - c0);
       const size_t shm = vanka_factor_smem(dm, p.max_m, p.max_np, sizeof(T), true);
-      k_vanka_factor<T><<<cnt, kFacThreads, shm, st>>>(cnt, p.fac_list + start + c0, dm, p.shared, p.ptr, p.dof,
+      SD_LAUNCH((k_vanka_factor<T>), cnt, kFacThreads, shm, st, cnt, p.fac_list + start + c0, dm, p.shared, p.ptr, p.dof,
                                                        p.nvel, p.npres, p.foff, K.rowptr, K.col, K.v64,
                                                        reinterpret_cast<T*>(p.fac), nsingular, p.max_m, p.max_np,
                                                        reinterpret_cast<T*>(p.fac_scratch), p.nsmall);
@@ -494,6 +496,7 @@ __global__ void __launch_bounds__(32 * (kNCW + 1)) k_vanka_apply_tma(
     const int4* __restrict__ meta, const int* __restrict__ pptr, const int64_t* __restrict__ foff,
     const int* __restrict__ dof, const int* __restrict__ pdst, const T* __restrict__ fac, const TR* __restrict__ r,
     T* __restrict__ yp, int* __restrict__ err) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + stages;
@@ -690,7 +693,7 @@ template <typename T, typename TR, int DIM, int NPM, int LP, int R>
 static cudaError_t launch_tma_bin(const DevPatches& p, const TmaBin& bn, const TR* r, T* yp, cudaStream_t st) {
   const size_t shm = 128 + (size_t)bn.stages * (bn.fac_bytes + 2 * bn.dof_bytes + bn.tp * 16) +
                      (size_t)kNCW * bn.rhs_elems * sizeof(T);
-  k_vanka_apply_tma<T, TR, DIM, NPM, LP, R><<<bn.grid, 32 * (kNCW + 1), shm, st>>>(
+  SD_LAUNCH((k_vanka_apply_tma<T, TR, DIM, NPM, LP, R>), bn.grid, 32 * (kNCW + 1), shm, st, 
       bn.start, bn.count, bn.ntiles, bn.tp, bn.stages, bn.fac_bytes, bn.dof_bytes, bn.rhs_elems, p.shared, p.meta,
       p.ptr, p.foff, p.dof, p.pdst, reinterpret_cast<const T*>(p.fac), r, yp, p.err);
   return cudaGetLastError();
@@ -828,6 +831,7 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_vanka_scatter(int64_t n, const int* __restrict__ tptr,
     const T* __restrict__ yp, T* __restrict__ x, T omega, const uint8_t* __restrict__ dir,
     const double* __restrict__ r64, double* __restrict__ out64, double* __restrict__ x64) {
+  pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int b = tptr[j], e = tptr[j + 1];
@@ -855,11 +859,11 @@ cudaError_t vanka_scatter(const DevPatches& p, int64_t n, const T* yp, T* x, dou
   if (n == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (mode == 0)
-    k_vanka_scatter<T, 0><<<blocks, 256, 0, st>>>(n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
+    SD_LAUNCH((k_vanka_scatter<T, 0>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
   else if (mode == 1)
-    k_vanka_scatter<T, 1><<<blocks, 256, 0, st>>>(n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
+    SD_LAUNCH((k_vanka_scatter<T, 1>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
   else
-    k_vanka_scatter<T, 2><<<blocks, 256, 0, st>>>(n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
+    SD_LAUNCH((k_vanka_scatter<T, 2>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
   return cudaGetLastError();
 }
 template cudaError_t vanka_scatter<float>(const DevPatches&, int64_t, const float*, float*, double, int,

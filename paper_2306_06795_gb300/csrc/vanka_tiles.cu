@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(NTHR, 512 / NTHR) k_vanka_factor_tc(int nlist,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
     const int* __restrict__ col, const double* __restrict__ Kval, float* __restrict__ fac, int* nsing, int rows_max,
     int max_np, int nsmall, float* __restrict__ gscr) {
+  pdl_enter();
   constexpr int NW = NTHR / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if ((int)blockIdx.x >= nlist) return;
@@ -481,7 +482,7 @@ template <int NTHR>
 static cudaError_t launch_factor_tc(const DevPatches& p, const DevCSR& K, const int* list, int cnt, int rows,
                                     float* gscr, int* nsingular, cudaStream_t st) {
   const size_t shm = vanka_factor_tc_smem(p.dim, rows, p.max_np, gscr != nullptr);
-  k_vanka_factor_tc<NTHR><<<cnt, NTHR, shm, st>>>(cnt, list, p.dim, p.shared, p.ptr, p.dof, p.nvel, p.npres, p.foff,
+  SD_LAUNCH((k_vanka_factor_tc<NTHR>), cnt, NTHR, shm, st, cnt, list, p.dim, p.shared, p.ptr, p.dof, p.nvel, p.npres, p.foff,
                                                   K.rowptr, K.col, K.v64, reinterpret_cast<float*>(p.fac), nsingular,
                                                   rows, p.max_np, p.nsmall, gscr);
   return cudaGetLastError();
@@ -595,6 +596,7 @@ __global__ void __launch_bounds__(64 * kTilePairs, 2) k_vanka_apply_tiles(int nl
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ dof,
     const int* __restrict__ pdst, const T* __restrict__ fac, const TR* __restrict__ r, T* __restrict__ yp,
     int* __restrict__ err) {
+  pdl_enter();
   constexpr int BS = NodeStride<DIM>::v;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -804,7 +806,7 @@ cudaError_t vanka_apply_tiles(const DevPatches& p, const TR* r, T* yp, cudaStrea
   const size_t shm = vanka_tiles_smem(p.tiles_stages, p.tiles_nodes, p.dim, sizeof(T));
   const bool one = p.max_np <= 1;
 #define SD_TILES_LAUNCH(D, NP)                                                                                     \
-  k_vanka_apply_tiles<T, TR, D, NP><<<p.tiles_grid, 64 * kTilePairs, shm, st>>>(                                   \
+  SD_LAUNCH((k_vanka_apply_tiles<T, TR, D, NP>), p.tiles_grid, 64 * kTilePairs, shm, st,                                    \
       p.nlarge, p.large, p.tiles_stages, p.tiles_nodes, p.shared, p.ptr, p.nvel, p.npres, p.foff, p.dof, p.pdst,   \
       reinterpret_cast<const T*>(p.fac), r, yp, p.err)
   if (p.dim == 2) {

@@ -120,6 +120,13 @@ def test_c4_full_size_sampled_vanka_and_solve(sd, c4):
         dofs = rng.choice(covered, size=40, replace=False)
         ref = vanka.sampled_apply(c4.K[l], c4.patches[l], r, dofs)
         assert rel(host(y)[dofs], ref) < 1e-11, l
+    # the coarsest relaxed level (a few hundred large patches) in full
+    lc = c4.nlevels - 2
+    n = c4.K[lc].shape[0]
+    r = rng.standard_normal(n)
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    sd.stokes_level_op(h64, sd.STOKES_OP_VANKA, lc, dev(r), None, y)
+    assert rel(host(y), vanka.VankaLevel(c4.K[lc], c4.patches[lc]).apply(r)) < 1e-11
     # FP32 and FP64 preconditioned solves reach 1e-8 within +-2 iterations
     b = dev(c4.b)
     its = {}
@@ -173,14 +180,28 @@ def test_c5_full_batch_solves_every_instance(sd):
         assert info[k][2] <= 1e-8
         assert np.linalg.norm(p.b - p.K[0] @ xh[o:o + n]) <= 1.01e-8 * np.linalg.norm(p.b)
         o += n
-    # FP64 cycle of the whole batch against the oracle on the smallest instance
+    # FP64 cycle of the whole batch against the oracle on the smallest, the
+    # largest, the shallowest and the deepest instance
     h64 = sd.stokes_setup(probs, dict(prm, precision=sd.STOKES_FP64))
     sd.stokes_factor_patches(h64)
     r = np.random.default_rng(34).standard_normal(b.size)
     z = torch.empty(b.size, dtype=torch.float64, device="cuda")
     sd.stokes_vcycle(h64, dev(r), z)
     zh = host(z)
-    k = int(np.argmin([p.b.size for p in probs]))
-    o = sum(p.b.size for p in probs[:k])
-    n = probs[k].b.size
-    assert rel(zh[o:o + n], make_oracle(probs[k], prm).apply(r[o:o + n])) < 1e-12
+    sizes = [p.b.size for p in probs]
+    depth = [p.nlevels for p in probs]
+    picks = {int(np.argmin(sizes)), int(np.argmax(sizes)), int(np.argmin(depth)), int(np.argmax(depth))}
+    assert min(depth) < max(depth)
+    for k in sorted(picks):
+        o = sum(sizes[:k])
+        n = sizes[k]
+        assert rel(zh[o:o + n], make_oracle(probs[k], prm).apply(r[o:o + n])) < 1e-12, k
+    # the smallest instance's FP32-preconditioned solution against the oracle's
+    from oracle import direct
+    k = int(np.argmin(sizes))
+    p = probs[k]
+    o = sum(sizes[:k])
+    xo, _, _ = krylov.fgmres(p.K[0], p.b, make_oracle(p, prm).apply, rtol=1e-8, restart=30, maxit=600)
+    off = p.field_off[0]
+    assert rel(direct.zero_mean_pressure(xh[o:o + sizes[k]], off, 2, p.Mp),
+               direct.zero_mean_pressure(xo, off, 2, p.Mp)) < 1e-5

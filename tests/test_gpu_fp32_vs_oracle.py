@@ -1,0 +1,57 @@
+"""The FP32-preconditioned solve against the oracle's FP64 solution, per
+config: the oracle's FGMRES(30) with the FP64 DC cycle (MGS Arnoldi) and the
+library's FGMRES with the FP32 cycle both solve to a 1e-8 relative true
+residual from x0 = 0; the solutions, pressure shifted to zero mass-weighted
+mean (the solution is unique up to that constant), agree to 1e-5 relative
+(worst element and 2-norm).  Where the oracle is too slow at the config's
+full size the same problem is taken on a smaller mesh, as named per case."""
+import numpy as np
+import pytest
+
+from oracle import direct, krylov
+from problems import configs
+from tests.helpers import make_oracle, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# name: (problem, parameters, size note)
+CASES = {
+    "C1 TH2D 16^2 lid (full size)": (configs.c1, lambda pr: configs.TH2D_VANKA),
+    "C2 TH2D manufactured at 64^2 (full size 256^2)": (lambda: configs.c2(64), lambda pr: configs.TH2D_VANKA),
+    "C2 DLSC-AMG at 64^2": (lambda: configs.c2(64), lambda pr: configs.th2d_dlsc(pr.nlevels)),
+    "C3 SV2D Vanka at 32^2 (full size 128^2)": (lambda: configs.c3(32), lambda pr: configs.SV2D_VANKA),
+    "C3 SV2D Vanka + DLSC at 32^2": (lambda: configs.c3(32), lambda pr: configs.sv_vanka_dlsc(pr.nlevels)),
+    "C4 TH3D lid at 8^3 (full size 32^3)": (lambda: configs.c4(8), lambda pr: configs.TH3D_VANKA),
+}
+
+
+@pytest.fixture(scope="module")
+def sd():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2306_06795_gb300 as sd
+    return sd
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp32_solution_matches_the_oracle_solution(sd, name):
+    make, params = CASES[name]
+    pr = make()
+    prm = params(pr)
+    o = make_oracle(pr, prm)
+    xo, its_o, rr_o = krylov.fgmres(pr.K[0], pr.b, o.apply, rtol=1e-8, restart=30, maxit=600)
+    assert rr_o <= 1e-8
+    h = sd.stokes_setup(pr, dict(prm, precision=sd.STOKES_FP32))
+    sd.stokes_factor_patches(h)
+    b = torch.tensor(pr.b, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    rc, info = sd.stokes_fgmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=600)
+    assert rc == sd.STOKES_OK and info[0][2] <= 1e-8
+    torch.cuda.synchronize()
+    off, d = pr.field_off[0], pr.dim
+    x32 = direct.zero_mean_pressure(x.cpu().numpy(), off, d, pr.Mp)
+    xoz = direct.zero_mean_pressure(xo, off, d, pr.Mp)
+    err = rel(x32, xoz)
+    print(f"{name}: FP32 vs oracle solution {err:.2e}; iterations {info[0][0]} (oracle FP64 {its_o})")
+    assert err < 1e-5
+    assert abs(info[0][0] - its_o) <= 2
