@@ -8,18 +8,15 @@
 namespace sd {
 
 // Programmatic dependent launch.  A kernel launched by launch_pdl may be
-// scheduled while the previous kernel of its stream is still finishing;
+// set up while the previous kernel of its stream is still finishing;
 // pdl_enter(), the first statement of every kernel of the solve path, waits
 // until that previous grid has completed and its writes are visible
-// (griddepcontrol.wait) and then lets the next kernel of the stream be
-// scheduled (griddepcontrol.launch_dependents), so the semantics stay
-// those of plain stream order while the launch latency overlaps the
-// previous kernel's tail.  Without a programmatic dependency both
-// instructions return at once.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// (griddepcontrol.wait), so the semantics stay those of plain stream order.
+// No kernel triggers its dependents early (griddepcontrol.launch_dependents):
+// measured on the C2 cycle, an early trigger made it slower (0.320 against
+// 0.309 ms without PDL), the implicit trigger at grid exit faster (0.304 ms).
+// Without a programmatic dependency the wait returns at once.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_wait() { pdl_enter(); }
 
 template <typename... KArgs, typename... Args>

@@ -291,21 +291,34 @@ __global__ void __launch_bounds__(kArThreads) k_ar_axpy_norm(KrChunks ch, const 
   if (threadIdx.x < NK) cf[threadIdx.x] = h2buf[(int64_t)s * ldh + threadIdx.x];
   __syncthreads();
   double acc[1] = {0.0};
-  constexpr int G = 8;
+  // P rows per thread per step with their column loads issued together
+  // (the pass reads V once, from DRAM: more loads in flight)
+  constexpr int G = 8, P = 4;
   const int64_t re = ch.end[c];
-  for (int64_t r = ch.beg[c] + threadIdx.x; r < re; r += kArThreads) {
-    double t = w[r];
+  for (int64_t r = ch.beg[c] + threadIdx.x; r < re; r += kArThreads * P) {
+    double t[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) t[p] = r + p * kArThreads < re ? w[r + p * kArThreads] : 0.0;
 #pragma unroll
     for (int k0 = 0; k0 < NK; k0 += G) {
-      double v[G];
+      double v[P][G];
 #pragma unroll
-      for (int k = 0; k < G; ++k) v[k] = k0 + k < NK ? V[(int64_t)(k0 + k) * ldv + r] : 0.0;
+      for (int p = 0; p < P; ++p)
 #pragma unroll
-      for (int k = 0; k < G; ++k)
-        if (k0 + k < NK) t = fma(-cf[k0 + k], v[k], t);
+        for (int k = 0; k < G; ++k)
+          v[p][k] = k0 + k < NK && r + p * kArThreads < re ? V[(int64_t)(k0 + k) * ldv + r + p * kArThreads] : 0.0;
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int k = 0; k < G; ++k)
+          if (k0 + k < NK) t[p] = fma(-cf[k0 + k], v[p][k], t[p]);
     }
-    w[r] = t;
-    acc[0] = fma(t, t, acc[0]);
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      if (r + p * kArThreads < re) {
+        w[r + p * kArThreads] = t[p];
+        acc[0] = fma(t[p], t[p], acc[0]);
+      }
   }
   ar_block_sums<1>(acc, red, bsum);
   if (ar_complete<1>(ch, c, bsum, partial, ldp, cnt, tot))
@@ -355,7 +368,7 @@ cudaError_t ar_dots(const KrChunks& ch, int nc, const double* V, int64_t ldv, co
   switch (nc) {
 #define SD_AR_DOTS(K)                                                                                           \
   case K:                                                                                                      \
-    return launch_pdl(k_ar_dots<K, (K >= 16 ? 2 : 1)>, dim3(ch.n), dim3(kArThreads), 0, s, ch, V, ldv, w,     \
+    return launch_pdl(k_ar_dots<K, 4>, dim3(ch.n), dim3(kArThreads), 0, s, ch, V, ldv, w,                       \
                       partial, ldp, cnt, h, ldh, zero_flag);
     SD_AR_CASES(SD_AR_DOTS)
 #undef SD_AR_DOTS
