@@ -10,8 +10,16 @@ in HBM; the cycle's working set (~1 GB) is far above L2, so no flush is
 needed between steps.
 
 Lines: the default arm prints the GPU line (value = solves/s over all ranks;
-N > 1 runs N independent replicas, scaling "weak").  --impl reference times
-the FP64 CPU oracle on a bounded sample on rank 0 only.
+N > 1 runs N independent replicas, scaling "weak").  At N = 1 the line also
+carries, untimed by the headline: the FP64-preconditioned form, the
+Krylov-wrapped and BTP variants, the paper's own solver setting on C2
+(FGMRES(20), residual reduced by 1e10), compact records of the other configs
+(C1, C2 with DLSC-AMG, C3 with Vanka and with Vanka + DLSC and the
+divergence of its solution, C4 with stationary and Krylov-wrapped Vanka, the
+C5 batch), the FP32-preconditioned solution's error against the oracle's
+solution on reduced sizes, and the CPU baseline (the oracle on the host
+cores, single thread and all cores).  --impl reference times the FP64 CPU
+oracle on a bounded sample on rank 0 only.
 """
 import os
 
@@ -135,55 +143,266 @@ def measured_peak():
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(pr, prm, iters=2):
-    """Time the FP64 oracle on a bounded sample of one solve: its setup
-    (dense patch matrices) and `iters` FGMRES iterations."""
+# The oracle runs in spawned worker processes, one thread each (the
+# environment above pins the BLAS threads), only in the cpu_baseline leg and
+# in the reference arm.
+def _oracle_c2_sample(_=None):
+    """Bounded sample of the C2 solve by the FP64 oracle: its setup (dense
+    patch factorisations), one DC cycle and one FGMRES iteration."""
     from oracle import krylov
+    from problems import configs
     from tests.helpers import make_oracle
 
+    pr = configs.c2()
+    prm = dict(configs.TH2D_VANKA)
     t0 = time.perf_counter()
     o = make_oracle(pr, prm)
     t1 = time.perf_counter()
-    krylov.fgmres(pr.K[0], pr.b, o.apply, rtol=1e-30, restart=30, maxit=iters)
+    o.apply(pr.b)
     t2 = time.perf_counter()
-    return t1 - t0, (t2 - t1) / iters
+    krylov.fgmres(pr.K[0], pr.b, o.apply, rtol=1e-30, restart=30, maxit=1)
+    t3 = time.perf_counter()
+    return {"setup_s": t1 - t0, "cycle_s": t2 - t1, "iter_s": t3 - t2}
 
 
-def cpu_line(pr, prm, solve_iters, iters=2):
-    setup_s, iter_s = oracle_sample(pr, prm, iters)
-    per_solve = setup_s + solve_iters * iter_s
-    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle setup + {iters} FGMRES iterations on the same problem, scaled to a "
-                      f"{solve_iters}-iteration solve ({setup_s:.1f} s setup, {iter_s:.2f} s/iteration)"}
+def _oracle_reduced_solve(name):
+    """The oracle's FGMRES(30) solve to 1e-8 of a reduced-size config;
+    returns its solution with the pressure shifted to zero mean."""
+    from oracle import direct, krylov
+    from problems import configs
+    from tests.helpers import make_oracle
+
+    make, params, note = configs.reduced_cases()[name]
+    pr = make()
+    t0 = time.perf_counter()
+    o = make_oracle(pr, params(pr))
+    x, its, rr = krylov.fgmres(pr.K[0], pr.b, o.apply, rtol=1e-8, restart=30, maxit=600)
+    t1 = time.perf_counter()
+    return {"name": name, "note": note, "iters": its, "true_relres": rr, "seconds": t1 - t0,
+            "x": direct.zero_mean_pressure(x, pr.field_off[0], pr.dim, pr.Mp)}
+
+
+def _pool(workers):
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    return ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+
+def _available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return float(line.split()[1]) / 1e6
+    except Exception:
+        pass
+    return 0.0
+
+
+def cpu_baseline(solve_iters, reduced=True):
+    """The FP64 oracle on the host cores, bounded samples of the C2 solve:
+    one process alone (single thread), then as many concurrent single-thread
+    processes as cores (capped by memory, about 3 GB each), each timing the
+    same sample; plus, when `reduced`, the oracle's full solves of the
+    reduced-size configs (their solutions are returned for comparison)."""
+    cores = os.cpu_count() or 1
+    with _pool(1) as ex:
+        one = ex.submit(_oracle_c2_sample).result()
+    per_solve = one["setup_s"] + solve_iters * one["iter_s"]
+    nproc = max(1, min(cores, int(_available_gb() // 3.5)))
+    with _pool(nproc) as ex:
+        many = list(ex.map(_oracle_c2_sample, range(nproc)))
+    agg = sum(1.0 / (m["setup_s"] + solve_iters * m["iter_s"]) for m in many)
+    out = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+           "sample": (f"C2: oracle setup ({one['setup_s']:.1f} s), one DC cycle ({one['cycle_s']:.2f} s) and one "
+                      f"FGMRES iteration ({one['iter_s']:.2f} s), measured; the solve time is extrapolated to "
+                      f"setup + {solve_iters} iterations (the GPU solve's count)"),
+           "vcycle_ms": 1e3 * one["cycle_s"], "setup_s": one["setup_s"], "iter_s": one["iter_s"],
+           "all_cores": {"value": agg, "unit": "solves/s", "cores": nproc,
+                         "sample": f"{nproc} concurrent single-thread processes, each the same sample, extrapolated "
+                                   f"the same way; value = sum of their rates",
+                         "vcycle_ms_mean": 1e3 * float(np.mean([m["cycle_s"] for m in many]))}}
+    if reduced:
+        from problems import configs
+        names = list(configs.reduced_cases())
+        with _pool(min(len(names), cores)) as ex:
+            sols = list(ex.map(_oracle_reduced_solve, names))
+        out["oracle_solves"] = {r["name"]: {k: v for k, v in r.items() if k != "name"} for r in sols}
+        c2 = out["oracle_solves"].get("C2")
+        if c2:
+            out["measured_solve"] = {"workload": "C2 at 64^2 (the same problem on a 64^2 mesh)", "seconds": c2["seconds"],
+                                     "iters": c2["iters"], "cores": 1}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores.  Each step is the
+    bounded sample of _oracle_c2_sample (setup, one cycle, one iteration,
+    single thread); ms_per_step is that measured sample, value the C2 solve
+    rate extrapolated from it (setup + ref_iters iterations)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from problems import configs
-    pr = configs.c2()
-    prm = dict(configs.TH2D_VANKA)
-    solve_iters = args.ref_iters
-    vals = []
-    for s in range(args.warmup + args.steps):
-        setup_s, iter_s = oracle_sample(pr, prm, iters=1)
-        if s >= args.warmup:
-            vals.append(setup_s + solve_iters * iter_s)
-    per = float(np.mean(vals))
-    v = 1.0 / per
+    samples = []
+    with _pool(1) as ex:
+        for s in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r = ex.submit(_oracle_c2_sample).result()
+            r["wall_s"] = time.perf_counter() - t0
+            if s >= args.warmup:
+                samples.append(r)
+    setup = float(np.mean([r["setup_s"] for r in samples]))
+    it = float(np.mean([r["iter_s"] for r in samples]))
+    cyc = float(np.mean([r["cycle_s"] for r in samples]))
+    step_ms = 1e3 * float(np.mean([r["setup_s"] + r["cycle_s"] + r["iter_s"] for r in samples]))
+    v = 1.0 / (setup + args.ref_iters * it)
+    sample = (f"each step: oracle setup + one DC cycle + one FGMRES iteration on C2 (single thread, measured; "
+              f"ms_per_step is this sample); value extrapolates a solve as setup + {args.ref_iters} iterations")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": "single process, host cores"},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: oracle setup + 1 FGMRES iteration, scaled to a "
-                                       f"{solve_iters}-iteration solve"},
+            "value_basis": "extrapolated from the measured per-step sample",
+            "vcycle_ms": 1e3 * cyc,
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- GPU arm
+def _zero_mean_pressure(pr, x):
+    """Shift the pressure to zero mass-weighted mean 1^T Mp p = 0 (the
+    solution is unique up to that constant)."""
+    off, d = pr.field_off[0], pr.dim
+    x = np.array(x, dtype=np.float64)
+    p = x[off[d]:off[d + 1]]
+    one = np.ones(p.size)
+    x[off[d]:off[d + 1]] = p - (one @ (pr.Mp @ p)) / (one @ (pr.Mp @ one))
+    return x
+
+
+def _relerr(a, b):
+    """The larger of the 2-norm and the worst-element relative differences."""
+    d = a - b
+    return float(max(np.linalg.norm(d) / np.linalg.norm(b), np.max(np.abs(d)) / np.max(np.abs(b))))
+
+
+def _solve_record(sd, torch, pr, prm, prec, stream, reps=2, warm=1, rtol=1e-8, restart=30, maxit=600, cycle=True):
+    """Factorisation + FGMRES solve from x0 = 0 timed on the device (CUDA
+    events, `reps` steps after `warm`), and the V-cycle alone; returns the
+    record and the solution."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    h = sd.stokes_setup(pr, dict(prm, precision=prec), stream=stream.cuda_stream)
+    b = torch.tensor(pr.b, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+    rec = {}
+    with torch.cuda.stream(stream):
+        def step():
+            sd.stokes_factor_patches(h)
+            x.zero_()
+            return sd.stokes_fgmres_solve(h, b, x, rtol=rtol, restart=restart, maxit=maxit)
+        for _ in range(warm):
+            rc, info = step()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            rc, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        iters = [i[0] for i in info]
+        rec = {"status": int(rc), "iters": int(max(iters)), "true_relres": float(max(i[2] for i in info)),
+               "ms_per_solve": e0.elapsed_time(e1) / reps}
+        if len(info) > 1:
+            rec["iters_min"] = int(min(iters))
+        if cycle:
+            z = torch.empty_like(b)
+            for _ in range(3):
+                sd.stokes_vcycle(h, b, z)
+            e0.record(stream)
+            for _ in range(10):
+                sd.stokes_vcycle(h, b, z)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rec["vcycle_ms"] = e0.elapsed_time(e1) / 10
+            rec["cycle_GBps"] = sd.stokes_cycle_bytes(h) / rec["vcycle_ms"] / 1e6
+    xs = x.cpu().numpy()
+    sd.stokes_destroy(h)
+    return rec, xs
+
+
+def config_records(sd, torch, stream, c2):
+    """Compact records of the other configs (full size, FP32- and
+    FP64-preconditioned solves to 1e-8), and the FP32 solutions of the
+    reduced-size configs the oracle solves in the cpu_baseline leg."""
+    from problems import configs, stokes
+    fp32, fp64 = sd.STOKES_FP32, sd.STOKES_FP64
+    out = {}
+
+    def both(name, pr, prm, fp64_reps=2, extra=None):
+        r32, x32 = _solve_record(sd, torch, pr, prm, fp32, stream)
+        r64, x64 = _solve_record(sd, torch, pr, prm, fp64, stream, reps=fp64_reps)
+        rec = {"dofs": int(pr.b.size), "levels": int(pr.nlevels), "fp32": r32, "fp64": r64,
+               "fp32_vs_fp64_solution_relerr": _relerr(_zero_mean_pressure(pr, x32), _zero_mean_pressure(pr, x64))}
+        if extra:
+            rec.update(extra(pr, x32))
+        out[name] = rec
+
+    def divergence(pr, x):
+        off = pr.field_off[0]
+        A = pr.K[0][: off[2], : off[2]]
+        energy = float(np.sqrt(x[: off[2]] @ (A @ x[: off[2]])))
+        return {"divergence_norm_fp32": stokes.divergence_norm(pr, x), "velocity_energy_norm": energy}
+
+    both("C1 TH2D 16^2 lid, Vanka", configs.c1(), configs.TH2D_VANKA)
+    both("C2 TH2D 256^2, DLSC-AMG (DLSC on every level)", c2, configs.th2d_dlsc(c2.nlevels))
+    c3 = configs.c3()
+    both("C3 SV2D 128^2, Vanka", c3, configs.SV2D_VANKA, extra=divergence)
+    both("C3 SV2D 128^2, Vanka on level 0 + DLSC below", c3, configs.sv_vanka_dlsc(c3.nlevels), extra=divergence)
+    del c3
+    c4 = configs.c4()
+    both("C4 TH3D 32^3 lid, stationary Vanka", c4, configs.TH3D_VANKA, fp64_reps=1)
+    kr = dict(schedule=0, nu1=2, nu2=2, eta_u=1.0, eta_p=1.0, omega=1.0,
+              relax=[sd.STOKES_RELAX_VANKA_KRYLOV] * (c4.nlevels - 1))
+    r, _ = _solve_record(sd, torch, c4, kr, fp32, stream)
+    out["C4 TH3D 32^3 lid, Krylov-wrapped Vanka (2 steps per level)"] = {"dofs": int(c4.b.size), "fp32": r}
+    del c4
+    # the batched workload: all 64 instances in one handle
+    probs = configs.c5()
+    h = sd.stokes_setup(probs, dict(configs.TH2D_VANKA, precision=fp32), stream=stream.cuda_stream)
+    b = torch.tensor(np.concatenate([p.b for p in probs]), dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    with torch.cuda.stream(stream):
+        def step():
+            sd.stokes_factor_patches(h)
+            x.zero_()
+            return sd.stokes_fgmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=600)
+        step()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rc, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    its = [i[0] for i in info]
+    out["C5 64 TH2D instances, n ~ U{32..192}, one handle"] = {
+        "dofs": int(b.numel()), "instances": len(probs), "instances_per_s": len(probs) * 1000.0 / ms,
+        "ms_per_batch": ms, "status": int(rc), "iters_min": int(min(its)), "iters_max": int(max(its)),
+        "true_relres_max": float(max(i[2] for i in info))}
+    sd.stokes_destroy(h)
+    del probs
+    # FP32 solutions of the reduced sizes, for the comparison with the oracle
+    reduced = {}
+    for name, (make, params, note) in configs.reduced_cases().items():
+        pr = make()
+        _, x32 = _solve_record(sd, torch, pr, params(pr), fp32, stream, reps=1, cycle=False)
+        reduced[name] = _zero_mean_pressure(pr, x32)
+    return out, reduced
+
+
 def run_gpu(args):
     import torch
 
@@ -417,8 +636,26 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
-    if args.cpu_baseline:
-        line["cpu_baseline"] = cpu_line(pr, prm, int(info64[0]))
+    if ws == 1 and args.configs:
+        with torch.cuda.stream(stream):
+            # the paper's own solver setting (Sec. 4): FGMRES(20), residual reduced by 1e10
+            ps = {}
+            for prec, nm in ((sd.STOKES_FP32, "fp32"), (sd.STOKES_FP64, "fp64")):
+                ps[nm], _ = _solve_record(sd, torch, pr, prm, prec, stream, rtol=1e-10, restart=20, cycle=False)
+            line["paper_setting"] = {"solver": "FGMRES(20) to a 1e-10 relative residual (Sec. 4)", **ps}
+            recs, reduced = config_records(sd, torch, stream, pr)
+        line["configs"] = recs
+    if args.cpu_baseline and ws == 1:
+        cb = cpu_baseline(int(info32[0]), reduced=args.configs)
+        solves = cb.pop("oracle_solves", {})
+        fp32_vs_oracle = {}
+        for name, r in solves.items():
+            if args.configs and name in reduced:
+                fp32_vs_oracle[name] = {"relerr": _relerr(reduced[name], r["x"]), "at": r["note"],
+                                        "oracle_iters": r["iters"]}
+        if fp32_vs_oracle:
+            line["fp32_vs_oracle_solution"] = fp32_vs_oracle
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -527,81 +764,6 @@ def run_gpu_c5(args):
         dist.destroy_process_group()
 
 
-def run_gpu_configs(args):
-    """One JSON line per config (C1, C2, C3 with Vanka and with DLSC on the
-    coarse levels, C4): FP32- and FP64-preconditioned solves to 1e-8 from
-    x0 = 0 (factorisation + FGMRES per step), iterations, true residuals,
-    the FP32 solution's error against the FP64 one, and the FP32 V-cycle
-    time.  Context for the C2 headline; rank 0 only."""
-    import torch
-
-    import paper_2306_06795_gb300 as sd
-    from problems import configs
-
-    ws, rank, local = dist_env()
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(device=dev)
-    cases = [("C1 TH2D 16^2 lid", configs.c1, lambda pr: configs.TH2D_VANKA),
-             ("C2 TH2D 256^2 manufactured", configs.c2, lambda pr: configs.TH2D_VANKA),
-             ("C3 SV2D 128^2 Vanka", configs.c3, lambda pr: configs.SV2D_VANKA),
-             ("C3 SV2D 128^2 Vanka + DLSC", configs.c3, lambda pr: configs.sv_vanka_dlsc(pr.nlevels)),
-             ("C4 TH3D 32^3 lid", configs.c4, lambda pr: configs.TH3D_VANKA)]
-    built = {}
-    for name, make, params in cases:
-        key = make.__name__
-        if key not in built:
-            built[key] = make()
-        pr = built[key]
-        prm = params(pr)
-        n = pr.b.size
-        b = torch.tensor(pr.b, dtype=torch.float64, device=dev)
-        res = {}
-        xs = {}
-        with torch.cuda.stream(stream):
-            for prec in (sd.STOKES_FP32, sd.STOKES_FP64):
-                h = sd.stokes_setup(pr, dict(prm, precision=prec), stream=stream.cuda_stream)
-                x = torch.zeros_like(b)
-
-                def step():
-                    sd.stokes_factor_patches(h)
-                    x.zero_()
-                    rc, info = sd.stokes_fgmres_solve(h, b, x, rtol=1e-8, restart=30, maxit=600)
-                    return rc, info[0]
-
-                for _ in range(2):
-                    rc, info = step()
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                reps = 3
-                e0.record(stream)
-                for _ in range(reps):
-                    rc, info = step()
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / reps
-                z = torch.empty_like(b)
-                for _ in range(3):
-                    sd.stokes_vcycle(h, b, z)
-                e0.record(stream)
-                for _ in range(10):
-                    sd.stokes_vcycle(h, b, z)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                res[prec] = dict(status=int(rc), iters=int(info[0]), true_relres=float(info[2]), ms_per_solve=ms,
-                                 vcycle_ms=e0.elapsed_time(e1) / 10, cycle_bytes=sd.stokes_cycle_bytes(h))
-                xs[prec] = x.cpu().numpy()
-                sd.stokes_destroy(h)
-        err = float(np.linalg.norm(xs[sd.STOKES_FP32] - xs[sd.STOKES_FP64]) / np.linalg.norm(xs[sd.STOKES_FP64]))
-        r32, r64 = res[sd.STOKES_FP32], res[sd.STOKES_FP64]
-        print(json.dumps({"config": name, "dofs": int(n), "levels": int(pr.nlevels),
-                          "fp32": r32, "fp64": r64, "fp32_vs_fp64_solution_relerr": err,
-                          "fp32_vcycle_GBps": r32["cycle_bytes"] / r32["vcycle_ms"] / 1e6}), flush=True)
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -609,6 +771,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the per-config records and the paper-setting record of the default line")
     ap.add_argument("--profile-cycles", type=int, default=0,
                     help="profiling driver: set up, factorise and run this many DC cycles, print nothing")
     ap.add_argument("--profile-problem", default=None,
@@ -617,9 +781,8 @@ def main():
                     help="profiling driver: set up, factorise and run one FP32-preconditioned solve")
     ap.add_argument("--ref-iters", type=int, default=34,
                     help="iterations a full oracle solve takes (scales the reference sample)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5", "configs"],
-                    help="c2: the single 256^2 problem (default); c5: the 64-instance batch; "
-                         "configs: one line per config C1-C4")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
+                    help="c2: the single 256^2 problem (default); c5: the 64-instance batch, sharded over ranks")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -627,8 +790,6 @@ def main():
         run_profile(args)
     elif args.workload == "c5":
         run_gpu_c5(args)
-    elif args.workload == "configs":
-        run_gpu_configs(args)
     else:
         run_gpu(args)
 

@@ -107,3 +107,17 @@ HO_AMG_TH2D = dict(schedule=0, nu1=1, nu2=1, eta_u=1.0, eta_p=1.0, omega=0.70)
 
 def ho_amg_th2d(n=16):
     return stokes.build_ho_amg(M.unit_square(n), nu=1.0, bc="lid", name=f"HO-AMG TH2D {n}^2 lid")
+
+
+# Reduced sizes of the configs, on which the FP64 oracle's FGMRES solve
+# finishes in seconds (the FP32-preconditioned solution is compared with the
+# oracle's there): name -> (problem builder, parameter builder, note).
+def reduced_cases():
+    return {
+        "C1": (c1, lambda pr: TH2D_VANKA, "full size"),
+        "C2": (lambda: c2(64), lambda pr: TH2D_VANKA, "64^2 (full size 256^2)"),
+        "C2 DLSC-AMG": (lambda: c2(64), lambda pr: th2d_dlsc(pr.nlevels), "64^2 (full size 256^2)"),
+        "C3 Vanka": (lambda: c3(32), lambda pr: SV2D_VANKA, "32^2 (full size 128^2)"),
+        "C3 Vanka + DLSC": (lambda: c3(32), lambda pr: sv_vanka_dlsc(pr.nlevels), "32^2 (full size 128^2)"),
+        "C4": (lambda: c4(8), lambda pr: TH3D_VANKA, "8^3 (full size 32^3)"),
+    }

@@ -67,3 +67,28 @@ def test_roofline_traffic_is_null_unless_the_kernel_sources_match(monkeypatch):
     assert bench.apply_traffic() == rec["dram_bytes"]
     monkeypatch.setattr(bench, "APPLY_L0_TRAFFIC", dict(rec, sha256="0" * 64))
     assert bench.apply_traffic() is None
+
+
+def test_relerr_takes_the_worst_element():
+    import numpy as np
+    b = np.ones(10000)
+    a = b.copy()
+    a[3] += 1e-4
+    assert bench._relerr(a, b) == pytest_approx(1e-4)
+
+
+def test_zero_mean_pressure_removes_the_mass_weighted_mean():
+    import numpy as np
+    from problems import configs
+    pr = configs.c1()
+    x = np.random.default_rng(0).standard_normal(pr.b.size)
+    y = bench._zero_mean_pressure(pr, x)
+    off = pr.field_off[0]
+    p = y[off[2]:off[3]]
+    assert abs(np.ones(p.size) @ (pr.Mp @ p)) < 1e-12 * np.abs(p).sum()
+    assert np.array_equal(y[: off[2]], x[: off[2]])
+
+
+def pytest_approx(v):
+    import pytest
+    return pytest.approx(v, rel=1e-9)

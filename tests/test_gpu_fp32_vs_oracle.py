@@ -15,15 +15,7 @@ from tests.helpers import make_oracle, rel
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-# name: (problem, parameters, size note)
-CASES = {
-    "C1 TH2D 16^2 lid (full size)": (configs.c1, lambda pr: configs.TH2D_VANKA),
-    "C2 TH2D manufactured at 64^2 (full size 256^2)": (lambda: configs.c2(64), lambda pr: configs.TH2D_VANKA),
-    "C2 DLSC-AMG at 64^2": (lambda: configs.c2(64), lambda pr: configs.th2d_dlsc(pr.nlevels)),
-    "C3 SV2D Vanka at 32^2 (full size 128^2)": (lambda: configs.c3(32), lambda pr: configs.SV2D_VANKA),
-    "C3 SV2D Vanka + DLSC at 32^2": (lambda: configs.c3(32), lambda pr: configs.sv_vanka_dlsc(pr.nlevels)),
-    "C4 TH3D lid at 8^3 (full size 32^3)": (lambda: configs.c4(8), lambda pr: configs.TH3D_VANKA),
-}
+CASES = configs.reduced_cases()
 
 
 @pytest.fixture(scope="module")
@@ -35,7 +27,7 @@ def sd():
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp32_solution_matches_the_oracle_solution(sd, name):
-    make, params = CASES[name]
+    make, params, note = CASES[name]
     pr = make()
     prm = params(pr)
     o = make_oracle(pr, prm)
@@ -52,6 +44,6 @@ def test_fp32_solution_matches_the_oracle_solution(sd, name):
     x32 = direct.zero_mean_pressure(x.cpu().numpy(), off, d, pr.Mp)
     xoz = direct.zero_mean_pressure(xo, off, d, pr.Mp)
     err = rel(x32, xoz)
-    print(f"{name}: FP32 vs oracle solution {err:.2e}; iterations {info[0][0]} (oracle FP64 {its_o})")
+    print(f"{name} at {note}: FP32 vs oracle solution {err:.2e}; iterations {info[0][0]} (oracle FP64 {its_o})")
     assert err < 1e-5
     assert abs(info[0][0] - its_o) <= 2
