@@ -179,6 +179,7 @@ struct stokes_handle {
   int cycle_launches = -1;    // kernels in one DC cycle (from the ledger)
   std::vector<void*> allocs;
   std::vector<int*> err_flags;  // device error flags of every bulk-copy pipeline
+  int* dsing = nullptr;         // singular-patch counter of the factorisation
 };
 
 // ------------------------------------------------------------- utilities
@@ -1988,7 +1989,9 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
         if (wb >= 0) {
           fw[wb].push_back(si);
         } else if (T == 4) {
-          if (rows <= kTcMaxSmemRows && vanka_factor_tc_smem(dim, rows, max_np, false) <= (size_t)optin) {
+          if (rows <= kTcMaxSmemRows &&
+              vanka_factor_tc_smem(dim, rows, max_np, false, rows >= kUmmaMinRows && rows <= kUmmaMaxRowsFac) <=
+                  (size_t)optin) {
             ft[rows].push_back(si);
           } else {
             fg.push_back(si);
@@ -2020,7 +2023,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       if (!fg.empty()) {
         size_t scr_bytes;
         if (T == 4) {
-          if (vanka_factor_tc_smem(dim, glob_rows, max_np, true) > (size_t)optin)
+          if (vanka_factor_tc_smem(dim, glob_rows, max_np, true, false) > (size_t)optin)
             return fail(STOKES_ERR_INVALID_ARG, "patch too large for the factorisation kernel");
           scr_bytes = (size_t)dp.fac_chunk * ((size_t)glob_rows * (glob_rows + 1) / 2 + glob_rows) * kTileElems * 4;
         } else {
@@ -2189,9 +2192,9 @@ int stokes_setup(const stokes_problem* const* probs, int32_t ninstances, const s
 
 int stokes_factor_patches(stokes_handle* h, int64_t* nsingular) {
   if (!h) return fail(STOKES_ERR_INVALID_ARG, "null handle");
-  int* dsing = nullptr;
   TRY(join_in(h));
-  TRY(dalloc(h, &dsing, 1));
+  if (!h->dsing) TRY(dalloc(h, &h->dsing, 1));
+  int* dsing = h->dsing;
   CK(cudaMemsetAsync(dsing, 0, sizeof(int), h->st));
   for (int l = 0; l < h->L; ++l) {
     Level& lv = h->lv[l];
@@ -2203,6 +2206,9 @@ int stokes_factor_patches(stokes_handle* h, int64_t* nsingular) {
   CK(cudaMemcpyAsync(&ns, dsing, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   if (nsingular) *nsingular = ns;
+  // a bounded wait of the tensor-core factorisation that ran out leaves
+  // unusable factors (the same flags as the bulk-copy pipelines)
+  TRY(check_pipeline_errors(h));
   h->factored = true;
   if (ns > 0) return fail(STOKES_ERR_SINGULAR_PATCH, std::to_string(ns) + " singular patches");
   return STOKES_OK;

@@ -139,7 +139,8 @@ struct DevPatches {
 };
 
 size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool global_a);
-size_t vanka_factor_tc_smem(int dim, int rows, int max_np, bool global_tiles);
+size_t vanka_factor_tc_smem(int dim, int rows, int max_np, bool global_tiles, bool umma);
+constexpr int kUmmaMinRows = 2, kUmmaMaxRowsFac = 3;  // tile rows factorised with tcgen05 products
 int vanka_factor_warp_bin(int m);  // 0, 1, 2 for m <= 8, 20, 32; -1 above
 size_t vanka_tiles_smem(int stages, int nodes, int dim, size_t elem);
 int vanka_tiles_blocks_per_sm(int stages, int nodes, int dim, int np_max, size_t elem);

@@ -10,9 +10,16 @@
 //   M_ij <- M_ij - X_i M_jK^T         (i >= j; i, j != K)
 //   M_iK <- X_i,  M_KK <- -P
 // and after the last pivot block M = -A^-1.  Both products are dense
-// contractions and run on the tensor cores (mma.sync m16n8k8, TF32 with the
-// split x = x_hi + x_lo and three products per step, which keeps FP32
-// accuracy); the 32 x 32 pivot inverse runs in the registers of one warp.
+// contractions and run on the tensor cores with the TF32 split
+// x = x_hi + x_lo and three products per step, which keeps FP32 accuracy.
+// Blocks of two or three tile rows (the 3D vertex patches) use the
+// 5th-generation tensor cores: per pivot block, the stacked rows
+// [M_iK]_{i != K} and P, then [X_i] and [M_jK], are staged in shared memory
+// as K-major TF32 operands (hi and lo parts), one thread issues
+// tcgen05.mma (M = 128, K = 8 per instruction) into a TMEM accumulator,
+// completion arrives on an mbarrier and the four warps read the rows back
+// with tcgen05.ld.  Larger blocks use mma.sync m16n8k8.  The 32 x 32 pivot
+// inverse runs in the registers of one warp.
 //
 // Apply: a persistent kernel in which each consumer warp solves one patch
 // at a time, fed by its own producer warp through a ring of bulk copies
@@ -25,6 +32,7 @@
 #include "common.cuh"
 #include "tiles.cuh"
 #include "tma.cuh"
+#include "umma.cuh"
 
 namespace sd {
 
@@ -191,10 +199,51 @@ __device__ bool tc_pivot_block(const FacTiles& F, float* P, float* prow, int K, 
   return __any_sync(0xffffffffu, bad);
 }
 
-size_t vanka_factor_tc_smem(int dim, int rows, int max_np, bool global_tiles) {
+// ------------------------------------------------ tcgen05 trailing products
+// K-major TF32 operand of up to 128 rows and 32 K-columns: 8-row x 4-element
+// (16-byte) core matrices, adjacent along K 128 bytes apart, 8-row groups
+// 1024 bytes apart.  Offset of element (row, k) in floats, and its inverse
+// (element e of the staging order, so consecutive threads write
+// consecutive words).
+__device__ __forceinline__ int kmaj_off(int row, int k) {
+  return ((row >> 3) << 8) + ((k >> 2) << 5) + ((row & 7) << 2) + (k & 3);
+}
+__device__ __forceinline__ void kmaj_rc(int e, int& row, int& k) {
+  row = ((e >> 8) << 3) + ((e >> 2) & 7);
+  k = (((e >> 5) & 7) << 2) + (e & 3);
+}
+constexpr int kUmmaRowsA = 128;          // M of every MMA; rows past the operand are not read back
+constexpr int kUmmaCols = 128;           // TMEM columns: X (32) and the trailing block (up to 64)
+constexpr int kUmmaMaxRows = kUmmaMaxRowsFac;  // tile rows handled on tcgen05 (trailing block up to 64 columns)
+constexpr uint32_t kUmmaLbo = 128, kUmmaSbo = 1024;
+
+// Staging: A_hi, A_lo (128 rows each), B_hi, B_lo (64 rows each), floats.
+constexpr int kUmmaStageFloats = 2 * kUmmaRowsA * 32 + 2 * 64 * 32;
+
+// D = A B^T for A (128 x 32) and B (N x 32) given as hi/lo TF32 parts: the
+// three products lo*hi, hi*lo, hi*hi in four K-steps each, issued by the
+// calling thread; completion arrives on bar.
+__device__ __forceinline__ void umma_split_product(uint32_t d_tmem, const float* Ahi, const float* Alo,
+                                                   const float* Bhi, const float* Blo, int N, uint64_t* bar) {
+  tc_fence_after();
+  const uint32_t idesc = idesc_tf32(kUmmaRowsA, N);
+  const float* As[3] = {Alo, Ahi, Ahi};
+  const float* Bs[3] = {Bhi, Blo, Bhi};
+  uint32_t acc = 0;
+  for (int q = 0; q < 3; ++q)
+    for (int s = 0; s < 4; ++s) {  // K-step s covers k = 8s .. 8s + 7: two core matrices, 256 bytes
+      const uint64_t ad = smem_desc_kmajor(As[q] + s * 64, kUmmaLbo, kUmmaSbo);
+      const uint64_t bd = smem_desc_kmajor(Bs[q] + s * 64, kUmmaLbo, kUmmaSbo);
+      umma_tf32(d_tmem, ad, bd, idesc, acc);
+      acc = 1;
+    }
+  umma_commit(bar);
+}
+
+size_t vanka_factor_tc_smem(int dim, int rows, int max_np, bool global_tiles, bool umma) {
   const size_t ntl = (size_t)rows * (rows + 1) / 2;
   size_t f = (global_tiles ? 0 : (ntl + rows) * kTileElems) + kTileElems + 32 + 4 + kMaxNp * kMaxNp +
-             2 * (size_t)dim * 32 * rows * max_np;
+             2 * (size_t)dim * 32 * rows * max_np + (umma ? kUmmaStageFloats + 32 : 0);
   return f * sizeof(float) + sizeof(int) * ((size_t)dim * 32 * rows + max_np + 2 * (32 * (size_t)rows + 1)) + 16;
 }
 
@@ -206,15 +255,16 @@ constexpr int tc_threads(int rows) { return rows <= 3 ? 128 : 256; }
 // of the launch (the shared-memory layout); with gscr the tiles live in
 // global scratch (rows_max tile rows per CTA).  Patches with storage id >=
 // nsmall get the tiled block, the others the packed one.
-template <int NTHR>
+template <int NTHR, bool UMMA>
 __global__ void __launch_bounds__(NTHR, 512 / NTHR) k_vanka_factor_tc(int nlist, const int* __restrict__ list,
     int dim, int shared, const int* __restrict__ ptr, const int* __restrict__ dof, const int* __restrict__ nvel,
     const int* __restrict__ npres, const int64_t* __restrict__ foff, const int* __restrict__ rowptr,
     const int* __restrict__ col, const double* __restrict__ Kval, float* __restrict__ fac, int* nsing, int rows_max,
-    int max_np, int nsmall, float* __restrict__ gscr) {
+    int max_np, int nsmall, float* __restrict__ gscr, int* __restrict__ err) {
   pdl_enter();
+  static_assert(!UMMA || NTHR == 128, "the tcgen05 path reads TMEM with one warpgroup");
   constexpr int NW = NTHR / 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   if ((int)blockIdx.x >= nlist) return;
   const int i = list[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
@@ -223,6 +273,27 @@ __global__ void __launch_bounds__(NTHR, 512 / NTHR) k_vanka_factor_tc(int nlist,
   const int nT = tile_rows(m), nn = nT * 32, ntl = nT * (nT + 1) / 2;
   const int ntl_max = rows_max * (rows_max + 1) / 2;
   float* sp = reinterpret_cast<float*>(smem_raw);
+  // tcgen05 staging (operands, then the mbarrier and the TMEM address)
+  float* Ahi = sp;
+  float* Alo = Ahi + kUmmaRowsA * 32;
+  float* Bhi = Alo + kUmmaRowsA * 32;
+  float* Blo = Bhi + 64 * 32;
+  uint64_t* ubar = reinterpret_cast<uint64_t*>(Blo + 64 * 32);
+  uint32_t* utaddr = reinterpret_cast<uint32_t*>(ubar + 1);
+  if constexpr (UMMA) sp += kUmmaStageFloats + 32;
+  uint32_t tmem = 0, uphase = 0;
+  bool uok = true;
+  if constexpr (UMMA) {
+    if (warp == 0) tmem_alloc(utaddr, kUmmaCols);
+    if (tid == 0) {
+      mbar_init(ubar, 1);
+      mbar_fence_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tmem = *utaddr;
+  }
   FacTiles F;
   if (gscr) {
     F.M = gscr + (size_t)blockIdx.x * (ntl_max + rows_max) * kTileElems;
@@ -348,20 +419,101 @@ __global__ void __launch_bounds__(NTHR, 512 / NTHR) k_vanka_factor_tc(int nlist,
         if (bad && lane == 0) misc[1] = 1.f;
       }
       __syncthreads();
-      for (int it = warp; it < 2 * (nT - 1); it += NW) {
-        const int ii = it >> 1, i2 = ii < K ? ii : ii + 1;
-        tc_x_rows(F, P, i2, K, (it & 1) * 16, g, t);
-      }
-      __syncthreads();
       const int nr = nT - 1;
-      for (int it = warp; it < nr * (nr + 1); it += NW) {
-        const int q = it >> 1;
-        int ia = 0;
-        while ((ia + 1) * (ia + 2) / 2 <= q) ++ia;
-        const int ja = q - ia * (ia + 1) / 2;
-        tc_update_rows(F, ia < K ? ia : ia + 1, ja < K ? ja : ja + 1, K, (it & 1) * 16, g, t);
+      if constexpr (UMMA) {
+        if (nr > 0 && uok) {
+          // round 1: X = [M_iK]_{i != K} P  (rows 32 ii + r of A are row r of M_{i2,K})
+          for (int e = tid; e < nr * 32 * 32; e += NTHR) {
+            int q, k;
+            kmaj_rc(e, q, k);
+            const int ii = q >> 5, i2 = ii < K ? ii : ii + 1;
+            uint32_t h, l;
+            tf32_split(F.get(i2, K, q & 31, k), h, l);
+            Ahi[e] = __uint_as_float(h);
+            Alo[e] = __uint_as_float(l);
+          }
+          for (int e = tid; e < 32 * 32; e += NTHR) {  // B(n, k) = P(k, n)
+            int n, k;
+            kmaj_rc(e, n, k);
+            uint32_t h, l;
+            tf32_split(P[fsw(k, n)], h, l);
+            Bhi[e] = __uint_as_float(h);
+            Blo[e] = __uint_as_float(l);
+          }
+          fence_async_smem();
+          __syncthreads();
+          if (tid == 0) umma_split_product(tmem, Ahi, Alo, Bhi, Blo, 32, ubar);
+          if (!mbar_wait(ubar, uphase)) uok = false;
+          uphase ^= 1;
+          uok = __syncthreads_and(uok);
+          if (uok) {
+            tc_fence_after();
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
+            const int q = 32 * warp + lane;
+            if (q < nr * 32) {
+              const int ii = q >> 5, i2 = ii < K ? ii : ii + 1;
+              float* Xi = F.X + i2 * kTileElems;
+#pragma unroll
+              for (int c = 0; c < 32; ++c) Xi[fsw(q & 31, c)] = v[c];
+            }
+            tc_fence_before();
+          }
+          __syncthreads();
+          // round 2: D = [X_i] [M_jK]^T, then M_ij -= D on the lower tiles
+          if (uok) {
+            for (int e = tid; e < nr * 32 * 32; e += NTHR) {
+              int q, k;
+              kmaj_rc(e, q, k);
+              const int ii = q >> 5, i2 = ii < K ? ii : ii + 1;
+              uint32_t h, l;
+              tf32_split(F.X[i2 * kTileElems + fsw(q & 31, k)], h, l);
+              Ahi[e] = __uint_as_float(h);
+              Alo[e] = __uint_as_float(l);
+              tf32_split(F.get(i2, K, q & 31, k), h, l);  // row n = q of B: row of M_{j2,K}
+              Bhi[e] = __uint_as_float(h);
+              Blo[e] = __uint_as_float(l);
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) umma_split_product(tmem + 32, Ahi, Alo, Bhi, Blo, nr * 32, ubar);
+            if (!mbar_wait(ubar, uphase)) uok = false;
+            uphase ^= 1;
+            uok = __syncthreads_and(uok);
+            if (uok) {
+              tc_fence_after();
+              const int q = 32 * warp + lane;
+              const int ii = q >> 5, i2 = ii < K ? ii : ii + 1;
+              for (int jj = 0; jj < nr; ++jj) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 + 32 * jj, v);
+                const int j2 = jj < K ? jj : jj + 1;
+                if (q < nr * 32 && j2 <= i2) {
+                  float* C = F.tile(i2, j2);
+#pragma unroll
+                  for (int c = 0; c < 32; ++c) C[fsw(q & 31, c)] -= v[c];
+                }
+              }
+              tc_fence_before();
+            }
+            __syncthreads();
+          }
+        }
+      } else {
+        for (int it = warp; it < 2 * (nT - 1); it += NW) {
+          const int ii = it >> 1, i2 = ii < K ? ii : ii + 1;
+          tc_x_rows(F, P, i2, K, (it & 1) * 16, g, t);
+        }
+        __syncthreads();
+        for (int it = warp; it < nr * (nr + 1); it += NW) {
+          const int q = it >> 1;
+          int ia = 0;
+          while ((ia + 1) * (ia + 2) / 2 <= q) ++ia;
+          const int ja = q - ia * (ia + 1) / 2;
+          tc_update_rows(F, ia < K ? ia : ia + 1, ja < K ? ja : ja + 1, K, (it & 1) * 16, g, t);
+        }
+        __syncthreads();
       }
-      __syncthreads();
       for (int e = tid; e < nr * kTileElems; e += NTHR) {
         const int ii = e >> 10, i2 = ii < K ? ii : ii + 1;
         const int r = (e >> 5) & 31, c = e & 31;
@@ -473,18 +625,31 @@ __global__ void __launch_bounds__(NTHR, 512 / NTHR) k_vanka_factor_tc(int nlist,
       for (int b = 0; b < np; ++b) Sout[a * np + b] = sing ? 0.f : Mx[a][np + b];
     if (sing) atomicAdd(nsing, 1);
   }
+  if constexpr (UMMA) {
+    // an MMA wait that ran out: the factors are unusable (flag for the
+    // host); wait once more, boundedly, for the MMAs in flight before the
+    // tensor memory is released
+    if (!uok) {
+      if (tid == 0) atomicOr(err, 32);
+      mbar_wait(ubar, uphase ^ 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kUmmaCols);
+  }
 }
 
 // Launches: the patches after `start` in the factorisation list, grouped by
 // tile rows nT = 1..8 (tiles in shared memory, one launch per group sized
 // for it), then the rest with the tiles in global scratch.
-template <int NTHR>
+template <int NTHR, bool UMMA>
 static cudaError_t launch_factor_tc(const DevPatches& p, const DevCSR& K, const int* list, int cnt, int rows,
                                     float* gscr, int* nsingular, cudaStream_t st) {
-  const size_t shm = vanka_factor_tc_smem(p.dim, rows, p.max_np, gscr != nullptr);
-  SD_LAUNCH((k_vanka_factor_tc<NTHR>), cnt, NTHR, shm, st, cnt, list, p.dim, p.shared, p.ptr, p.dof, p.nvel, p.npres, p.foff,
-                                                  K.rowptr, K.col, K.v64, reinterpret_cast<float*>(p.fac), nsingular,
-                                                  rows, p.max_np, p.nsmall, gscr);
+  const size_t shm = vanka_factor_tc_smem(p.dim, rows, p.max_np, gscr != nullptr, UMMA);
+  SD_LAUNCH((k_vanka_factor_tc<NTHR, UMMA>), cnt, NTHR, shm, st, cnt, list, p.dim, p.shared, p.ptr, p.dof, p.nvel,
+            p.npres, p.foff, K.rowptr, K.col, K.v64, reinterpret_cast<float*>(p.fac), nsingular, rows, p.max_np,
+            p.nsmall, gscr, p.err);
   return cudaGetLastError();
 }
 
@@ -493,16 +658,18 @@ cudaError_t vanka_factor_tc(const DevPatches& p, const DevCSR& K, int start, int
     const int cnt = p.nfac_tc[rows];
     if (cnt == 0) continue;
     const cudaError_t e =
-        tc_threads(rows) == 128
-            ? launch_factor_tc<128>(p, K, p.fac_list + start, cnt, rows, nullptr, nsingular, st)
-            : launch_factor_tc<256>(p, K, p.fac_list + start, cnt, rows, nullptr, nsingular, st);
+        rows >= 2 && rows <= kUmmaMaxRows
+            ? launch_factor_tc<128, true>(p, K, p.fac_list + start, cnt, rows, nullptr, nsingular, st)
+        : tc_threads(rows) == 128
+            ? launch_factor_tc<128, false>(p, K, p.fac_list + start, cnt, rows, nullptr, nsingular, st)
+            : launch_factor_tc<256, false>(p, K, p.fac_list + start, cnt, rows, nullptr, nsingular, st);
     if (e != cudaSuccess) return e;
     start += cnt;
   }
   const int nglob = p.npatch - start;
   for (int c0 = 0; c0 < nglob; c0 += p.fac_chunk) {
     const int cnt = std::min(p.fac_chunk, nglob - c0);
-    const cudaError_t e = launch_factor_tc<256>(p, K, p.fac_list + start + c0, cnt, p.tc_glob_rows,
+    const cudaError_t e = launch_factor_tc<256, false>(p, K, p.fac_list + start + c0, cnt, p.tc_glob_rows,
                                                 reinterpret_cast<float*>(p.fac_scratch), nsingular, st);
     if (e != cudaSuccess) return e;
   }
@@ -823,7 +990,8 @@ template cudaError_t vanka_apply_tiles<float, float>(const DevPatches&, const fl
 template cudaError_t vanka_apply_tiles<double, double>(const DevPatches&, const double*, double*, cudaStream_t);
 
 cudaError_t vanka_tiles_prepare_kernels(int optin) {
-  const void* ks[] = {(const void*)k_vanka_factor_tc<128>, (const void*)k_vanka_factor_tc<256>,
+  const void* ks[] = {(const void*)k_vanka_factor_tc<128, false>, (const void*)k_vanka_factor_tc<256, false>,
+                      (const void*)k_vanka_factor_tc<128, true>,
                       tiles_kernel_of(4, 2, true),      tiles_kernel_of(4, 2, false),
                       tiles_kernel_of(4, 3, true),      tiles_kernel_of(4, 3, false), tiles_kernel_of(8, 2, true),
                       tiles_kernel_of(8, 2, false),     tiles_kernel_of(8, 3, true), tiles_kernel_of(8, 3, false)};
