@@ -46,8 +46,8 @@ METRIC = "Stokes solves/s to 1e-8 rel-res (FP32 DC-AMG preconditioned FGMRES)"
 # dram__bytes_read.sum + dram__bytes_write.sum of one level-0 FP32 apply launch from an ncu capture,
 # keyed by the SHA-256 of the kernel's sources at capture time: when the sources differ the figure
 # no longer describes the kernel and the bench line reports traffic as null
-APPLY_L0_TRAFFIC = {"dram_bytes": 87.55e6, "sources": ["vanka.cu", "tma.cuh", "common.cuh"],
-                    "sha256": None}
+APPLY_L0_TRAFFIC = {"dram_bytes": 84885248 + 2157312, "sources": ["vanka.cu", "tma.cuh", "common.cuh"],
+                    "sha256": "f4cbd86fe0ea9a8abec2260fbe4b4108e01d9bec66923916e907066a45f07a78"}
 
 
 def apply_traffic():
@@ -368,6 +368,23 @@ def config_records(sd, torch, stream, c2):
     del c3
     c4 = configs.c4()
     both("C4 TH3D 32^3 lid, stationary Vanka", c4, configs.TH3D_VANKA, fp64_reps=1)
+    # FP32 factorisation alone: trailing products of the three-tile-row
+    # blocks on mma.sync (default) and on tcgen05
+    fac = {}
+    for v, nm in ((0, "mma_sync"), (1, "tcgen05")):
+        h = sd.stokes_setup(c4, dict(configs.TH3D_VANKA, precision=fp32, factor_tcgen05=v), stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            sd.stokes_factor_patches(h)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                sd.stokes_factor_patches(h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        fac[nm] = e0.elapsed_time(e1) / 3
+        sd.stokes_destroy(h)
+    out["C4 TH3D 32^3 lid, stationary Vanka"]["fp32_factor_ms"] = fac
     kr = dict(schedule=0, nu1=2, nu2=2, eta_u=1.0, eta_p=1.0, omega=1.0,
               relax=[sd.STOKES_RELAX_VANKA_KRYLOV] * (c4.nlevels - 1))
     r, _ = _solve_record(sd, torch, c4, kr, fp32, stream)

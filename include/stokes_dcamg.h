@@ -162,6 +162,9 @@ typedef struct {
   int32_t precision;         /* STOKES_FP32 or STOKES_FP64 cycle */
   int32_t preconditioner;    /* STOKES_PRECOND_DC or STOKES_PRECOND_BTP */
   int32_t btp_steps;         /* BTP: Krylov-wrapped Jacobi steps per relaxation (1..4) */
+  int32_t factor_tcgen05;    /* FP32 factorisation of patch blocks with three 32 x 32 tile rows
+                                (3D vertex patches): 0 = trailing products on mma.sync (default,
+                                faster at these sizes), 1 = on tcgen05 with TMEM accumulators */
 } stokes_params;
 
 typedef struct {

@@ -79,7 +79,7 @@ class stokes_params(C.Structure):
                 ("eta_u", C.c_double), ("eta_p", C.c_double), ("omega", C.POINTER(C.c_double)),
                 ("relax", C.POINTER(C.c_int32)), ("cheb_deg", C.c_int32 * 3), ("dlsc_sweeps", C.c_int32),
                 ("mcg_deg", C.c_int32), ("precision", C.c_int32), ("preconditioner", C.c_int32),
-                ("btp_steps", C.c_int32)]
+                ("btp_steps", C.c_int32), ("factor_tcgen05", C.c_int32)]
 
 
 class stokes_solve_info(C.Structure):
@@ -254,7 +254,8 @@ def _params(keep, prm, nlevels, dim=2):
     """prm: dict with schedule, nu1, nu2, eta_u, eta_p, omega (scalar or per
     level; omega0 overrides level 0), relax (list or None), cheb_deg (default:
     the DLSC degrees of the paper's table for the dimension, (3, 3, 6) in 2D
-    and (4, 4, 16) in 3D), dlsc_sweeps, mcg_deg, precision."""
+    and (4, 4, 16) in 3D), dlsc_sweeps, mcg_deg, precision, preconditioner,
+    btp_steps, factor_tcgen05."""
     s = stokes_params()
     s.schedule = int(prm.get("schedule", 0))
     s.nu1 = int(prm.get("nu1", 1))
@@ -278,6 +279,7 @@ def _params(keep, prm, nlevels, dim=2):
     s.precision = int(prm.get("precision", STOKES_FP32))
     s.preconditioner = int(prm.get("preconditioner", STOKES_PRECOND_DC))
     s.btp_steps = int(prm.get("btp_steps", 2))
+    s.factor_tcgen05 = int(prm.get("factor_tcgen05", 0))
     return s
 
 

@@ -120,6 +120,7 @@ struct stokes_handle {
   int precond = STOKES_PRECOND_DC;
   std::string tune_report = "{}";  // autotuner choices (JSON)
   int btp_steps = 2;
+  bool factor_tcgen05 = false;     // 3-tile-row FP32 patch blocks: tcgen05 trailing products
   std::vector<Level> btpA, btpM;  // SA hierarchies of A and of M_p / nu (TH)
   DevCSR btpB, btpMinv;           // B (pressure rows x velocity columns); SV exact mass inverse
   void* btp_tp = nullptr;         // level-0 pressure work vector
@@ -1629,6 +1630,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
   if (h->prec != STOKES_FP32 && h->prec != STOKES_FP64) return fail(STOKES_ERR_INVALID_ARG, "precision");
   h->precond = prm->preconditioner;
   h->btp_steps = prm->btp_steps;
+  h->factor_tcgen05 = prm->factor_tcgen05 != 0;
   if (h->precond != STOKES_PRECOND_DC && h->precond != STOKES_PRECOND_BTP)
     return fail(STOKES_ERR_INVALID_ARG, "unknown preconditioner");
   if (h->precond == STOKES_PRECOND_BTP) {
@@ -1912,6 +1914,7 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
     dp.npatch = npatch;
     dp.dim = dim;
     dp.shared = shared ? 1 : 0;
+    dp.tcgen05 = h->factor_tcgen05 ? 1 : 0;
     dp.nsmall = (int)small.size();
     dp.nlarge = (int)large.size();
     dp.max_m = max_m;
@@ -1990,7 +1993,8 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
           fw[wb].push_back(si);
         } else if (T == 4) {
           if (rows <= kTcMaxSmemRows &&
-              vanka_factor_tc_smem(dim, rows, max_np, false, rows >= kUmmaMinRows && rows <= kUmmaMaxRowsFac) <=
+              vanka_factor_tc_smem(dim, rows, max_np, false,
+                                   h->factor_tcgen05 && rows >= kUmmaMinRows && rows <= kUmmaMaxRowsFac) <=
                   (size_t)optin) {
             ft[rows].push_back(si);
           } else {

@@ -109,6 +109,7 @@ struct DevPatches {
   int64_t fac_elems = 0;
   void* fac = nullptr;    // factors, float or double
   int shared = 1;         // one velocity block shared by all components
+  int tcgen05 = 0;        // FP32 three-tile-row blocks: trailing products on tcgen05
   int* small = nullptr;   // storage ids of the patches in bulk-copy bins (packed blocks)
   int nsmall = 0;
   int* large = nullptr;   // storage ids of the rest (tiled blocks), by descending m
@@ -140,7 +141,9 @@ struct DevPatches {
 
 size_t vanka_factor_smem(int dim, int max_m, int max_np, size_t elem, bool global_a);
 size_t vanka_factor_tc_smem(int dim, int rows, int max_np, bool global_tiles, bool umma);
-constexpr int kUmmaMinRows = 2, kUmmaMaxRowsFac = 3;  // tile rows factorised with tcgen05 products
+// Tile rows whose blocks may be factorised with tcgen05 products (the 3D
+// vertex patches, m = 65), when the handle asks for it.
+constexpr int kUmmaMinRows = 3, kUmmaMaxRowsFac = 3;
 int vanka_factor_warp_bin(int m);  // 0, 1, 2 for m <= 8, 20, 32; -1 above
 size_t vanka_tiles_smem(int stages, int nodes, int dim, size_t elem);
 int vanka_tiles_blocks_per_sm(int stages, int nodes, int dim, int np_max, size_t elem);

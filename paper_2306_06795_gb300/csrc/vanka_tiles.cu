@@ -12,13 +12,16 @@
 // and after the last pivot block M = -A^-1.  Both products are dense
 // contractions and run on the tensor cores with the TF32 split
 // x = x_hi + x_lo and three products per step, which keeps FP32 accuracy.
-// Blocks of two or three tile rows (the 3D vertex patches) use the
-// 5th-generation tensor cores: per pivot block, the stacked rows
+// Blocks of three tile rows (the 3D vertex patches) can use the
+// 5th-generation tensor cores (stokes_params.factor_tcgen05): per pivot block, the stacked rows
 // [M_iK]_{i != K} and P, then [X_i] and [M_jK], are staged in shared memory
 // as K-major TF32 operands (hi and lo parts), one thread issues
 // tcgen05.mma (M = 128, K = 8 per instruction) into a TMEM accumulator,
 // completion arrives on an mbarrier and the four warps read the rows back
-// with tcgen05.ld.  Larger blocks use mma.sync m16n8k8.  The 32 x 32 pivot
+// with tcgen05.ld.  At these sizes (32 x 32 x 32 products) the staging, the
+// two dependent MMA round trips per pivot block and the lower occupancy cost
+// more than the faster products (C4: 22.5 ms against 17.7 ms), so the
+// default, and every other block, uses mma.sync m16n8k8.  The 32 x 32 pivot
 // inverse runs in the registers of one warp.
 //
 // Apply: a persistent kernel in which each consumer warp solves one patch
@@ -217,8 +220,12 @@ constexpr int kUmmaCols = 128;           // TMEM columns: X (32) and the trailin
 constexpr int kUmmaMaxRows = kUmmaMaxRowsFac;  // tile rows handled on tcgen05 (trailing block up to 64 columns)
 constexpr uint32_t kUmmaLbo = 128, kUmmaSbo = 1024;
 
-// Staging: A_hi, A_lo (128 rows each), B_hi, B_lo (64 rows each), floats.
-constexpr int kUmmaStageFloats = 2 * kUmmaRowsA * 32 + 2 * 64 * 32;
+// Staging, 64 rows of 32 floats each, in the order A_hi, A_lo, B_hi, B_lo.
+// An MMA reads 128 rows of A: from A_hi it reads A_hi and A_lo, from A_lo
+// it reads A_lo and B_hi; the accumulator rows past the operand's (at most
+// 64) rows are never read back, so the buffers need no padding.
+constexpr int kUmmaStageRows = 64;
+constexpr int kUmmaStageFloats = 4 * kUmmaStageRows * 32;
 
 // D = A B^T for A (128 x 32) and B (N x 32) given as hi/lo TF32 parts: the
 // three products lo*hi, hi*lo, hi*hi in four K-steps each, issued by the
@@ -275,10 +282,10 @@ __global__ void __launch_bounds__(NTHR, 512 / NTHR) k_vanka_factor_tc(int nlist,
   float* sp = reinterpret_cast<float*>(smem_raw);
   // tcgen05 staging (operands, then the mbarrier and the TMEM address)
   float* Ahi = sp;
-  float* Alo = Ahi + kUmmaRowsA * 32;
-  float* Bhi = Alo + kUmmaRowsA * 32;
-  float* Blo = Bhi + 64 * 32;
-  uint64_t* ubar = reinterpret_cast<uint64_t*>(Blo + 64 * 32);
+  float* Alo = Ahi + kUmmaStageRows * 32;
+  float* Bhi = Alo + kUmmaStageRows * 32;
+  float* Blo = Bhi + kUmmaStageRows * 32;
+  uint64_t* ubar = reinterpret_cast<uint64_t*>(Blo + kUmmaStageRows * 32);
   uint32_t* utaddr = reinterpret_cast<uint32_t*>(ubar + 1);
   if constexpr (UMMA) sp += kUmmaStageFloats + 32;
   uint32_t tmem = 0, uphase = 0;
@@ -658,7 +665,7 @@ cudaError_t vanka_factor_tc(const DevPatches& p, const DevCSR& K, int start, int
     const int cnt = p.nfac_tc[rows];
     if (cnt == 0) continue;
     const cudaError_t e =
-        rows >= 2 && rows <= kUmmaMaxRows
+        p.tcgen05 && rows >= kUmmaMinRows && rows <= kUmmaMaxRows
             ? launch_factor_tc<128, true>(p, K, p.fac_list + start, cnt, rows, nullptr, nsingular, st)
         : tc_threads(rows) == 128
             ? launch_factor_tc<128, false>(p, K, p.fac_list + start, cnt, rows, nullptr, nsingular, st)

@@ -63,14 +63,18 @@ def test_3d_large_coarse_patches_fp64(sd):
     assert rel(host(z), o.apply(r)) < 1e-12
 
 
-def test_3d_large_coarse_patches_fp32(sd):
+@pytest.mark.parametrize("tcgen05", [0, 1])
+def test_3d_large_coarse_patches_fp32(sd, tcgen05):
     """FP32 on the 8^3 cavity: patches with m > 32 velocity DoFs per
-    component are factorised by the blocked sweep on tensor cores (3xTF32)
-    and those outside the bulk-copy bins are solved from tiled blocks; every
-    level's Vanka op agrees with the FP64 oracle to FP32 accuracy, and the
-    FP32 cycle with the FP64 oracle cycle to 1e-5."""
+    component are factorised by the blocked sweep on tensor cores (3xTF32;
+    with tcgen05 = 1 the three-tile-row blocks run their trailing products as
+    tcgen05.mma with TMEM accumulators) and those outside the bulk-copy bins
+    are solved from tiled blocks; every level's Vanka op agrees with the FP64
+    oracle to FP32 accuracy, and the FP32 cycle with the FP64 oracle cycle to
+    1e-5."""
     pr = stokes.build_th(M.unit_cube(8), bc="lid")
-    prm = dict(configs.TH3D_VANKA)
+    prm = dict(configs.TH3D_VANKA, factor_tcgen05=tcgen05)
+    assert max(int(np.asarray(p.nvel)[:, 0].max()) for p in pr.patches[:2]) == 65  # three tile rows
     h = sd.stokes_setup(pr, dict(prm, precision=sd.STOKES_FP32))
     assert sd.stokes_factor_patches(h) == 0
     o = make_oracle(pr, prm)
