@@ -360,6 +360,16 @@ def config_records(sd, torch, stream, c2):
         energy = float(np.sqrt(x[: off[2]] @ (A @ x[: off[2]])))
         return {"divergence_norm_fp32": stokes.divergence_norm(pr, x), "velocity_energy_norm": energy}
 
+    # the setup step of C2 by the host route and by the device route (Alg. 1
+    # with the device strength, prolongators, Galerkin products and patch lists)
+    from problems import device_setup, mesh as Mh
+    setup_s = {}
+    for nm, steps in (("host_route_s", stokes.HostSteps), ("device_route_s", device_setup.DeviceSteps(sd))):
+        t0 = time.perf_counter()
+        stokes.build_th(Mh.unit_square(256), nu=1.0, bc="noslip", rhs="manufactured", max_levels=6, steps=steps)
+        torch.cuda.synchronize()
+        setup_s[nm] = time.perf_counter() - t0
+    out["C2 setup step (mesh, assembly, Alg. 1 hierarchy, patch lists)"] = setup_s
     both("C1 TH2D 16^2 lid, Vanka", configs.c1(), configs.TH2D_VANKA)
     both("C2 TH2D 256^2, DLSC-AMG (DLSC on every level)", c2, configs.th2d_dlsc(c2.nlevels))
     c3 = configs.c3()

@@ -211,19 +211,38 @@ def field_offsets(nvel, npres, d):
     return np.array([c * nvel for c in range(d + 1)] + [d * nvel + npres], dtype=np.int64)
 
 
-def build_hierarchy(K1, A1, Ap, d, nvel1, npres1, max_levels, max_coarse):
+class HostSteps:
+    """The steps of Alg. 1 the setup route takes, on the host (the default):
+    the scalar SA hierarchy of one field, the Galerkin product and the
+    Vanka patch lists of a Galerkin level.  A device route supplies the same
+    three methods (see problems/device_setup.py)."""
+
+    @staticmethod
+    def sa_field(A, B, max_levels, max_coarse):
+        return sa.sa_field(A, B, max_levels, max_coarse)
+
+    @staticmethod
+    def galerkin(K, P):
+        return _csr(P.T @ K @ P)
+
+    @staticmethod
+    def patches(K, off, d):
+        return make_patches(K, off, d)
+
+
+def build_hierarchy(K1, A1, Ap, d, nvel1, npres1, max_levels, max_coarse, steps=HostSteps):
     """Alg. 1: scalar SA per field (each velocity component on its block of
     K1, pressure on the auxiliary Laplacian Ap), l_max = min over fields,
     block-diagonal P_l and Galerkin K_{l+1} = P_l^T K_l P_l.  Returns the K1
     hierarchy (K1, K2, ...), the P_l and the pressure near-null vectors."""
-    Pv, Av, Bv = sa.sa_field(A1, np.ones(nvel1), max_levels, max_coarse)
-    Pp, Ap_, Bp = sa.sa_field(Ap, np.ones(npres1), max_levels, max_coarse)
+    Pv, Av, Bv = steps.sa_field(A1, np.ones(nvel1), max_levels, max_coarse)
+    Pp, Ap_, Bp = steps.sa_field(Ap, np.ones(npres1), max_levels, max_coarse)
     # identical scalar blocks per component give identical hierarchies
     lmax = min(len(Av), len(Ap_))
     Ks, Ps, offs = [K1], [], [field_offsets(nvel1, npres1, d)]
     for l in range(lmax - 1):
         P = _blockdiag([Pv[l]] * d + [Pp[l]])
-        Kc = _csr(P.T @ Ks[-1] @ P)
+        Kc = steps.galerkin(Ks[-1], P)
         Ps.append(P)
         Ks.append(Kc)
         offs.append(field_offsets(Pv[l].shape[1], Pp[l].shape[1], d))
@@ -360,8 +379,9 @@ def build_ho_amg(mesh, nu=1.0, bc="lid", rhs="zero", seed=None, max_levels=10, m
 
 
 def build_th(mesh, nu=1.0, bc="lid", rhs="zero", seed=None, max_levels=10,
-             max_coarse=50, name="th"):
-    """Taylor-Hood P2/P1 K0 with its P1isoP2/P1 K1 and the Alg. 1 hierarchy."""
+             max_coarse=50, name="th", steps=HostSteps):
+    """Taylor-Hood P2/P1 K0 with its P1isoP2/P1 K1 and the Alg. 1 hierarchy
+    (built by `steps`: HostSteps, or a device route)."""
     d = mesh.dim
     exact = {}
     rhs_fn = None
@@ -383,14 +403,15 @@ def build_th(mesh, nu=1.0, bc="lid", rhs="zero", seed=None, max_levels=10,
             b[c * n2:(c + 1) * n2] = zc
     K1, A1, B1pat = p1iso_K1(V, mesh.cells, None, npres, bnd, nu)
     Ap = pressure_laplacian(mesh)
-    Ks, Ps, offs, Bp = build_hierarchy(K1, A1, Ap, d, n2, npres, max_levels - 1, max_coarse)
+    Ks, Ps, offs, Bp = build_hierarchy(K1, A1, Ap, d, n2, npres, max_levels - 1, max_coarse, steps)
     off0 = field_offsets(n2, npres, d)
     K = [k0["K"]] + Ks
     P0 = _csr(sp.identity(K[0].shape[0], format="csr"))
     P = [P0] + Ps
     field_off = [off0] + offs
     bpat = {0: k0["Bpat"], 1: B1pat}
-    patches = [make_patches(K[l], field_off[l], d, Bpattern=bpat.get(l)) for l in range(len(K) - 1)]
+    patches = [make_patches(K[l], field_off[l], d, Bpattern=bpat[l]) if l in bpat
+               else steps.patches(K[l], field_off[l], d) for l in range(len(K) - 1)]
     L = len(K)
     cn = np.zeros(K[-1].shape[0])
     offL = field_off[-1]
