@@ -204,7 +204,7 @@ __device__ __forceinline__ bool ar_complete(const KrChunks& ch, int c, const dou
 }
 
 template <int NK, int U>
-__global__ void __launch_bounds__(kArThreads) k_ar_dots(KrChunks ch, const double* __restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(kArThreads, 2) k_ar_dots(KrChunks ch, const double* __restrict__ V, int64_t ldv,
     const double* __restrict__ w, double* __restrict__ partial, int ldp, int* __restrict__ cnt,
     double* __restrict__ hout, int ldh, int* __restrict__ zero_flag) {
   griddep_wait();
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kArThreads) k_ar_dots(KrChunks ch, const doubl
 }
 
 template <int NK>
-__global__ void __launch_bounds__(kArThreads) k_ar_axpy_dots(KrChunks ch, const double* __restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(kArThreads, 2) k_ar_axpy_dots(KrChunks ch, const double* __restrict__ V, int64_t ldv,
     const double* __restrict__ coef, int ldh, double* __restrict__ w, double* __restrict__ partial, int ldp,
     int* __restrict__ cnt, double* __restrict__ hout) {
   griddep_wait();
@@ -246,6 +246,9 @@ __global__ void __launch_bounds__(kArThreads) k_ar_axpy_dots(KrChunks ch, const 
   const int s = ch.seg[c];
   if (threadIdx.x < NK) cf[threadIdx.x] = coef[(int64_t)s * ldh + threadIdx.x];
   __syncthreads();
+  // the coefficients are read from shared memory at each use (volatile), so
+  // that the NK accumulators, not NK hoisted coefficients, hold the registers
+  const volatile double* cfv = cf;
   double acc[NK];
 #pragma unroll
   for (int k = 0; k < NK; ++k) acc[k] = 0.0;
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kArThreads) k_ar_axpy_dots(KrChunks ch, const 
       for (int k = 0; k < G; ++k) v[k] = k0 + k < NK ? V[(int64_t)(k0 + k) * ldv + r] : 0.0;
 #pragma unroll
       for (int k = 0; k < G; ++k)
-        if (k0 + k < NK) t = fma(-cf[k0 + k], v[k], t);
+        if (k0 + k < NK) t = fma(-cfv[k0 + k], v[k], t);
     }
     w[r] = t;
 #pragma unroll
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kArThreads) k_ar_axpy_dots(KrChunks ch, const 
 }
 
 template <int NK>
-__global__ void __launch_bounds__(kArThreads) k_ar_axpy_norm(KrChunks ch, const double* __restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(kArThreads, 2) k_ar_axpy_norm(KrChunks ch, const double* __restrict__ V, int64_t ldv,
     const double* __restrict__ h1buf, const double* __restrict__ h2buf, int ldh, double* __restrict__ w,
     double* __restrict__ partial, int ldp, int* __restrict__ cnt, int m, int j, FgState st, double rtol, int maxit) {
   griddep_wait();
@@ -290,6 +293,7 @@ __global__ void __launch_bounds__(kArThreads) k_ar_axpy_norm(KrChunks ch, const 
   const int s = ch.seg[c];
   if (threadIdx.x < NK) cf[threadIdx.x] = h2buf[(int64_t)s * ldh + threadIdx.x];
   __syncthreads();
+  const volatile double* cfv = cf;  // read at each use, as in k_ar_axpy_dots
   double acc[1] = {0.0};
   // P rows per thread per step with their column loads issued together
   // (the pass reads V once, from DRAM: more loads in flight)
@@ -308,10 +312,12 @@ __global__ void __launch_bounds__(kArThreads) k_ar_axpy_norm(KrChunks ch, const 
         for (int k = 0; k < G; ++k)
           v[p][k] = k0 + k < NK && r + p * kArThreads < re ? V[(int64_t)(k0 + k) * ldv + r + p * kArThreads] : 0.0;
 #pragma unroll
-      for (int p = 0; p < P; ++p)
+      for (int k = 0; k < G; ++k)
+        if (k0 + k < NK) {
+          const double ck = cfv[k0 + k];
 #pragma unroll
-        for (int k = 0; k < G; ++k)
-          if (k0 + k < NK) t[p] = fma(-cf[k0 + k], v[p][k], t[p]);
+          for (int p = 0; p < P; ++p) t[p] = fma(-ck, v[p][k], t[p]);
+        }
     }
 #pragma unroll
     for (int p = 0; p < P; ++p)
@@ -368,7 +374,8 @@ cudaError_t ar_dots(const KrChunks& ch, int nc, const double* V, int64_t ldv, co
   switch (nc) {
 #define SD_AR_DOTS(K)                                                                                           \
   case K:                                                                                                      \
-    return launch_pdl(k_ar_dots<K, 4>, dim3(ch.n), dim3(kArThreads), 0, s, ch, V, ldv, w,                       \
+    return launch_pdl(k_ar_dots<K, (K <= 8 ? 4 : K <= 16 ? 2 : 1)>, dim3(ch.n), dim3(kArThreads), 0, s, ch, V,   \
+                      ldv, w,                                                                                     \
                       partial, ldp, cnt, h, ldh, zero_flag);
     SD_AR_CASES(SD_AR_DOTS)
 #undef SD_AR_DOTS
