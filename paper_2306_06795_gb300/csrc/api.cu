@@ -155,6 +155,9 @@ struct stokes_handle {
   double* Z = nullptr;
   double* w = nullptr;
   double* partial = nullptr;
+  void* fold_x0 = nullptr;    // while the DC cycle runs level 1: x0, which level 1's last scatter adds x1 to
+  bool folded = false;        // ... and whether it did
+  bool r32_ready = false;     // the FP32 copy of the cycle input is already in lv[0].b (FGMRES steps)
   double* hd = nullptr;   // device h: [ninst][ldh]
   double* yd = nullptr;   // device coefficients [ninst][ldh]
   int* actd = nullptr;
@@ -473,7 +476,7 @@ int L_apply(stokes_handle* h, const Level& lv, const TR* r, T* yp) {
 
 template <typename T>
 int L_scatter(stokes_handle* h, const Level& lv, const T* yp, T* x, double omega, int mode,
-              const double* r64 = nullptr, double* out64 = nullptr, double* x64 = nullptr) {
+              const double* r64 = nullptr, double* out64 = nullptr, double* x64 = nullptr, T* xadd = nullptr) {
   const DevPatches& p = lv.pat;
   if (h->led.count) {
     double b = 4.0 * (lv.n + 1) + double(p.nslots) * sizeof(T);
@@ -481,11 +484,12 @@ int L_scatter(stokes_handle* h, const Level& lv, const T* yp, T* x, double omega
     else if (mode == 1) b += 2.0 * lv.n * sizeof(T);
     else b += double(lv.n) * (sizeof(T) + 1 + 8);
     if (x64 && mode != 2) b += 8.0 * lv.n;
+    if (xadd) b += 2.0 * lv.n * sizeof(T);
     h->led.bytes += b;
     h->led.launches += 1;
     return STOKES_OK;
   }
-  CK(vanka_scatter<T>(p, lv.n, yp, x, omega, mode, h->dir0, r64, out64, h->st, x64));
+  CK(vanka_scatter<T>(p, lv.n, yp, x, omega, mode, h->dir0, r64, out64, h->st, x64, xadd));
   return STOKES_OK;
 }
 
@@ -726,8 +730,10 @@ int relax_krylov(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T
 // A DLSC level runs nsweeps calls of dlsc_sweeps DLSC sweeps instead.
 template <typename T>
 int relax(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b, int nsweeps, bool zero_guess,
-          const double* r64 = nullptr, double* out64 = nullptr, double* x64 = nullptr) {
+          const double* r64 = nullptr, double* out64 = nullptr, double* x64 = nullptr, T* xadd = nullptr) {
   Level& L = lvs[l];
+  if (xadd && (L.krylov || L.dlsc || L.jacobi || nsweeps < 1 || out64))
+    return fail(STOKES_ERR_INVALID_ARG, "internal: accumulate target on a non-Vanka relaxation");
   if (L.krylov) {
     if (nsweeps == 0) {
       if (zero_guess) TRY(L_zero<T>(h, L.n, x));
@@ -751,13 +757,14 @@ int relax(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b, in
   for (int s = 0; s < nsweeps; ++s) {
     const bool last_out = out64 && s == nsweeps - 1;
     double* xd = s == nsweeps - 1 ? x64 : nullptr;
+    T* xa = s == nsweeps - 1 ? xadd : nullptr;
     if (s == 0 && zero_guess) {
       TRY((L_apply<T, T>(h, L, b, yp)));
-      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 0, r64, out64, xd));
+      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 0, r64, out64, xd, xa));
     } else {
       TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
       TRY((L_apply<T, T>(h, L, r, yp)));
-      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 1, r64, out64, xd));
+      TRY(L_scatter<T>(h, L, yp, x, L.omega, last_out ? 2 : 1, r64, out64, xd, xa));
     }
   }
   return STOKES_OK;
@@ -785,7 +792,13 @@ int vcycle(stokes_handle* h, std::vector<Level>& lvs, int l) {
   TRY((L_spmv<T, T, T, T, T>(h, L.R, kval<T>(L.R), r, (const T*)nullptr, reinterpret_cast<T*>(C.b), SPMV_SET)));
   TRY(vcycle<T>(h, lvs, l + 1));
   TRY((L_spmv<T, T, T, T, T>(h, L.P, kval<T>(L.P), reinterpret_cast<const T*>(C.x), (const T*)nullptr, x, SPMV_ADD)));
-  if (relax_here) TRY(relax<T>(h, lvs, l, x, b, nu2, false));
+  // level 1 of the DC cycle with P0 = I: the last scatter of the
+  // post-relaxation also adds x1 to x0 (dc_cycle then skips x0 += x1)
+  T* fold = main && l == 1 && h->fold_x0 && relax_here && nu2 > 0 && !L.krylov && !L.dlsc && !L.jacobi
+                ? reinterpret_cast<T*>(h->fold_x0)
+                : nullptr;
+  if (relax_here) TRY(relax<T>(h, lvs, l, x, b, nu2, false, nullptr, nullptr, nullptr, fold));
+  if (fold) h->folded = true;
   return STOKES_OK;
 }
 
@@ -823,7 +836,8 @@ int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
   if (sizeof(T) == 8) {
     r0 = reinterpret_cast<const T*>(r64);
   } else {
-    TRY((L_cast<double, T>(h, L0.n, r64, reinterpret_cast<T*>(L0.b))));
+    // inside FGMRES the kernel that forms r64 also wrote its FP32 copy
+    if (!h->r32_ready) TRY((L_cast<double, T>(h, L0.n, r64, reinterpret_cast<T*>(L0.b))));
     r0 = reinterpret_cast<const T*>(L0.b);
   }
   const bool skip0 = h->schedule == STOKES_DC_SKIP0 || !(L0.has_patches || L0.dlsc);
@@ -848,8 +862,14 @@ int dc_cycle(stokes_handle* h, const double* r64, double* z64) {
   } else {
     TRY(restrict0_sv(h, x0d, r64));
   }
-  TRY(vcycle<T>(h, h->lv, 1));
-  if (L0.Pident) TRY((L_axpy<T, T>(h, L0.n, 1.0, reinterpret_cast<const T*>(L1.x), x0)));  // P0 = I
+  h->fold_x0 = L0.Pident ? x0 : nullptr;
+  h->folded = false;
+  const int rc1 = vcycle<T>(h, h->lv, 1);
+  h->fold_x0 = nullptr;
+  TRY(rc1);
+  if (L0.Pident) {  // P0 = I
+    if (!h->folded) TRY((L_axpy<T, T>(h, L0.n, 1.0, reinterpret_cast<const T*>(L1.x), x0)));
+  }
   else TRY((L_spmv<T, T, T, T, T>(h, L0.P, kval<T>(L0.P), reinterpret_cast<const T*>(L1.x), (const T*)nullptr, x0, SPMV_ADD)));
   if (!skip0 && h->nu2 > 0) TRY(relax<T>(h, h->lv, 0, x0, r0, h->nu2, false, r64, z64));
   else TRY(L_finalize<T>(h, L0.n, x0, r64, z64));
@@ -2308,6 +2328,12 @@ int seg_dots(stokes_handle* h, const double* V, int64_t ldv, int ncols, const do
   return STOKES_OK;
 }
 
+// An FP32 DC cycle inside FGMRES reads its input in FP32 from lv[0].b: the
+// kernel that forms each Krylov vector writes that copy too, so the cycle
+// needs no FP64-to-FP32 conversion launch.
+bool r32_input(const stokes_handle* h) { return h->prec == STOKES_FP32 && h->precond == STOKES_PRECOND_DC; }
+float* r32_out(stokes_handle* h) { return r32_input(h) ? reinterpret_cast<float*>(h->lv[0].b) : nullptr; }
+
 // One Arnoldi step j (Sec. 4, right-preconditioned flexible GMRES):
 // z_j = M_dc^-1 v_j (the DC cycle), w = K0 z_j, classical Gram-Schmidt twice,
 // device-side Givens update and v_{j+1} = w / ||w|| for running instances;
@@ -2318,7 +2344,10 @@ int arnoldi_step(stokes_handle* h, int j, double rtol, int maxit) {
   Level& L0 = h->lv[0];
   double* vj = h->V + (size_t)j * n;
   double* zj = h->Z + (size_t)j * n;
-  TRY(run_cycle(h, vj, zj));
+  h->r32_ready = r32_input(h);
+  const int rc0 = run_cycle(h, vj, zj);
+  h->r32_ready = false;
+  TRY(rc0);
   CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, zj, zj, h->w, SPMV_SET, 0, 0, nullptr, h->st)));
   // classical Gram-Schmidt twice: h1 = V^T w, w -= V h1, h2 = V^T w,
   // w -= V h2, then ||w||^2 (a second pass is needed at nearly every step:
@@ -2330,7 +2359,8 @@ int arnoldi_step(stokes_handle* h, int j, double rtol, int maxit) {
     CK(ar_axpy_dots(h->arch, nc, h->V, n, h->hd, h->ldh, h->w, h->partial, h->ldp, h->arcnt, h->yd, h->st));
     CK(ar_axpy_norm_update(h->arch, nc, h->V, n, h->hd, h->yd, h->ldh, h->w, h->partial, h->ldp, h->arcnt,
                            h->krylov_m, j, h->fg, rtol, maxit, h->st));
-    CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st));
+    CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st,
+               r32_out(h)));
     CK(cudaMemcpyAsync(h->hstat + j, h->fg.stat + j, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     return STOKES_OK;
   }
@@ -2342,7 +2372,8 @@ int arnoldi_step(stokes_handle* h, int j, double rtol, int maxit) {
   CK(multidot_partial(h->ndchunks, h->dbeg, h->dend, 1, h->w, 0, h->w, h->partial, h->ldp, h->st));
   CK(multidot_finish(ni, h->sd_beg, h->sd_end, 1, h->partial, h->ldp, h->yd + nc, h->ldh, 0, h->st));
   CK(fg_update(ni, h->krylov_m, j, h->fg, h->yd, h->hd, h->ldh, rtol, maxit, h->st));
-  CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st));
+  CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->w, h->V + (size_t)(j + 1) * n, h->fg.scale, h->st,
+             r32_out(h)));
   CK(cudaMemcpyAsync(h->hstat + j, h->fg.stat + j, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   return STOKES_OK;
 }
@@ -2411,7 +2442,7 @@ extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x,
     CK((spmv<double, double, double, double, double>(L0.K, L0.K.v64, x, b, h->V, SPMV_RES, 0, 0, nullptr, h->st)));
     TRY(seg_dots(h, h->V, 0, 1, h->V, 0));
     CK(fg_start(ni, m, h->fg, h->hd, h->ldh, rtol, maxit, 0, h->st));
-    CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->V, h->V, h->fg.scale, h->st));
+    CK(seg_mul(h->nchunks, h->cbeg, h->cend, h->cseg, h->V, h->V, h->fg.scale, h->st, r32_out(h)));
     CK(cudaMemcpyAsync(h->hstat + m, h->fg.stat + m, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (!h->hstat[m]) break;
@@ -2423,7 +2454,7 @@ extern "C" int stokes_fgmres_solve(stokes_handle* h, const double* b, double* x,
       cudaGraphExec_t ge;
       TRY(iter_graph(h, j, rtol, maxit, &ge));
       CK(cudaGraphLaunch(ge, h->st));
-      h->launches += h->cycle_launches + (j + 1 <= kArMaxCols ? 5 : 11);
+      h->launches += h->cycle_launches - (r32_input(h) ? 1 : 0) + (j + 1 <= kArMaxCols ? 5 : 11);
       CK(cudaEventRecord(h->ev_iter[j], h->st));
       last = j;
       if (j > 0) {

@@ -188,11 +188,11 @@ cudaError_t vanka_apply(const DevPatches& p, const TR* r, T* yp, cudaStream_t st
 // ascending patch order; mode 0: x_j = omega s_j / cnt_j; mode 1: x_j +=
 // omega s_j / cnt_j; mode 2 (final level-0 output): out_j = dir_j ? r64_j :
 // double(x_j + omega s_j / cnt_j).  With x64 (modes 0, 1) the new x is also
-// written in FP64.
+// written in FP64; with xadd (modes 0, 1) it is also added to xadd_j.
 template <typename T>
 cudaError_t vanka_scatter(const DevPatches& p, int64_t n, const T* yp, T* x, double omega, int mode,
                           const uint8_t* dir, const double* r64, double* out64, cudaStream_t st,
-                          double* x64 = nullptr);
+                          double* x64 = nullptr, T* xadd = nullptr);
 
 // Elementwise helpers
 template <typename TI, typename TO>
@@ -332,9 +332,10 @@ cudaError_t ar_axpy_dots(const KrChunks& ch, int nc, const double* V, int64_t ld
 cudaError_t ar_axpy_norm_update(const KrChunks& ch, int nc, const double* V, int64_t ldv, const double* h1,
                                 const double* h2, int ldh, double* w, double* partial, int ldp, int* cnt, int m, int j,
                                 const FgState& st, double rtol, int maxit, cudaStream_t s);
-// out[row] = in[row] * f[seg(row)] (0 when f is 0)
+// out[row] = in[row] * f[seg(row)] (0 when f is 0); out32, when given,
+// receives the same values rounded to FP32
 cudaError_t seg_mul(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, const double* in,
-                    double* out, const double* f, cudaStream_t s);
+                    double* out, const double* f, cudaStream_t s, float* out32 = nullptr);
 
 // out[row] = in[row] * scale_inv(seg)  where scale_inv = (den[seg*ldd + kd] > 0 && active[seg]) ? 1/den : 0
 cudaError_t seg_scale(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg,

@@ -349,14 +349,18 @@ __global__ void k_fg_solve(int ninst, int m, FgState st, int ldh) {
   }
 }
 
-// out[row] = in[row] * f[seg(row)]
+// out[row] = in[row] * f[seg(row)] (and its FP32 rounding in out32)
 __global__ void __launch_bounds__(256) k_seg_mul(const int64_t* __restrict__ cbeg, const int64_t* __restrict__ cend,
-                                                 const int* __restrict__ cseg, const double* __restrict__ in,
-                                                 double* __restrict__ out, const double* __restrict__ f) {
+                                                 const int* __restrict__ cseg, const double* in, double* out,
+                                                 const double* __restrict__ f, float* __restrict__ out32) {
   pdl_enter();
   const int c = blockIdx.x;
   const double v = f[cseg[c]];
-  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += 256) out[r] = v == 0.0 ? 0.0 : in[r] * v;
+  for (int64_t r = cbeg[c] + threadIdx.x; r < cend[c]; r += 256) {
+    const double o = v == 0.0 ? 0.0 : in[r] * v;
+    out[r] = o;
+    if (out32) out32[r] = (float)o;
+  }
 }
 
 cudaError_t fg_start(int ninst, int m, const FgState& st, const double* h, int ldh, double rtol, int maxit, int first,
@@ -425,9 +429,9 @@ cudaError_t fg_solve(int ninst, int m, const FgState& st, int ldh, cudaStream_t 
   return cudaGetLastError();
 }
 cudaError_t seg_mul(int nchunks, const int64_t* cbeg, const int64_t* cend, const int* cseg, const double* in,
-                    double* out, const double* f, cudaStream_t s) {
+                    double* out, const double* f, cudaStream_t s, float* out32) {
   if (nchunks == 0) return cudaSuccess;
-  SD_LAUNCH(k_seg_mul, nchunks, 256, 0, s, cbeg, cend, cseg, in, out, f);
+  SD_LAUNCH(k_seg_mul, nchunks, 256, 0, s, cbeg, cend, cseg, in, out, f, out32);
   return cudaGetLastError();
 }
 

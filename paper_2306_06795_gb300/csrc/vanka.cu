@@ -830,7 +830,7 @@ cudaError_t vanka_prepare_kernels() {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_vanka_scatter(int64_t n, const int* __restrict__ tptr,
     const T* __restrict__ yp, T* __restrict__ x, T omega, const uint8_t* __restrict__ dir,
-    const double* __restrict__ r64, double* __restrict__ out64, double* __restrict__ x64) {
+    const double* __restrict__ r64, double* __restrict__ out64, double* __restrict__ x64, T* __restrict__ xadd) {
   pdl_enter();
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
@@ -851,24 +851,27 @@ __global__ void __launch_bounds__(256) k_vanka_scatter(int64_t n, const int* __r
   const T xn = MODE == 0 ? upd : x[j] + upd;
   x[j] = xn;
   if (x64) x64[j] = double(xn);  // FP64 copy for the FP64 defect-correction residual
+  if (xadd) xadd[j] += xn;       // the coarse correction of the level above (identity prolongation)
 }
 
 template <typename T>
 cudaError_t vanka_scatter(const DevPatches& p, int64_t n, const T* yp, T* x, double omega, int mode,
-                          const uint8_t* dir, const double* r64, double* out64, cudaStream_t st, double* x64) {
+                          const uint8_t* dir, const double* r64, double* out64, cudaStream_t st, double* x64,
+                          T* xadd) {
   if (n == 0) return cudaSuccess;
+  if (mode == 2 && xadd) return cudaErrorInvalidValue;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (mode == 0)
-    SD_LAUNCH((k_vanka_scatter<T, 0>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
+    SD_LAUNCH((k_vanka_scatter<T, 0>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64, xadd);
   else if (mode == 1)
-    SD_LAUNCH((k_vanka_scatter<T, 1>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
+    SD_LAUNCH((k_vanka_scatter<T, 1>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64, xadd);
   else
-    SD_LAUNCH((k_vanka_scatter<T, 2>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64);
+    SD_LAUNCH((k_vanka_scatter<T, 2>), blocks, 256, 0, st, n, p.tptr, yp, x, T(omega), dir, r64, out64, x64, xadd);
   return cudaGetLastError();
 }
 template cudaError_t vanka_scatter<float>(const DevPatches&, int64_t, const float*, float*, double, int,
-                                          const uint8_t*, const double*, double*, cudaStream_t, double*);
+                                          const uint8_t*, const double*, double*, cudaStream_t, double*, float*);
 template cudaError_t vanka_scatter<double>(const DevPatches&, int64_t, const double*, double*, double, int,
-                                           const uint8_t*, const double*, double*, cudaStream_t, double*);
+                                           const uint8_t*, const double*, double*, cudaStream_t, double*, double*);
 
 }  // namespace sd
