@@ -65,6 +65,11 @@ struct CoarseSet {
 // pressure-correction right-hand side.
 struct DLSCData {
   DevCSR A, B, BT;
+  // p0 > 0: the level's rows are velocity rows [0, p0) then pressure rows
+  // [p0, n) (one instance), and A, B, B^T hold only their nonempty rows:
+  // A the velocity rows, B the pressure rows, B^T the velocity rows with
+  // its columns counted from p0; the sweep works on the two row ranges
+  int64_t p0 = 0;
   uint8_t* kind = nullptr;  // 0 velocity, 1 pressure, 2 rows not relaxed here
   double lamA = 0, lamS = 0;
   void* muinv = nullptr;    // level vector in the cycle precision, or nullptr (Mu = I)
@@ -637,9 +642,13 @@ namespace {
 // pressure-correction Chebyshev solves, then the velocity correction (D.BT
 // already carries Mu^-1, so B D.BT = B Mu^-1 B^T and D.BT q = Mu^-1 B^T q).
 template <typename T>
+int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b);
+
+template <typename T>
 int dlsc_sweep(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b) {
   Level& L = lvs[l];
   DLSCData& D = L.dl;
+  if (D.p0 > 0) return dlsc_sweep_split<T>(h, lvs, l, x, b);
   T** v = reinterpret_cast<T**>(D.v);
   T *res = v[0], *vs = v[1], *q = v[2], *dp = v[3], *t1 = v[4], *t2 = v[5], *cr = v[6], *c0 = v[7], *c1 = v[8];
   const int64_t n = L.n;
@@ -669,6 +678,48 @@ int dlsc_sweep(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* 
   TRY((L_axpy<T, T>(h, n, 1.0, vs, x)));
   TRY((L_axpy<T, T>(h, n, 1.0, dp, x)));
   TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), q, (const T*)nullptr, x, SPMV_ADD)));
+  return STOKES_OK;
+}
+
+// The same sweep on a level whose velocity rows [0, p0) precede its
+// pressure rows [p0, n): every step runs on its own row range (the momentum
+// solve and B^T on the velocity rows, B and the Schur solves on the pressure
+// rows, whose vectors are the level vectors from p0 on), so no launch spends
+// threads or bandwidth on rows the block leaves empty.
+template <typename T>
+int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b) {
+  Level& L = lvs[l];
+  DLSCData& D = L.dl;
+  T** v = reinterpret_cast<T**>(D.v);
+  T *res = v[0], *vs = v[1], *q = v[2], *dp = v[3], *t1 = v[4], *t2 = v[5], *cr = v[6], *c0 = v[7], *c1 = v[8];
+  const int64_t nv = D.p0, np = L.n - D.p0;
+  auto P = [nv](T* p) { return p + nv; };
+  const double fa = std::pow(0.5, h->dim);
+  // res = [f - A u - B^T p; g - B u]
+  TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, res, SPMV_RES)));
+  // v* ~ A^-1 (f - A u - B^T p)
+  TRY(cheb_run<T>(h, D.A, kval<T>(D.A), nullptr, nullptr, nullptr, nullptr, res, nullptr, 0, 1.0, fa * D.lamA,
+                  1.1 * D.lamA, h->cheb_deg[0], vs, cr, c0, c1, nv));
+  // q ~ S^-1 (g - B (u + v*)),  S = B Mu^-1 B^T
+  TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), vs, P(res), P(t1), SPMV_RES)));
+  TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), t2, nullptr, P(t1), nullptr, 1, 1.0, fa * D.lamS,
+                  1.1 * D.lamS, h->cheb_deg[1], P(q), P(cr), P(c0), P(c1), np));
+  // dp ~ S^-1 ( -(B Mu^-1 A Mu^-1 B^T) q )
+  TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), P(q), (const T*)nullptr, t1, SPMV_SET)));
+  TRY((L_spmv<T, T, T, T, T>(h, D.A, kval<T>(D.A), t1, (const T*)nullptr, t2, SPMV_SET)));
+  T* ta = t2;  // A Mu^-1 B^T q
+  T* tb = t1;
+  if (D.muinv) {
+    TRY(L_diag_scale<T>(h, nv, reinterpret_cast<const T*>(D.muinv), t2, t1));
+    std::swap(ta, tb);
+  }
+  TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), ta, (const T*)nullptr, P(tb), SPMV_SET)));
+  TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), ta, nullptr, P(tb), nullptr, 1, -1.0, fa * D.lamS,
+                  1.1 * D.lamS, h->cheb_deg[2], P(dp), P(cr), P(c0), P(c1), np));
+  // u += v* + Mu^-1 B^T q ;  p += dp
+  TRY((L_axpy<T, T>(h, nv, 1.0, vs, x)));
+  TRY((L_axpy<T, T>(h, np, 1.0, P(dp), P(x))));
+  TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), P(q), (const T*)nullptr, x, SPMV_ADD)));
   return STOKES_OK;
 }
 
@@ -1338,9 +1389,35 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
       BT.rowptr.push_back((int)BT.col.size());
     }
   }
-  TRY(upload_csr(h, lv.dl.A, A));
-  TRY(upload_csr(h, lv.dl.B, B));
-  TRY(upload_csr(h, lv.dl.BT, BT));
+  // one velocity run followed by one pressure run: keep only the nonempty rows
+  int64_t p0 = 0;
+  while (p0 < lv.n && kind[p0] == 0) ++p0;
+  bool split = p0 > 0 && p0 < lv.n;
+  for (int64_t i = p0; split && i < lv.n; ++i) split = kind[i] == 1;
+  if (split) {
+    auto rows = [](const HostCSR& M, int64_t r0, int64_t r1, int ncols, int shift) {
+      HostCSR o;
+      o.nrows = (int)(r1 - r0);
+      o.ncols = ncols;  // rowptr starts as {0}
+      for (int64_t i = r0; i < r1; ++i) {
+        for (int e = M.rowptr[i]; e < M.rowptr[i + 1]; ++e) {
+          o.col.push_back(M.col[e] - shift);
+          o.val.push_back(M.val[e]);
+        }
+        o.rowptr.push_back((int)o.col.size());
+      }
+      return o;
+    };
+    const int nv = (int)p0, np = (int)(lv.n - p0);
+    TRY(upload_csr(h, lv.dl.A, rows(A, 0, p0, nv, 0)));
+    TRY(upload_csr(h, lv.dl.B, rows(B, p0, lv.n, nv, 0)));
+    TRY(upload_csr(h, lv.dl.BT, rows(BT, 0, p0, np, nv)));
+    lv.dl.p0 = p0;
+  } else {
+    TRY(upload_csr(h, lv.dl.A, A));
+    TRY(upload_csr(h, lv.dl.B, B));
+    TRY(upload_csr(h, lv.dl.BT, BT));
+  }
   TRY(upload(h, &lv.dl.kind, kind));
   if (mass) {
     if (h->prec == STOKES_FP32) {
