@@ -70,6 +70,7 @@ struct DLSCData {
   // A the velocity rows, B the pressure rows, B^T the velocity rows with
   // its columns counted from p0; the sweep works on the two row ranges
   int64_t p0 = 0;
+  DevCSR S;                 // p0 > 0: S = B Mu^-1 B^T on the pressure rows (formed in FP64 at setup)
   uint8_t* kind = nullptr;  // 0 velocity, 1 pressure, 2 rows not relaxed here
   double lamA = 0, lamS = 0;
   void* muinv = nullptr;    // level vector in the cycle precision, or nullptr (Mu = I)
@@ -685,7 +686,8 @@ int dlsc_sweep(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* 
 // pressure rows [p0, n): every step runs on its own row range (the momentum
 // solve and B^T on the velocity rows, B and the Schur solves on the pressure
 // rows, whose vectors are the level vectors from p0 on), so no launch spends
-// threads or bandwidth on rows the block leaves empty.
+// threads or bandwidth on rows the block leaves empty; each Schur Chebyshev
+// step is one launch on the assembled S = B Mu^-1 B^T instead of B^T then B.
 template <typename T>
 int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b) {
   Level& L = lvs[l];
@@ -702,7 +704,7 @@ int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, con
                   1.1 * D.lamA, h->cheb_deg[0], vs, cr, c0, c1, nv));
   // q ~ S^-1 (g - B (u + v*)),  S = B Mu^-1 B^T
   TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), vs, P(res), P(t1), SPMV_RES)));
-  TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), t2, nullptr, P(t1), nullptr, 1, 1.0, fa * D.lamS,
+  TRY(cheb_run<T>(h, D.S, kval<T>(D.S), nullptr, nullptr, nullptr, nullptr, P(t1), nullptr, 1, 1.0, fa * D.lamS,
                   1.1 * D.lamS, h->cheb_deg[1], P(q), P(cr), P(c0), P(c1), np));
   // dp ~ S^-1 ( -(B Mu^-1 A Mu^-1 B^T) q )
   TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), P(q), (const T*)nullptr, t1, SPMV_SET)));
@@ -714,7 +716,7 @@ int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, con
     std::swap(ta, tb);
   }
   TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), ta, (const T*)nullptr, P(tb), SPMV_SET)));
-  TRY(cheb_run<T>(h, D.B, kval<T>(D.B), &D.BT, kval<T>(D.BT), ta, nullptr, P(tb), nullptr, 1, -1.0, fa * D.lamS,
+  TRY(cheb_run<T>(h, D.S, kval<T>(D.S), nullptr, nullptr, nullptr, nullptr, P(tb), nullptr, 1, -1.0, fa * D.lamS,
                   1.1 * D.lamS, h->cheb_deg[2], P(dp), P(cr), P(c0), P(c1), np));
   // u += v* + Mu^-1 B^T q ;  p += dp
   TRY((L_axpy<T, T>(h, nv, 1.0, vs, x)));
@@ -1409,9 +1411,40 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
       return o;
     };
     const int nv = (int)p0, np = (int)(lv.n - p0);
+    const HostCSR Bp = rows(B, p0, lv.n, nv, 0), BTv = rows(BT, 0, p0, np, nv);
+    // S = B (Mu^-1 B^T) on the pressure rows, the Schur operator of Alg. 2,
+    // formed once (FP64 sums in the order of B's row, then B^T's row k);
+    // columns in first-appearance order, then sorted
+    HostCSR S;
+    S.nrows = S.ncols = np;
+    std::vector<double> acc(np, 0.0);
+    std::vector<int> mark(np, -1), cols;
+    for (int i = 0; i < np; ++i) {
+      cols.clear();
+      for (int e = Bp.rowptr[i]; e < Bp.rowptr[i + 1]; ++e) {
+        const int k = Bp.col[e];
+        const double bik = Bp.val[e];
+        for (int f = BTv.rowptr[k]; f < BTv.rowptr[k + 1]; ++f) {
+          const int j = BTv.col[f];
+          if (mark[j] != i) {
+            mark[j] = i;
+            acc[j] = 0.0;
+            cols.push_back(j);
+          }
+          acc[j] += bik * BTv.val[f];
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      for (int j : cols) {
+        S.col.push_back(j);
+        S.val.push_back(acc[j]);
+      }
+      S.rowptr.push_back((int)S.col.size());
+    }
     TRY(upload_csr(h, lv.dl.A, rows(A, 0, p0, nv, 0)));
-    TRY(upload_csr(h, lv.dl.B, rows(B, p0, lv.n, nv, 0)));
-    TRY(upload_csr(h, lv.dl.BT, rows(BT, 0, p0, np, nv)));
+    TRY(upload_csr(h, lv.dl.B, Bp));
+    TRY(upload_csr(h, lv.dl.BT, BTv));
+    TRY(upload_csr(h, lv.dl.S, S));
     lv.dl.p0 = p0;
   } else {
     TRY(upload_csr(h, lv.dl.A, A));
