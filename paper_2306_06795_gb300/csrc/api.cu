@@ -71,6 +71,7 @@ struct DLSCData {
   // its columns counted from p0; the sweep works on the two row ranges
   int64_t p0 = 0;
   DevCSR S;                 // p0 > 0: S = B Mu^-1 B^T on the pressure rows (formed in FP64 at setup)
+  bool pp_zero = false;     // K has no pressure-pressure entries on the relaxed rows
   uint8_t* kind = nullptr;  // 0 velocity, 1 pressure, 2 rows not relaxed here
   double lamA = 0, lamS = 0;
   void* muinv = nullptr;    // level vector in the cycle precision, or nullptr (Mu = I)
@@ -592,6 +593,19 @@ int L_cheb_step(stokes_handle* h, const DevCSR& M, const T* val, const T* w, con
   return STOKES_OK;
 }
 
+template <typename T>
+int L_cheb_first(stokes_handle* h, const DevCSR& M, const T* val, const T* b, double s, double theta, T* x, T* r,
+                 T* dout, double alpha, double beta, bool accumulate) {
+  if (h->led.count) {
+    h->led.bytes += double(M.nnz) * (sizeof(T) + 4) + 4.0 * (M.nrows + 1) + double(M.ncols) * sizeof(T) +
+                    double(M.nrows) * sizeof(T) * (accumulate ? 5 : 4);
+    h->led.launches += M.nrows > 0;
+    return STOKES_OK;
+  }
+  CK(cheb_first<T>(M, val, b, s, theta, x, r, dout, alpha, beta, accumulate, h->st));
+  return STOKES_OK;
+}
+
 template <typename TI, typename TO>
 int L_scatter_rows(stokes_handle* h, int64_t n, const TI* in, const int* rows, TO* out) {
   if (h->led.count) {
@@ -609,13 +623,24 @@ int L_scatter_rows(stokes_handle* h, int64_t n, const TI* in, const int* rows, T
 template <typename T>
 int cheb_run(stokes_handle* h, const DevCSR& M, const T* mval, const DevCSR* BT, const T* btval, T* tS,
              const T* dinv, const T* rhs, const uint8_t* mask, uint8_t want, double s, double lo, double hi,
-             int degree, T* x, T* r, T* d0, T* d1, int64_t n) {
+             int degree, T* x, T* r, T* d0, T* d1, int64_t n, bool accumulate = false) {
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
   double rho = 1.0 / sigma;
-  TRY(L_cheb_init<T>(h, n, rhs, dinv, mask, want, s, theta, r, d0, x));
   T* dc = d0;
   T* dn = d1;
-  for (int k = 0; k < degree; ++k) {
+  int k = 0;
+  if (!BT && !dinv && !mask && degree > 0 && M.nrows == n) {
+    // initialisation fused into the first step (x accumulates with `accumulate`)
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    TRY(L_cheb_first<T>(h, M, mval, rhs, s, theta, x, r, dn, rho_new * rho, 2.0 * rho_new / delta, accumulate));
+    std::swap(dc, dn);
+    rho = rho_new;
+    k = 1;
+  } else {
+    if (accumulate) return fail(STOKES_ERR_INVALID_ARG, "internal: accumulating Chebyshev needs the fused first step");
+    TRY(L_cheb_init<T>(h, n, rhs, dinv, mask, want, s, theta, r, d0, x));
+  }
+  for (; k < degree; ++k) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const double alpha = rho_new * rho, beta = 2.0 * rho_new / delta;
     const T* w = dc;
@@ -697,13 +722,20 @@ int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, con
   const int64_t nv = D.p0, np = L.n - D.p0;
   auto P = [nv](T* p) { return p + nv; };
   const double fa = std::pow(0.5, h->dim);
+  // without a pressure-pressure block the momentum and pressure corrections
+  // accumulate into x directly, and g - B (u + v*) is the pressure residual
+  // of the updated x
+  const bool acc = D.pp_zero;
   // res = [f - A u - B^T p; g - B u]
   TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, res, SPMV_RES)));
   // v* ~ A^-1 (f - A u - B^T p)
   TRY(cheb_run<T>(h, D.A, kval<T>(D.A), nullptr, nullptr, nullptr, nullptr, res, nullptr, 0, 1.0, fa * D.lamA,
-                  1.1 * D.lamA, h->cheb_deg[0], vs, cr, c0, c1, nv));
+                  1.1 * D.lamA, h->cheb_deg[0], acc ? x : vs, cr, c0, c1, nv, acc));
   // q ~ S^-1 (g - B (u + v*)),  S = B Mu^-1 B^T
-  TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), vs, P(res), P(t1), SPMV_RES)));
+  if (acc)
+    TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), x, P(const_cast<T*>(b)), P(t1), SPMV_RES)));
+  else
+    TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), vs, P(res), P(t1), SPMV_RES)));
   TRY(cheb_run<T>(h, D.S, kval<T>(D.S), nullptr, nullptr, nullptr, nullptr, P(t1), nullptr, 1, 1.0, fa * D.lamS,
                   1.1 * D.lamS, h->cheb_deg[1], P(q), P(cr), P(c0), P(c1), np));
   // dp ~ S^-1 ( -(B Mu^-1 A Mu^-1 B^T) q )
@@ -717,10 +749,12 @@ int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, con
   }
   TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), ta, (const T*)nullptr, P(tb), SPMV_SET)));
   TRY(cheb_run<T>(h, D.S, kval<T>(D.S), nullptr, nullptr, nullptr, nullptr, P(tb), nullptr, 1, -1.0, fa * D.lamS,
-                  1.1 * D.lamS, h->cheb_deg[2], P(dp), P(cr), P(c0), P(c1), np));
+                  1.1 * D.lamS, h->cheb_deg[2], acc ? P(x) : P(dp), P(cr), P(c0), P(c1), np, acc));
   // u += v* + Mu^-1 B^T q ;  p += dp
-  TRY((L_axpy<T, T>(h, nv, 1.0, vs, x)));
-  TRY((L_axpy<T, T>(h, np, 1.0, P(dp), P(x))));
+  if (!acc) {
+    TRY((L_axpy<T, T>(h, nv, 1.0, vs, x)));
+    TRY((L_axpy<T, T>(h, np, 1.0, P(dp), P(x))));
+  }
   TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), P(q), (const T*)nullptr, x, SPMV_ADD)));
   return STOKES_OK;
 }
@@ -1361,6 +1395,7 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
   // level 0 (the P2 grid): Mu = diag(Mu_diag); levels >= 1: Mu = I
   const bool mass = l == 0;
   std::vector<double> muinv(mass ? lv.n : 0, 0.0);
+  bool has_pp = false;
   for (int k = 0; k < ninst; ++k) {
     const stokes_problem* p = probs[k];
     if (p->nlevels <= l) continue;
@@ -1381,7 +1416,10 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
         const int c = K->col[e];
         const bool cvel = c < off[dim];
         HostCSR& dst = vel ? (cvel ? A : BT) : (cvel ? B : A);
-        if (!vel && !cvel) continue;  // zero block
+        if (!vel && !cvel) {  // zero block (a nonzero entry here is left out of A, B, B^T)
+          if (K->val[e] != 0.0) has_pp = true;
+          continue;
+        }
         dst.col.push_back((int)(o + c));
         // B^T rows carry Mu^-1 (velocity row i of B^T scaled by 1/Mu_i)
         dst.val.push_back(mass && vel && !cvel ? K->val[e] * muinv[o + i] : K->val[e]);
@@ -1446,6 +1484,7 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
     TRY(upload_csr(h, lv.dl.BT, BTv));
     TRY(upload_csr(h, lv.dl.S, S));
     lv.dl.p0 = p0;
+    lv.dl.pp_zero = !has_pp;
   } else {
     TRY(upload_csr(h, lv.dl.A, A));
     TRY(upload_csr(h, lv.dl.B, B));

@@ -177,6 +177,48 @@ cudaError_t cheb_step(const DevCSR& M, const T* val, const T* w, const T* dinv, 
   SD_LAUNCH((k_cheb_step<T, 8>), blocks, 256, 0, st, M.nrows, M.rowptr, M.col, val, w, dinv, x, r, d_in, d_out, T(alpha), T(beta));
   return cudaGetLastError();
 }
+template <typename T, int TPR, bool ACC>
+__global__ void __launch_bounds__(256) k_cheb_first(int nrows, const int* __restrict__ rowptr,
+                                                    const int* __restrict__ col, const T* __restrict__ val,
+                                                    const T* __restrict__ b, T s, T c, T* __restrict__ x,
+                                                    T* __restrict__ r, T* __restrict__ dout, T alpha, T beta) {
+  pdl_enter();
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = tid / TPR;
+  const int lane = (int)(tid % TPR);
+  const bool valid = row < nrows;
+  T sum = T(0);
+  if (valid)
+    for (int k = rowptr[row] + lane; k < rowptr[row + 1]; k += TPR) sum += val[k] * b[col[k]];
+#pragma unroll
+  for (int off = TPR / 2; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off, TPR);
+  if (valid && lane == 0) {
+    const T bv = b[row];
+    const T d0 = c * bv;  // d0 = (s / theta) b;  M d0 = c M b
+    x[row] = ACC ? x[row] + d0 : d0;
+    const T rv = s * bv - c * sum;
+    r[row] = rv;
+    dout[row] = alpha * d0 + beta * rv;
+  }
+}
+template <typename T>
+cudaError_t cheb_first(const DevCSR& M, const T* val, const T* b, double s, double theta, T* x, T* r, T* d_out,
+                       double alpha, double beta, bool accumulate, cudaStream_t st) {
+  if (M.nrows == 0) return cudaSuccess;
+  const int64_t total = (int64_t)M.nrows * 8;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  if (accumulate)
+    SD_LAUNCH((k_cheb_first<T, 8, true>), blocks, 256, 0, st, M.nrows, M.rowptr, M.col, val, b, T(s), T(s / theta), x,
+              r, d_out, T(alpha), T(beta));
+  else
+    SD_LAUNCH((k_cheb_first<T, 8, false>), blocks, 256, 0, st, M.nrows, M.rowptr, M.col, val, b, T(s), T(s / theta), x,
+              r, d_out, T(alpha), T(beta));
+  return cudaGetLastError();
+}
+template cudaError_t cheb_first<float>(const DevCSR&, const float*, const float*, double, double, float*, float*,
+                                       float*, double, double, bool, cudaStream_t);
+template cudaError_t cheb_first<double>(const DevCSR&, const double*, const double*, double, double, double*, double*,
+                                        double*, double, double, bool, cudaStream_t);
 template cudaError_t cheb_step<float>(const DevCSR&, const float*, const float*, const float*, float*, float*,
                                       const float*, float*, double, double, cudaStream_t);
 template cudaError_t cheb_step<double>(const DevCSR&, const double*, const double*, const double*, double*, double*,

@@ -223,6 +223,12 @@ cudaError_t cheb_init(int64_t n, const T* b, const T* dinv, const uint8_t* mask,
 template <typename T>
 cudaError_t cheb_step(const DevCSR& M, const T* val, const T* w, const T* dinv, T* x, T* r, const T* d_in, T* d_out,
                       double alpha, double beta, cudaStream_t st);
+// The first step fused with the initialisation (no mask, no dinv):
+//   d0 = (s / theta) b;  x = d0 (accumulate: x += d0);  r = s b - M d0;
+//   d_out = alpha d0 + beta r
+template <typename T>
+cudaError_t cheb_first(const DevCSR& M, const T* val, const T* b, double s, double theta, T* x, T* r, T* d_out,
+                       double alpha, double beta, bool accumulate, cudaStream_t st);
 // out[rows[i]] = T(in[i])
 template <typename TI, typename TO>
 cudaError_t scatter_rows(int64_t n, const TI* in, const int* rows, TO* out, cudaStream_t st);
