@@ -72,6 +72,7 @@ struct DLSCData {
   int64_t p0 = 0;
   DevCSR S;                 // p0 > 0: S = B Mu^-1 B^T on the pressure rows (formed in FP64 at setup)
   bool pp_zero = false;     // K has no pressure-pressure entries on the relaxed rows
+  DevCSR T;                 // p0 > 0: T = B Mu^-1 A Mu^-1 B^T on the pressure rows (setup, FP64)
   uint8_t* kind = nullptr;  // 0 velocity, 1 pressure, 2 rows not relaxed here
   double lamA = 0, lamS = 0;
   void* muinv = nullptr;    // level vector in the cycle precision, or nullptr (Mu = I)
@@ -712,13 +713,15 @@ int dlsc_sweep(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* 
 // solve and B^T on the velocity rows, B and the Schur solves on the pressure
 // rows, whose vectors are the level vectors from p0 on), so no launch spends
 // threads or bandwidth on rows the block leaves empty; each Schur Chebyshev
-// step is one launch on the assembled S = B Mu^-1 B^T instead of B^T then B.
+// step is one launch on the assembled S = B Mu^-1 B^T instead of B^T then B,
+// and the pressure-correction right-hand side one SpMV with the assembled
+// T = B Mu^-1 A Mu^-1 B^T instead of four launches.
 template <typename T>
 int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, const T* b) {
   Level& L = lvs[l];
   DLSCData& D = L.dl;
   T** v = reinterpret_cast<T**>(D.v);
-  T *res = v[0], *vs = v[1], *q = v[2], *dp = v[3], *t1 = v[4], *t2 = v[5], *cr = v[6], *c0 = v[7], *c1 = v[8];
+  T *res = v[0], *vs = v[1], *q = v[2], *dp = v[3], *t1 = v[4], *cr = v[6], *c0 = v[7], *c1 = v[8];
   const int64_t nv = D.p0, np = L.n - D.p0;
   auto P = [nv](T* p) { return p + nv; };
   const double fa = std::pow(0.5, h->dim);
@@ -738,17 +741,9 @@ int dlsc_sweep_split(stokes_handle* h, std::vector<Level>& lvs, int l, T* x, con
     TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), vs, P(res), P(t1), SPMV_RES)));
   TRY(cheb_run<T>(h, D.S, kval<T>(D.S), nullptr, nullptr, nullptr, nullptr, P(t1), nullptr, 1, 1.0, fa * D.lamS,
                   1.1 * D.lamS, h->cheb_deg[1], P(q), P(cr), P(c0), P(c1), np));
-  // dp ~ S^-1 ( -(B Mu^-1 A Mu^-1 B^T) q )
-  TRY((L_spmv<T, T, T, T, T>(h, D.BT, kval<T>(D.BT), P(q), (const T*)nullptr, t1, SPMV_SET)));
-  TRY((L_spmv<T, T, T, T, T>(h, D.A, kval<T>(D.A), t1, (const T*)nullptr, t2, SPMV_SET)));
-  T* ta = t2;  // A Mu^-1 B^T q
-  T* tb = t1;
-  if (D.muinv) {
-    TRY(L_diag_scale<T>(h, nv, reinterpret_cast<const T*>(D.muinv), t2, t1));
-    std::swap(ta, tb);
-  }
-  TRY((L_spmv<T, T, T, T, T>(h, D.B, kval<T>(D.B), ta, (const T*)nullptr, P(tb), SPMV_SET)));
-  TRY(cheb_run<T>(h, D.S, kval<T>(D.S), nullptr, nullptr, nullptr, nullptr, P(tb), nullptr, 1, -1.0, fa * D.lamS,
+  // dp ~ S^-1 ( -(B Mu^-1 A Mu^-1 B^T) q ), the right-hand side by the assembled T
+  TRY((L_spmv<T, T, T, T, T>(h, D.T, kval<T>(D.T), P(q), (const T*)nullptr, P(t1), SPMV_SET)));
+  TRY(cheb_run<T>(h, D.S, kval<T>(D.S), nullptr, nullptr, nullptr, nullptr, P(t1), nullptr, 1, -1.0, fa * D.lamS,
                   1.1 * D.lamS, h->cheb_deg[2], acc ? P(x) : P(dp), P(cr), P(c0), P(c1), np, acc));
   // u += v* + Mu^-1 B^T q ;  p += dp
   if (!acc) {
@@ -1450,36 +1445,47 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
     };
     const int nv = (int)p0, np = (int)(lv.n - p0);
     const HostCSR Bp = rows(B, p0, lv.n, nv, 0), BTv = rows(BT, 0, p0, np, nv);
-    // S = B (Mu^-1 B^T) on the pressure rows, the Schur operator of Alg. 2,
-    // formed once (FP64 sums in the order of B's row, then B^T's row k);
-    // columns in first-appearance order, then sorted
-    HostCSR S;
-    S.nrows = S.ncols = np;
-    std::vector<double> acc(np, 0.0);
-    std::vector<int> mark(np, -1), cols;
-    for (int i = 0; i < np; ++i) {
-      cols.clear();
-      for (int e = Bp.rowptr[i]; e < Bp.rowptr[i + 1]; ++e) {
-        const int k = Bp.col[e];
-        const double bik = Bp.val[e];
-        for (int f = BTv.rowptr[k]; f < BTv.rowptr[k + 1]; ++f) {
-          const int j = BTv.col[f];
-          if (mark[j] != i) {
-            mark[j] = i;
-            acc[j] = 0.0;
-            cols.push_back(j);
+    // X Y of two host CSRs (X's columns index Y's rows), row i scaled by
+    // rs[i] when given: FP64 sums in the order of X's row, then Y's row k;
+    // columns sorted
+    auto product = [](const HostCSR& X, const HostCSR& Y, const double* rs) {
+      HostCSR Z;
+      Z.nrows = X.nrows;
+      Z.ncols = Y.ncols;
+      std::vector<double> acc(Y.ncols, 0.0);
+      std::vector<int> mark(Y.ncols, -1), cols;
+      for (int i = 0; i < X.nrows; ++i) {
+        cols.clear();
+        for (int e = X.rowptr[i]; e < X.rowptr[i + 1]; ++e) {
+          const int k = X.col[e];
+          const double xik = X.val[e];
+          for (int f = Y.rowptr[k]; f < Y.rowptr[k + 1]; ++f) {
+            const int j = Y.col[f];
+            if (mark[j] != i) {
+              mark[j] = i;
+              acc[j] = 0.0;
+              cols.push_back(j);
+            }
+            acc[j] += xik * Y.val[f];
           }
-          acc[j] += bik * BTv.val[f];
         }
+        std::sort(cols.begin(), cols.end());
+        for (int j : cols) {
+          Z.col.push_back(j);
+          Z.val.push_back(rs ? rs[i] * acc[j] : acc[j]);
+        }
+        Z.rowptr.push_back((int)Z.col.size());
       }
-      std::sort(cols.begin(), cols.end());
-      for (int j : cols) {
-        S.col.push_back(j);
-        S.val.push_back(acc[j]);
-      }
-      S.rowptr.push_back((int)S.col.size());
-    }
-    TRY(upload_csr(h, lv.dl.A, rows(A, 0, p0, nv, 0)));
+      return Z;
+    };
+    const HostCSR Av = rows(A, 0, p0, nv, 0);
+    // S = B (Mu^-1 B^T), the Schur operator of Alg. 2 (B^T already carries
+    // Mu^-1), and T = B Mu^-1 A (Mu^-1 B^T), the operator of the right-hand
+    // side of the pressure-correction solve, both on the pressure rows
+    const HostCSR S = product(Bp, BTv, nullptr);
+    const HostCSR T = product(Bp, product(Av, BTv, mass ? muinv.data() : nullptr), nullptr);
+    TRY(upload_csr(h, lv.dl.T, T));
+    TRY(upload_csr(h, lv.dl.A, Av));
     TRY(upload_csr(h, lv.dl.B, Bp));
     TRY(upload_csr(h, lv.dl.BT, BTv));
     TRY(upload_csr(h, lv.dl.S, S));
