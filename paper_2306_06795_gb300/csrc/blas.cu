@@ -144,6 +144,70 @@ template cudaError_t cheb_init<float>(int64_t, const float*, const float*, const
 template cudaError_t cheb_init<double>(int64_t, const double*, const double*, const uint8_t*, uint8_t, double, double,
                                        double*, double*, double*, cudaStream_t);
 
+// Both Chebyshev steps on the sliced-ELLPACK copy of M (a warp owns 32
+// consecutive rows, one per lane, values and columns of step k of the 32
+// rows contiguous; padding has column -1): STEP = 0 the plain step (w = d_in
+// or B^T d, dinv optional), STEP = 1 / 2 the first step from b, x set / x
+// accumulated.  Each row sums its entries in CSR order.
+template <typename T, int STEP>
+__global__ void __launch_bounds__(256) k_cheb_sell(int nrows, int nchunks, const int64_t* __restrict__ soff,
+                                                   const int* __restrict__ scol, const T* __restrict__ sval,
+                                                   const T* __restrict__ w, const T* __restrict__ dinv,
+                                                   T* __restrict__ x, T* __restrict__ r, const T* __restrict__ din,
+                                                   T* __restrict__ dout, T s, T c, T alpha, T beta) {
+  pdl_enter();
+  const int ch = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (ch >= nchunks) return;
+  const int lane = threadIdx.x & 31;
+  const int row = ch * 32 + lane;
+  const int64_t o0 = soff[ch];
+  const int wd = (int)((soff[ch + 1] - o0) >> 5);
+  const T* vp = sval + o0 + lane;
+  const int* cp = scol + o0 + lane;
+  constexpr int U = sizeof(T) == 4 ? 8 : 4;
+  T sum = T(0);
+  for (int k = 0; k < wd; k += U) {
+    T v[U];
+    int cc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int kk = k + u;
+      v[u] = kk < wd ? __ldcs(vp + (int64_t)kk * 32) : T(0);
+      cc[u] = kk < wd ? __ldcs(cp + (int64_t)kk * 32) : -1;
+    }
+    T xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? w[cc[u]] : T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cc[u] >= 0) sum += v[u] * xv[u];
+  }
+  if (row >= nrows) return;
+  if (STEP == 0) {
+    const T dv = din[row];
+    x[row] += dv;
+    const T rv = r[row] - (dinv ? dinv[row] * sum : sum);
+    r[row] = rv;
+    dout[row] = alpha * dv + beta * rv;
+  } else {
+    const T bv = w[row];
+    const T d0 = c * bv;
+    x[row] = STEP == 2 ? x[row] + d0 : d0;
+    const T rv = s * bv - c * sum;
+    r[row] = rv;
+    dout[row] = alpha * d0 + beta * rv;
+  }
+}
+
+template <typename T> static const T* sell_vals(const DevCSR& M);
+template <> const float* sell_vals<float>(const DevCSR& M) { return M.sv32; }
+template <> const double* sell_vals<double>(const DevCSR& M) { return M.sv64; }
+// the sliced copy when M has one and val is M's own value array
+template <typename T>
+static bool use_sell(const DevCSR& M, const T* val) {
+  return M.schunks > 0 && sell_vals<T>(M) && (const void*)val == (sizeof(T) == 4 ? (const void*)M.v32 : (const void*)M.v64);
+}
+
 template <typename T, int TPR>
 __global__ void __launch_bounds__(256) k_cheb_step(int nrows, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const T* __restrict__ val,
@@ -172,6 +236,12 @@ template <typename T>
 cudaError_t cheb_step(const DevCSR& M, const T* val, const T* w, const T* dinv, T* x, T* r, const T* d_in, T* d_out,
                       double alpha, double beta, cudaStream_t st) {
   if (M.nrows == 0) return cudaSuccess;
+  if (use_sell<T>(M, val)) {
+    const unsigned blocks = (unsigned)((M.schunks + 7) / 8);
+    SD_LAUNCH((k_cheb_sell<T, 0>), blocks, 256, 0, st, M.nrows, M.schunks, M.soff, M.scol, sell_vals<T>(M), w, dinv,
+              x, r, d_in, d_out, T(0), T(0), T(alpha), T(beta));
+    return cudaGetLastError();
+  }
   const int64_t total = (int64_t)M.nrows * 8;
   const unsigned blocks = (unsigned)((total + 255) / 256);
   SD_LAUNCH((k_cheb_step<T, 8>), blocks, 256, 0, st, M.nrows, M.rowptr, M.col, val, w, dinv, x, r, d_in, d_out, T(alpha), T(beta));
@@ -205,6 +275,16 @@ template <typename T>
 cudaError_t cheb_first(const DevCSR& M, const T* val, const T* b, double s, double theta, T* x, T* r, T* d_out,
                        double alpha, double beta, bool accumulate, cudaStream_t st) {
   if (M.nrows == 0) return cudaSuccess;
+  if (use_sell<T>(M, val)) {
+    const unsigned blocks = (unsigned)((M.schunks + 7) / 8);
+    if (accumulate)
+      SD_LAUNCH((k_cheb_sell<T, 2>), blocks, 256, 0, st, M.nrows, M.schunks, M.soff, M.scol, sell_vals<T>(M), b,
+                (const T*)nullptr, x, r, (const T*)nullptr, d_out, T(s), T(s / theta), T(alpha), T(beta));
+    else
+      SD_LAUNCH((k_cheb_sell<T, 1>), blocks, 256, 0, st, M.nrows, M.schunks, M.soff, M.scol, sell_vals<T>(M), b,
+                (const T*)nullptr, x, r, (const T*)nullptr, d_out, T(s), T(s / theta), T(alpha), T(beta));
+    return cudaGetLastError();
+  }
   const int64_t total = (int64_t)M.nrows * 8;
   const unsigned blocks = (unsigned)((total + 255) / 256);
   if (accumulate)
