@@ -84,6 +84,8 @@ struct Level {
   DevCSR K;
   bool hasP = false, Pident = false;
   DevCSR P, R;
+  bool hasRK = false;  // R K assembled: the restricted residual is one launch
+  DevCSR RK;
   bool has_patches = false;
   DevPatches pat;
   double omega = 1.0;
@@ -355,6 +357,40 @@ HostCSR transpose(const HostCSR& a) {
   return t;
 }
 
+// X Y of two host CSRs (X's columns index Y's rows), row i scaled by rs[i]
+// when given: FP64 sums in the order of X's row, then Y's row k; columns
+// sorted.
+HostCSR csr_product(const HostCSR& X, const HostCSR& Y, const double* rs) {
+  HostCSR Z;
+  Z.nrows = X.nrows;
+  Z.ncols = Y.ncols;
+  std::vector<double> acc(Y.ncols, 0.0);
+  std::vector<int> mark(Y.ncols, -1), cols;
+  for (int i = 0; i < X.nrows; ++i) {
+    cols.clear();
+    for (int e = X.rowptr[i]; e < X.rowptr[i + 1]; ++e) {
+      const int k = X.col[e];
+      const double xik = X.val[e];
+      for (int f = Y.rowptr[k]; f < Y.rowptr[k + 1]; ++f) {
+        const int j = Y.col[f];
+        if (mark[j] != i) {
+          mark[j] = i;
+          acc[j] = 0.0;
+          cols.push_back(j);
+        }
+        acc[j] += xik * Y.val[f];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int j : cols) {
+      Z.col.push_back(j);
+      Z.val.push_back(rs ? rs[i] * acc[j] : acc[j]);
+    }
+    Z.rowptr.push_back((int)Z.col.size());
+  }
+  return Z;
+}
+
 bool is_identity(const stokes_csr* c) {
   if (c->nrows != c->ncols || c->nnz != c->nrows) return false;
   for (int i = 0; i < c->nrows; ++i)
@@ -604,6 +640,18 @@ int L_cheb_first(stokes_handle* h, const DevCSR& M, const T* val, const T* b, do
     return STOKES_OK;
   }
   CK(cheb_first<T>(M, val, b, s, theta, x, r, dout, alpha, beta, accumulate, h->st));
+  return STOKES_OK;
+}
+
+template <typename T>
+int L_restrict_res(stokes_handle* h, const Level& L, const T* b, const T* x, T* y) {
+  if (h->led.count) {
+    h->led.bytes += double(L.R.nnz + L.RK.nnz) * (sizeof(T) + 4) + 8.0 * (L.R.nrows + 1) +
+                    double(L.R.ncols + L.RK.ncols + L.R.nrows) * sizeof(T);
+    h->led.launches += L.R.nrows > 0;
+    return STOKES_OK;
+  }
+  CK(restrict_res<T>(L.R, kval<T>(L.R), b, L.RK, kval<T>(L.RK), x, y, h->st));
   return STOKES_OK;
 }
 
@@ -870,8 +918,12 @@ int vcycle(stokes_handle* h, std::vector<Level>& lvs, int l) {
   TRY(L_coarse<T>(h, L, b, x));
   T* r = reinterpret_cast<T*>(L.r);
   Level& C = lvs[l + 1];
-  TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
-  TRY((L_spmv<T, T, T, T, T>(h, L.R, kval<T>(L.R), r, (const T*)nullptr, reinterpret_cast<T*>(C.b), SPMV_SET)));
+  if (main && L.hasRK) {
+    TRY(L_restrict_res<T>(h, L, b, x, reinterpret_cast<T*>(C.b)));
+  } else {
+    TRY((L_spmv<T, T, T, T, T>(h, L.K, kval<T>(L.K), x, b, r, SPMV_RES)));
+    TRY((L_spmv<T, T, T, T, T>(h, L.R, kval<T>(L.R), r, (const T*)nullptr, reinterpret_cast<T*>(C.b), SPMV_SET)));
+  }
   TRY(vcycle<T>(h, lvs, l + 1));
   TRY((L_spmv<T, T, T, T, T>(h, L.P, kval<T>(L.P), reinterpret_cast<const T*>(C.x), (const T*)nullptr, x, SPMV_ADD)));
   // level 1 of the DC cycle with P0 = I: the last scatter of the
@@ -1445,45 +1497,12 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
     };
     const int nv = (int)p0, np = (int)(lv.n - p0);
     const HostCSR Bp = rows(B, p0, lv.n, nv, 0), BTv = rows(BT, 0, p0, np, nv);
-    // X Y of two host CSRs (X's columns index Y's rows), row i scaled by
-    // rs[i] when given: FP64 sums in the order of X's row, then Y's row k;
-    // columns sorted
-    auto product = [](const HostCSR& X, const HostCSR& Y, const double* rs) {
-      HostCSR Z;
-      Z.nrows = X.nrows;
-      Z.ncols = Y.ncols;
-      std::vector<double> acc(Y.ncols, 0.0);
-      std::vector<int> mark(Y.ncols, -1), cols;
-      for (int i = 0; i < X.nrows; ++i) {
-        cols.clear();
-        for (int e = X.rowptr[i]; e < X.rowptr[i + 1]; ++e) {
-          const int k = X.col[e];
-          const double xik = X.val[e];
-          for (int f = Y.rowptr[k]; f < Y.rowptr[k + 1]; ++f) {
-            const int j = Y.col[f];
-            if (mark[j] != i) {
-              mark[j] = i;
-              acc[j] = 0.0;
-              cols.push_back(j);
-            }
-            acc[j] += xik * Y.val[f];
-          }
-        }
-        std::sort(cols.begin(), cols.end());
-        for (int j : cols) {
-          Z.col.push_back(j);
-          Z.val.push_back(rs ? rs[i] * acc[j] : acc[j]);
-        }
-        Z.rowptr.push_back((int)Z.col.size());
-      }
-      return Z;
-    };
     const HostCSR Av = rows(A, 0, p0, nv, 0);
     // S = B (Mu^-1 B^T), the Schur operator of Alg. 2 (B^T already carries
     // Mu^-1), and T = B Mu^-1 A (Mu^-1 B^T), the operator of the right-hand
     // side of the pressure-correction solve, both on the pressure rows
-    const HostCSR S = product(Bp, BTv, nullptr);
-    const HostCSR T = product(Bp, product(Av, BTv, mass ? muinv.data() : nullptr), nullptr);
+    const HostCSR S = csr_product(Bp, BTv, nullptr);
+    const HostCSR T = csr_product(Bp, csr_product(Av, BTv, mass ? muinv.data() : nullptr), nullptr);
     TRY(upload_csr(h, lv.dl.T, T));
     TRY(upload_csr(h, lv.dl.A, Av));
     TRY(upload_csr(h, lv.dl.B, Bp));
@@ -1923,7 +1942,18 @@ static int setup_impl(stokes_handle* h, const stokes_problem* const* probs, int 
       lv.hasP = true;
       lv.Pident = ident && l == 0;
       TRY(upload_csr(h, lv.P, P));
-      TRY(upload_csr(h, lv.R, transpose(P)));
+      const HostCSR R = transpose(P);
+      TRY(upload_csr(h, lv.R, R));
+      // levels >= 3: R (b - K x) as R b - (R K) x in one launch where R K has
+      // no more entries than K and R together (on levels 1 and 2 the
+      // sliced-ELLPACK / row-block residual and restriction measured faster)
+      if (l >= 3) {
+        HostCSR RK = csr_product(R, K, nullptr);
+        if (RK.col.size() <= K.col.size() + R.col.size()) {
+          TRY(upload_csr(h, lv.RK, RK));
+          lv.hasRK = true;
+        }
+      }
     }
     // coarsest blocks of the instances ending at l
     std::vector<int> boff, bn;

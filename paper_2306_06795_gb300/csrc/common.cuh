@@ -79,6 +79,12 @@ template <typename TA, typename TX, typename TB, typename TY, typename TACC>
 cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y, int mode,
                  double s0, double s1, const uint8_t* kind, cudaStream_t st);
 
+// y = R b - (R K) x: the restricted residual of a level with R K assembled
+// (R and RK have the same rows; vector CSR, the wider of their TPRs).
+template <typename T>
+cudaError_t restrict_res(const DevCSR& R, const T* rval, const T* b, const DevCSR& RK, const T* rkval, const T* x,
+                         T* y, cudaStream_t st);
+
 // Side streams and events that let independent launches of one step run
 // side by side: fork on the main stream, launch on the sides, join back.
 constexpr int kForkMax = 6;

@@ -2,6 +2,8 @@
 // transfers and the FP64 defect-correction residual (steps a1-a3).
 // TPR threads cooperate on a row; the group size is chosen from the mean
 // row length so that a warp streams contiguous values and columns.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sd {
@@ -242,6 +244,56 @@ cudaError_t spmv(const DevCSR& A, const TA* val, const TX* x, const TB* b, TY* y
     default: return launch_mode<TA, TX, TB, TY, TACC, 32>(A, val, x, b, y, mode, s0, s1, kind, st);
   }
 }
+
+// y = R b - (R K) x, both sums of a coarse row by the same TPR lanes (each
+// in CSR order per lane, then a fixed shuffle tree).
+template <typename T, int TPR>
+__global__ void __launch_bounds__(256) k_restrict_res(int nrows, const int* __restrict__ rp, const int* __restrict__ rc,
+                                                      const T* __restrict__ rv, const T* __restrict__ b,
+                                                      const int* __restrict__ kp, const int* __restrict__ kc,
+                                                      const T* __restrict__ kv, const T* __restrict__ x,
+                                                      T* __restrict__ y) {
+  pdl_enter();
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = tid / TPR;
+  const int lane = (int)(tid % TPR);
+  const bool valid = row < nrows;
+  T s1 = T(0), s2 = T(0);
+  if (valid) {
+    for (int k = rp[row] + lane; k < rp[row + 1]; k += TPR) s1 += rv[k] * b[rc[k]];
+    for (int k = kp[row] + lane; k < kp[row + 1]; k += TPR) s2 += kv[k] * x[kc[k]];
+  }
+#pragma unroll
+  for (int off = TPR / 2; off > 0; off >>= 1) {
+    s1 += __shfl_down_sync(0xffffffffu, s1, off, TPR);
+    s2 += __shfl_down_sync(0xffffffffu, s2, off, TPR);
+  }
+  if (valid && lane == 0) y[row] = s1 - s2;
+}
+
+template <typename T>
+cudaError_t restrict_res(const DevCSR& R, const T* rval, const T* b, const DevCSR& RK, const T* rkval, const T* x,
+                         T* y, cudaStream_t st) {
+  if (R.nrows == 0) return cudaSuccess;
+  if (RK.nrows != R.nrows) return cudaErrorInvalidValue;
+  const int tpr = std::max(R.tpr, RK.tpr);
+  const int64_t total = (int64_t)R.nrows * tpr;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+#define SD_RR(TP) SD_LAUNCH((k_restrict_res<T, TP>), blocks, 256, 0, st, R.nrows, R.rowptr, R.col, rval, b, RK.rowptr, RK.col, rkval, x, y)
+  switch (tpr) {
+    case 2: SD_RR(2); break;
+    case 4: SD_RR(4); break;
+    case 8: SD_RR(8); break;
+    case 16: SD_RR(16); break;
+    default: SD_RR(32); break;
+  }
+#undef SD_RR
+  return cudaGetLastError();
+}
+template cudaError_t restrict_res<float>(const DevCSR&, const float*, const float*, const DevCSR&, const float*,
+                                         const float*, float*, cudaStream_t);
+template cudaError_t restrict_res<double>(const DevCSR&, const double*, const double*, const DevCSR&, const double*,
+                                          const double*, double*, cudaStream_t);
 
 #define SD_SPMV(TA, TX, TB, TY, TACC)                                                                  \
   template cudaError_t spmv<TA, TX, TB, TY, TACC>(const DevCSR&, const TA*, const TX*, const TB*, TY*, \
