@@ -2405,12 +2405,28 @@ int stokes_factor_patches(stokes_handle* h, int64_t* nsingular) {
   if (!h->dsing) TRY(dalloc(h, &h->dsing, 1));
   int* dsing = h->dsing;
   CK(cudaMemsetAsync(dsing, 0, sizeof(int), h->st));
+  // the levels are independent (own factors and scratch): each runs on a
+  // side stream, forked from and joined back to the handle's stream, so the
+  // latency-bound launches of the small levels overlap the large ones
+  CK(cudaEventRecord(h->fj.fork, h->st));
+  bool used[kForkMax] = {};
   for (int l = 0; l < h->L; ++l) {
     Level& lv = h->lv[l];
     if (!lv.has_patches) continue;
-    if (h->prec == STOKES_FP32) CK(vanka_factor<float>(lv.pat, lv.K, dsing, h->st));
-    else CK(vanka_factor<double>(lv.pat, lv.K, dsing, h->st));
+    const int k = l % kForkMax;
+    cudaStream_t s = h->fj.side[k];
+    if (!used[k]) {
+      CK(cudaStreamWaitEvent(s, h->fj.fork, 0));
+      used[k] = true;
+    }
+    if (h->prec == STOKES_FP32) CK(vanka_factor<float>(lv.pat, lv.K, dsing, s));
+    else CK(vanka_factor<double>(lv.pat, lv.K, dsing, s));
   }
+  for (int k = 0; k < kForkMax; ++k)
+    if (used[k]) {
+      CK(cudaEventRecord(h->fj.join[k], h->fj.side[k]));
+      CK(cudaStreamWaitEvent(h->st, h->fj.join[k], 0));
+    }
   int ns = 0;
   CK(cudaMemcpyAsync(&ns, dsing, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
