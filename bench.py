@@ -61,6 +61,24 @@ def apply_traffic():
     return APPLY_L0_TRAFFIC["dram_bytes"] if hsh.hexdigest() == APPLY_L0_TRAFFIC["sha256"] else None
 
 
+def fgmres_leg(n, nnz_k0, iters, restart, outside_ms, peak_gbs):
+    """The FGMRES leg outside the cycle, per iteration: algorithmic bytes and
+    FP64 FMAs of the Arnoldi step j (NK = j + 1 basis vectors): the FP64 K0
+    SpMV (values, columns, row pointers, z gathered, w written), the three
+    fused Gram-Schmidt passes (dots: NK columns + w; axpy + dots: NK columns +
+    w read and written; axpy + norm: the same) and the next Krylov vector (w
+    read, v written in FP64 and FP32); 4 NK + 1 FMAs per row plus one per
+    nonzero of K0.  Against the measured time outside the cycle."""
+    steps = [(j % restart) + 1 for j in range(iters)]
+    byt = sum(nnz_k0 * 12 + 4 * (n + 1) + 16 * n + (3 * nk + 5) * 8 * n + 20 * n for nk in steps) / iters
+    dfma = sum(nnz_k0 + (4 * nk + 1) * n for nk in steps) / iters
+    return {"outside_cycle_ms_per_iter": outside_ms, "bytes_per_iter": byt, "dfma_per_iter": dfma,
+            "GBps": byt / outside_ms / 1e6, "frac_of_measured_hbm": byt / outside_ms / 1e6 / peak_gbs,
+            "T_dfma_per_s": dfma / outside_ms / 1e9,
+            "note": "time outside the cycle = (step - factorisation - iterations x cycle) / iterations; "
+                    "includes the restart's residual and x += Z y"}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -643,6 +661,9 @@ def run_gpu(args):
         "fp64_precond": {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_step": ms64},
         "fp32_vs_fp64_solution_relerr": err32,
         "factor_ms": {"fp32": fct[sd.STOKES_FP32], "fp64": fct[sd.STOKES_FP64]},
+        "fgmres": fgmres_leg(int(pr.K[0].shape[0]), int(pr.K[0].nnz), int(info32[0]), 30,
+                             (ms - fct[sd.STOKES_FP32] - int(info32[0]) * vc[sd.STOKES_FP32][0]) / int(info32[0]),
+                             peak),
         "vcycle": {"fp32_ms": vc[sd.STOKES_FP32][0], "fp64_ms": vc[sd.STOKES_FP64][0],
                    "fp32_bytes": vc[sd.STOKES_FP32][1], "fp64_bytes": vc[sd.STOKES_FP64][1],
                    "fp32_GBps": vc[sd.STOKES_FP32][1] / vc[sd.STOKES_FP32][0] / 1e6,

@@ -92,3 +92,16 @@ def test_zero_mean_pressure_removes_the_mass_weighted_mean():
 def pytest_approx(v):
     import pytest
     return pytest.approx(v, rel=1e-9)
+
+
+def test_fgmres_leg_counts_the_arnoldi_steps_of_each_restart():
+    """Iterations 1..3 with restart 2 use 1, 2, then 1 basis vectors; each
+    step reads K0 once (12 B per nonzero) and V in three passes."""
+    import bench
+    n, nnz = 10, 30
+    rec = bench.fgmres_leg(n, nnz, 3, 2, 0.5, 1000.0)
+    per = [nnz * 12 + 4 * (n + 1) + 16 * n + (3 * k + 5) * 8 * n + 20 * n for k in (1, 2, 1)]
+    assert rec["bytes_per_iter"] == sum(per) / 3
+    assert rec["dfma_per_iter"] == sum(nnz + (4 * k + 1) * n for k in (1, 2, 1)) / 3
+    assert abs(rec["GBps"] - rec["bytes_per_iter"] / 0.5 / 1e6) < 1e-12
+    assert abs(rec["frac_of_measured_hbm"] - rec["GBps"] / 1000.0) < 1e-12
