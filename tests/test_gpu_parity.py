@@ -96,6 +96,25 @@ def test_vcycle_fp64_matches_oracle(sd, c1, h64):
         assert rel(host(z), o.apply(r)) < 1e-12
 
 
+def test_vcycle_fp64_five_levels_matches_oracle(sd):
+    """A 64^2 cavity has five levels, so level 3 restricts its residual as
+    R b - (R K) x in one launch (R K assembled at setup) and the cycle's
+    other fused steps all run; the FP64 cycle equals the oracle's, and so
+    does the FP32 cycle to FP32 accuracy."""
+    pr = stokes.build_th(M.unit_square(64), bc="lid")
+    assert pr.nlevels >= 5
+    o = make_oracle(pr, PRM)
+    r = np.random.default_rng(41).standard_normal(pr.b.size)
+    ref = o.apply(r)
+    for prec, tol in ((sd.STOKES_FP64, 1e-12), (sd.STOKES_FP32, 1e-5)):
+        h = sd.stokes_setup(pr, dict(PRM, precision=prec))
+        sd.stokes_factor_patches(h)
+        z = torch.empty(r.size, dtype=torch.float64, device="cuda")
+        sd.stokes_vcycle(h, dev(r), z)
+        assert rel(host(z), ref) < tol, prec
+        sd.stokes_destroy(h)
+
+
 def test_vcycle_replay_is_bitwise_deterministic(sd, c1, h32):
     r = dev(np.random.default_rng(12).standard_normal(c1.b.size))
     z1 = torch.empty_like(r)
