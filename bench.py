@@ -716,8 +716,9 @@ def run_gpu(args):
 
 def run_profile(args):
     """Kernel launches for ncu: factorisation, then DC cycles (graph replays),
-    on C2 (default), C4, or the 3D Taylor-Hood lid-driven cavity on an N^3
-    cube (`cubeN`, a small case of the C4 kernels)."""
+    on C2 (default), C2 with DLSC relaxation on every level (`c2-dlsc`), C4,
+    or the 3D Taylor-Hood lid-driven cavity on an N^3 cube (`cubeN`, a small
+    case of the C4 kernels)."""
     import torch
 
     import paper_2306_06795_gb300 as sd
@@ -726,6 +727,9 @@ def run_profile(args):
     name = args.profile_problem or "c2"
     if name == "c2":
         pr, prm = configs.c2(), configs.TH2D_VANKA
+    elif name == "c2-dlsc":
+        pr = configs.c2()
+        prm = configs.th2d_dlsc(pr.nlevels)
     elif name == "c4":
         pr, prm = configs.c4(), configs.TH3D_VANKA
     else:
@@ -829,7 +833,7 @@ def main():
     ap.add_argument("--profile-cycles", type=int, default=0,
                     help="profiling driver: set up, factorise and run this many DC cycles, print nothing")
     ap.add_argument("--profile-problem", default=None,
-                    help="profiling driver problem: c2 (default), c4, or cubeN (3D lid-driven cavity on an N^3 cube)")
+                    help="profiling driver problem: c2 (default), c2-dlsc, c4, or cubeN (3D lid-driven cavity on an N^3 cube)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling driver: set up, factorise and run one FP32-preconditioned solve")
     ap.add_argument("--ref-iters", type=int, default=34,
