@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(NTHR, 512 / NTHR) k_vanka_factor_tc(int nlist,
       const int nr = nT - 1;
       if constexpr (UMMA) {
         if (nr > 0 && uok) {
-          // round 1: X = [M_iK]_{i != K} P  (rows 32 ii + r of A are row r of M_{i2,K})
+          // pass 1: X = [M_iK]_{i != K} P  (rows 32 ii + r of A are row r of M_{i2,K})
           for (int e = tid; e < nr * 32 * 32; e += NTHR) {
             int q, k;
             kmaj_rc(e, q, k);
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(NTHR, 512 / NTHR) k_vanka_factor_tc(int nlist,
             tc_fence_before();
           }
           __syncthreads();
-          // round 2: D = [X_i] [M_jK]^T, then M_ij -= D on the lower tiles
+          // pass 2: D = [X_i] [M_jK]^T, then M_ij -= D on the lower tiles
           if (uok) {
             for (int e = tid; e < nr * 32 * 32; e += NTHR) {
               int q, k;
