@@ -237,7 +237,7 @@ constexpr int kSellRows = 262144;
 // stream SpMV.
 constexpr int kStreamMinRows = 32768;
 
-int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
+int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c, int sell_rows = kSellRows) {
   d.nrows = c.nrows;
   d.ncols = c.ncols;
   d.nnz = (int64_t)c.col.size();
@@ -269,10 +269,10 @@ int upload_csr(stokes_handle* h, DevCSR& d, const HostCSR& c) {
     TRY(upload(h, &d.tdesc, td));
     return STOKES_OK;
   };
-  if (c.nrows >= kStreamMinRows && c.nrows < kSellRows && maxrow <= kStreamNnz) return stream_tiles();
+  if (c.nrows >= kStreamMinRows && c.nrows < sell_rows && maxrow <= kStreamNnz) return stream_tiles();
   // sliced ELLPACK copy when the padding to the longest row of each chunk
   // of 32 rows stays small
-  if (c.nrows >= kSellRows) {
+  if (c.nrows >= sell_rows) {
     const int nch = (c.nrows + 31) / 32;
     std::vector<int64_t> off(nch + 1, 0);
     for (int ch = 0; ch < nch; ++ch) {
@@ -1503,11 +1503,14 @@ static int setup_dlsc(stokes_handle* h, Level& lv, const stokes_problem* const* 
     // side of the pressure-correction solve, both on the pressure rows
     const HostCSR S = csr_product(Bp, BTv, nullptr);
     const HostCSR T = csr_product(Bp, csr_product(Av, BTv, mass ? muinv.data() : nullptr), nullptr);
-    TRY(upload_csr(h, lv.dl.T, T));
-    TRY(upload_csr(h, lv.dl.A, Av));
-    TRY(upload_csr(h, lv.dl.B, Bp));
-    TRY(upload_csr(h, lv.dl.BT, BTv));
-    TRY(upload_csr(h, lv.dl.S, S));
+    // the DLSC operators take the sliced-ELLPACK copy from 64 k rows on (their
+    // Chebyshev steps and SpMVs measured faster there than on row-block tiles)
+    constexpr int kDlscSellRows = 65536;
+    TRY(upload_csr(h, lv.dl.T, T, kDlscSellRows));
+    TRY(upload_csr(h, lv.dl.A, Av, kDlscSellRows));
+    TRY(upload_csr(h, lv.dl.B, Bp, kDlscSellRows));
+    TRY(upload_csr(h, lv.dl.BT, BTv, kDlscSellRows));
+    TRY(upload_csr(h, lv.dl.S, S, kDlscSellRows));
     lv.dl.p0 = p0;
     lv.dl.pp_zero = !has_pp;
   } else {
