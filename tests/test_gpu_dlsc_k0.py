@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import direct, krylov
-from problems import configs
+from problems import configs, mesh as M, stokes
 from tests.helpers import make_oracle, rel
 
 pytestmark = pytest.mark.gpu
@@ -108,3 +108,25 @@ def test_dlsc_amg_c2_full_size(sd):
         assert rc == sd.STOKES_OK and info[0][2] <= 1e-8
         its[prec] = info[0][0]
     assert abs(its[sd.STOKES_FP32] - its[sd.STOKES_FP64]) <= 2
+
+
+def test_dlsc_batched_instances_fp64(sd):
+    """Two Taylor-Hood instances in one handle (the same operator, so the
+    same Chebyshev bounds, which batched DLSC requires; different right-hand
+    sides), DLSC on every level: a batched handle keeps the level-sized DLSC
+    operators with row masks (one-instance handles take the row-range
+    sweep), and each instance's part of the FP64 cycle equals the oracle's."""
+    probs = [stokes.build_th(M.unit_square(16), bc="noslip", rhs="random_b", seed=s) for s in (91, 92)]
+    prm = configs.th2d_dlsc(probs[0].nlevels)
+    h = sd.stokes_setup(probs, dict(prm, precision=sd.STOKES_FP64))
+    sd.stokes_factor_patches(h)
+    r = np.concatenate([np.random.default_rng(k).standard_normal(p.b.size) for k, p in enumerate(probs)])
+    z = torch.empty(r.size, dtype=torch.float64, device="cuda")
+    sd.stokes_vcycle(h, dev(r), z)
+    zh = host(z)
+    o = 0
+    for p in probs:
+        n = p.b.size
+        assert rel(zh[o:o + n], make_oracle(p, prm).apply(r[o:o + n])) < 1e-12
+        o += n
+    sd.stokes_destroy(h)
