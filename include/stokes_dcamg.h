@@ -135,7 +135,10 @@ typedef struct {
   const stokes_csr* R0p;          /* Pi^T M_dg, n_cg x n_dg, or NULL for TH */
   const stokes_csr* Mcg;          /* P1 mass matrix of the K1 pressure, or NULL */
   double mcg_lo, mcg_hi;          /* interval holding the eigenvalues of diag(Mcg)^-1 Mcg */
-  /* DLSC (Sec. 3.3.2): largest-eigenvalue estimates per level, may be NULL */
+  /* DLSC (Sec. 3.3.2): largest-eigenvalue estimates per level, may be NULL.
+   * A level's Chebyshev interval is one per handle: the instances of a
+   * handle that relax a level with DLSC must give the same lambda_A and
+   * lambda_S for it (stokes_setup rejects others). */
   const double* lambda_A;         /* [nlevels] of the velocity block A */
   const double* lambda_S;         /* [nlevels] of B Mu^-1 B^T */
   /* BTP (Sec. 4), used when stokes_params.preconditioner is
